@@ -1,0 +1,262 @@
+"""FP64 CPU oracle of the 3D Gaussian Splatting tile rasterizer (Kerbl et al. 2023).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this package.
+It shares no code with the CUDA path (``paper_2308_04079_gb300``) and never imports it;
+the product path never imports this package.
+
+Functions (each a thin ctypes marshaller around ``gs_oracle.c``):
+
+* :func:`preprocess`       per-Gaussian cull / EWA projection / radius / tile rectangle /
+                           SH colour (Sec. 4, Sec. 6, eq. volume-render, eq. quat).
+* :func:`bin_instances`    the binning definition of App. C / Algorithm 2 on given fp32
+                           screen-space values: keys, one stable sort, tile ranges.
+* :func:`render_forward`   per-pixel front-to-back blending, eq. front-to-back, with the
+                           App. C numerical-stability rules.
+* :func:`render_backward`  analytic FP64 gradients (Sec. 6 traversal, App. A chain rule).
+* :func:`sh_eval`          real spherical-harmonic basis, bands 0..3, and its gradient.
+* :func:`quat_to_rot`      eq. quat of App. A.
+
+Every pixel/Gaussian decision that lies within a relative margin of its threshold is
+reported as ambiguous (``pix_amb``, ``gauss_amb``), see the bit constants below.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+# per-Gaussian ambiguity bits
+AMB_CULL = 1
+AMB_RECT = 2
+AMB_RGB = 4
+AMB_PIXEL = 8
+AMB_CLAMP = 16
+# per-pixel ambiguity bits
+PIX_DECISION = 1
+PIX_CLAMP = 2
+
+DEFAULT_CFG = dict(
+    tile_w=16, tile_h=16,          # Sec. 6 / App. C: 16x16 tiles
+    alpha_min=1.0 / 255.0,         # App. C: skip alpha < 1/255
+    alpha_max=0.99,                # App. C: clamp alpha at 0.99
+    T_min=1e-4,                    # App. C: stop before accumulated opacity exceeds 0.9999
+    dilation=0.3,                  # low-pass filter added to the diagonal of Sigma'
+    guard=1.3,                     # guard band on the frustum tangents (Sec. 6)
+    extent=3.0,                    # 3-sigma screen extent (Sec. 6, 99% interval)
+    radius_max=1 << 24,            # radius clamp (pixels)
+    eps_geom=2e-6,                 # ambiguity margin, geometric decisions (relative)
+    eps_alpha=1e-4,                # ambiguity margin, alpha / transmittance decisions (relative)
+)
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        D = ctypes.POINTER(ctypes.c_double)
+        I32 = ctypes.POINTER(ctypes.c_int32)
+        U32 = ctypes.POINTER(ctypes.c_uint32)
+        U8 = ctypes.POINTER(ctypes.c_uint8)
+        F = ctypes.POINTER(ctypes.c_float)
+        U64 = ctypes.POINTER(ctypes.c_uint64)
+        L = ctypes.c_long
+        lib.orc_quat_to_rot.argtypes = [D, D]
+        lib.orc_sh_eval.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D]
+        lib.orc_preprocess.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
+                                       I32, D, D, D, D, I32, I32, D, D, U32, I32, I32]
+        lib.orc_render_forward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
+                                           D, U8, D, D, I32, U8, U32]
+        lib.orc_render_backward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
+                                            D, U8, D, D, D, D, D, D, D, D, D, U8, U32]
+        lib.orc_bin.argtypes = [L, F, F, I32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                L, U64, U32, U32]
+        lib.orc_bin.restype = L
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def cam_array(cam) -> np.ndarray:
+    """Flatten a camera (width, height, fx, fy, cx, cy, R (world->camera), t, near)."""
+    a = np.zeros(19, dtype=np.float64)
+    a[0], a[1] = cam.width, cam.height
+    a[2], a[3], a[4], a[5] = cam.fx, cam.fy, cam.cx, cam.cy
+    a[6:15] = np.asarray(cam.R, dtype=np.float64).reshape(9)
+    a[15:18] = np.asarray(cam.t, dtype=np.float64).reshape(3)
+    a[18] = cam.near
+    return a
+
+
+def cfg_array(**overrides) -> np.ndarray:
+    c = dict(DEFAULT_CFG)
+    for k, v in overrides.items():
+        if k not in c:
+            raise KeyError(k)
+        c[k] = v
+    return np.array([c["tile_w"], c["tile_h"], c["alpha_min"], c["alpha_max"], c["T_min"],
+                     c["dilation"], c["guard"], c["extent"], c["radius_max"], c["eps_geom"],
+                     c["eps_alpha"]], dtype=np.float64)
+
+
+def _gauss_args(g):
+    n = int(np.asarray(g.means).shape[0])
+    means = _f64(g.means).reshape(n, 3)
+    scales = _f64(g.scales).reshape(n, 3)
+    quats = _f64(g.quats).reshape(n, 4)
+    opac = _f64(g.opacities).reshape(n)
+    sh = _f64(g.sh)
+    sh_stride = sh.shape[1]
+    return n, means, scales, quats, opac, sh, int(g.sh_degree), int(sh_stride)
+
+
+def tiles_xy(cam, cfg: np.ndarray):
+    tw, th = int(cfg[0]), int(cfg[1])
+    return (cam.width + tw - 1) // tw, (cam.height + th - 1) // th
+
+
+def quat_to_rot(q) -> np.ndarray:
+    q = _f64(q).reshape(4)
+    R = np.zeros(9)
+    _load().orc_quat_to_rot(_p(q, ctypes.c_double), _p(R, ctypes.c_double))
+    return R.reshape(3, 3)
+
+
+def sh_eval(deg: int, dirs):
+    dirs = _f64(dirs).reshape(-1, 3)
+    n = dirs.shape[0]
+    D = (deg + 1) ** 2
+    Y = np.zeros((n, D))
+    dY = np.zeros((n, D, 3))
+    _load().orc_sh_eval(deg, n, _p(dirs, ctypes.c_double), _p(Y, ctypes.c_double), _p(dY, ctypes.c_double))
+    return Y, dY
+
+
+def preprocess(g, cam, cfg: np.ndarray | None = None) -> dict:
+    cfg = cfg_array() if cfg is None else cfg
+    n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
+    ca = cam_array(cam)
+    out = dict(visible=np.zeros(n, np.int32), uv=np.zeros((n, 2)), depth=np.zeros(n),
+               cov2d=np.zeros((n, 3)), conic=np.zeros((n, 3)), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32), rgb=np.zeros((n, 3)), rgb_raw=np.zeros((n, 3)),
+               amb=np.zeros(n, np.uint32), rect_in=np.zeros((n, 4), np.int32),
+               rect_out=np.zeros((n, 4), np.int32))
+    D, I32, U32 = ctypes.c_double, ctypes.c_int32, ctypes.c_uint32
+    _load().orc_preprocess(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
+                           _p(ca, D), _p(cfg, D), _p(out["visible"], I32), _p(out["uv"], D),
+                           _p(out["depth"], D), _p(out["cov2d"], D), _p(out["conic"], D),
+                           _p(out["radius"], I32), _p(out["rect"], I32), _p(out["rgb"], D),
+                           _p(out["rgb_raw"], D), _p(out["amb"], U32), _p(out["rect_in"], I32),
+                           _p(out["rect_out"], I32))
+    return out
+
+
+def _mask_arg(cam, cfg, tile_mask):
+    if tile_mask is None:
+        return None
+    TX, TY = tiles_xy(cam, cfg)
+    m = np.ascontiguousarray(np.asarray(tile_mask, dtype=np.uint8).reshape(TX * TY))
+    return m
+
+
+def render_forward(g, cam, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
+    """Planar image [3, H, W], final transmittance [H, W], last contributor (1-based
+    position in the tile list, 0 = none) [H, W], per-pixel and per-Gaussian ambiguity."""
+    cfg = cfg_array() if cfg is None else cfg
+    n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
+    ca = cam_array(cam)
+    W, H = cam.width, cam.height
+    bg = _f64(bg).reshape(3)
+    m = _mask_arg(cam, cfg, tile_mask)
+    img = np.zeros((3, H, W))
+    T = np.ones((H, W))
+    last = np.zeros((H, W), np.int32)
+    pix = np.zeros((H, W), np.uint8)
+    gamb = np.zeros(n, np.uint32)
+    D = ctypes.c_double
+    _load().orc_render_forward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
+                               _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(img, D), _p(T, D),
+                               _p(last, ctypes.c_int32), _p(pix, ctypes.c_uint8), _p(gamb, ctypes.c_uint32))
+    return dict(img=img, T=T, last=last, pix_amb=pix, gauss_amb=gamb)
+
+
+def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
+    """Analytic FP64 gradients of L = <dL_dimg, image> w.r.t. every input, plus the
+    screen-space gradients (mean2D, conic, opacity, colour) that the backward walk
+    accumulates."""
+    cfg = cfg_array() if cfg is None else cfg
+    n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
+    ca = cam_array(cam)
+    W, H = cam.width, cam.height
+    bg = _f64(bg).reshape(3)
+    dimg = _f64(dL_dimg).reshape(3, H, W)
+    m = _mask_arg(cam, cfg, tile_mask)
+    out = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               opacities=np.zeros(n), sh=np.zeros_like(sh), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
+               rgb=np.zeros((n, 3)), pix_amb=np.zeros((H, W), np.uint8), gauss_amb=np.zeros(n, np.uint32))
+    D = ctypes.c_double
+    _load().orc_render_backward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
+                                _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(dimg, D),
+                                _p(out["means"], D), _p(out["scales"], D), _p(out["quats"], D),
+                                _p(out["opacities"], D), _p(out["sh"], D), _p(out["uv"], D), _p(out["conic"], D),
+                                _p(out["rgb"], D), _p(out["pix_amb"], ctypes.c_uint8),
+                                _p(out["gauss_amb"], ctypes.c_uint32))
+    return out
+
+
+def bin_instances(uv, depth, radius, width: int, height: int, tile_w: int = 16, tile_h: int = 16,
+                  capacity: int | None = None):
+    """Binning definition on given fp32 (u, v), fp32 depth and integer radius
+    (radius <= 0: culled).  Returns (keys u64 [K], vals u32 [K], ranges u32 [T, 2])."""
+    uv = np.ascontiguousarray(np.asarray(uv, dtype=np.float32).reshape(-1, 2))
+    depth = np.ascontiguousarray(np.asarray(depth, dtype=np.float32).reshape(-1))
+    radius = np.ascontiguousarray(np.asarray(radius, dtype=np.int32).reshape(-1))
+    n = uv.shape[0]
+    TX, TY = (width + tile_w - 1) // tile_w, (height + tile_h - 1) // tile_h
+    ranges = np.zeros((TX * TY, 2), np.uint32)
+    lib = _load()
+    if capacity is None:
+        capacity = instance_count(uv, radius, width, height, tile_w, tile_h)
+    keys = np.zeros(max(capacity, 1), np.uint64)
+    vals = np.zeros(max(capacity, 1), np.uint32)
+    K = lib.orc_bin(n, _p(uv, ctypes.c_float), _p(depth, ctypes.c_float), _p(radius, ctypes.c_int32),
+                    width, height, tile_w, tile_h, capacity, _p(keys, ctypes.c_uint64),
+                    _p(vals, ctypes.c_uint32), _p(ranges, ctypes.c_uint32))
+    if K < 0:
+        raise OverflowError("instance count exceeds capacity")
+    return keys[:K], vals[:K], ranges
+
+
+def instance_count(uv, radius, width, height, tile_w=16, tile_h=16) -> int:
+    """Number of (Gaussian, overlapped tile) instances, by the same rectangle rule."""
+    uv = np.asarray(uv, dtype=np.float32).reshape(-1, 2)
+    radius = np.asarray(radius, dtype=np.int64).reshape(-1)
+    TX, TY = (width + tile_w - 1) // tile_w, (height + tile_h - 1) // tile_h
+    fu = np.floor(uv[:, 0]).astype(np.int64)
+    fv = np.floor(uv[:, 1]).astype(np.int64)
+    x0 = np.clip(np.floor_divide(fu - radius, tile_w), 0, TX)
+    x1 = np.clip(np.floor_divide(fu + radius, tile_w) + 1, 0, TX)
+    y0 = np.clip(np.floor_divide(fv - radius, tile_h), 0, TY)
+    y1 = np.clip(np.floor_divide(fv + radius, tile_h) + 1, 0, TY)
+    ok = (radius > 0) & (x0 < x1) & (y0 < y1)
+    return int(np.sum(np.where(ok, (x1 - x0) * (y1 - y0), 0)))
+
