@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable tile rasterizer: 1080p forward+backward frames/s at 3M
+Gaussians (synthetic large unbounded scene, SH degree 3, 1920x1080).
+
+One step = one pass of the whole hot path over one frame: gs_preprocess, gs_bin_sort,
+gs_render_forward, gs_render_backward (tiles, then Gaussians).  Inputs are resident in HBM
+for ``value``; ``e2e`` repeats the measurement with the inputs in pinned host memory and the
+image and gradients copied back every step.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this project has) on a
+bounded sample of the same frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p fwd+bwd frames/s at 3M Gaussians"
+UNIT = "frames/s"
+WORKLOAD = "large unbounded scene: 3M Gaussians, SH degree 3, 1920x1080, forward+backward"
+
+# Peak used for the ALU-bound render kernels: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz.
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# FP32 flops per evaluated (pixel, Gaussian) pair on the path every evaluation takes
+# (offset 2, quadratic form 7, exp 2, opacity 1, clamp 1, threshold 1) and extra flops of a
+# blended pair (forward: transmittance 2, weight 1, colour 6; backward: recovery 5,
+# colour gradient 3, alpha gradient 7, R update 9, conic/mean/opacity gradients 15).
+FLOPS_EVAL = 14
+FLOPS_BLEND_FWD = 9
+FLOPS_BLEND_BWD = 39
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# Our arm
+# ------------------------------------------------------------------------------------------
+def launches_per_step(layout) -> int:
+    binning = (1 + layout.depth_passes + 1 + 1 + layout.key_passes + 1) if layout.depth_passes else \
+        (1 + 1 + layout.key_passes + 1)
+    return 1 + binning + 1 + 2
+
+
+def byte_model(n, n_vis, K, P, tiles, sh_floats, layout):
+    """Algorithmic DRAM bytes per launch of each stage (kernel table)."""
+    b = {}
+    b["preprocess"] = n * (44 + 48) + n_vis * sh_floats * 4
+    depth_sort = (8 * n + layout.depth_passes * 16 * n) if layout.depth_passes else 0
+    key_bytes = 4 if layout.depth_passes else 8
+    b["bin_sort"] = depth_sort + n_vis * 16 + K * (key_bytes + 4) + layout.key_passes * 2 * K * (key_bytes + 4) \
+        + K * key_bytes + tiles * 8
+    b["render_forward"] = K * 4 + n_vis * 40 + P * 20 + tiles * 8
+    b["render_backward_tiles"] = K * 4 + n_vis * (40 + 36) + P * 20 + tiles * 8
+    b["render_backward_gaussians"] = n_vis * (44 + sh_floats * 4 + 36 + 16) + n * (4 + 236 + 8)
+    return b
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import synthetic as S
+    from paper_2308_04079_gb300 import Frame, GaussianTensors, _abi, make_config
+    from paper_2308_04079_gb300 import build as gbuild
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if gbuild.needs_build():
+        gbuild.build()
+    g, cam, bg, dimg = S.config3(k=1 + rank)
+    bg = tuple(float(x) for x in bg)
+    gt = GaussianTensors.from_numpy(g, device=dev).prepared()
+    d_dimg = torch.from_numpy(dimg).to(dev)
+    cfg = make_config(sort_mode=args.sort_mode)
+    fr = Frame(gt.n, cam, cfg, device=dev)
+    fr.ensure_binned(gt)
+    K = int(fr.last_status.num_instances)
+    fr = Frame(gt.n, cam, cfg, capacity=int(K * 1.15) + 4096, device=dev)
+    img, T, last = fr.outputs()
+    grads = fr.new_grads(gt)
+    stream = torch.cuda.current_stream()
+    stages = ["preprocess", "bin_sort", "render_forward", "render_backward_tiles", "render_backward_gaussians"]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fr.preprocess(gt)
+        if ev is not None:
+            ev[1].record(stream)
+        fr.bin_sort()
+        if ev is not None:
+            ev[2].record(stream)
+        fr.render_forward(bg, img, T, last)
+        if ev is not None:
+            ev[3].record(stream)
+        fr.render_backward_tiles(bg, d_dimg, T, last)
+        if ev is not None:
+            ev[4].record(stream)
+        fr.render_backward_gaussians(gt, grads)
+        if ev is not None:
+            ev[5].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    code, st = fr.status()
+    if code not in (_abi.GS_OK, _abi.GS_ERR_NUMERIC):
+        raise RuntimeError(f"warm-up step failed: {_abi.status_string(code)}")
+    n_vis, K = int(st.num_visible), int(st.num_instances)
+    sum_last = float(last.to(torch.float64).sum().item())
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(events[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    code, st = fr.status()
+    if code not in (_abi.GS_OK, _abi.GS_ERR_NUMERIC):
+        raise RuntimeError(f"timed step failed: {_abi.status_string(code)}")
+    total_ms = t0.elapsed_time(t1)
+    stage_ms = {s: float(np.mean([events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps)]))
+                for i, s in enumerate(stages)}
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers --------------------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, g, gt, fr, dimg, bg, img, T, last, grads, stream, world, dev)
+
+    hbm_peak, peak_kind = load_peaks()
+    P = cam.width * cam.height
+    sh_floats = 48
+    bytes_ = byte_model(gt.n, n_vis, K, P, fr.tiles, sh_floats, fr.layout)
+    kernels = {}
+    for s in stages:
+        kernels[s] = {"ms": round(stage_ms[s], 4), "alg_bytes": int(bytes_[s]),
+                      "gbs": round(bytes_[s] / (stage_ms[s] * 1e-3) / 1e9, 1)}
+    evals = sum_last
+    flops_fwd = evals * FLOPS_EVAL
+    flops_bwd = evals * (FLOPS_EVAL + FLOPS_BLEND_BWD)
+    kernels["render_forward"]["alg_tflops"] = round(flops_fwd / (stage_ms["render_forward"] * 1e-3) / 1e12, 2)
+    kernels["render_backward_tiles"]["alg_tflops"] = round(
+        flops_bwd / (stage_ms["render_backward_tiles"] * 1e-3) / 1e12, 2)
+    dom = max(stages, key=lambda s: stage_ms[s])
+    if dom in ("render_forward", "render_backward_tiles"):
+        fl = flops_fwd if dom == "render_forward" else flops_bwd
+        ach = fl / (stage_ms[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(ALU_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(ach / ALU_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "units": f"{int(evals)} evaluated (pixel, Gaussian) pairs"}
+    else:
+        ach = bytes_[dom] / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, cam, bg, dimg, args.cpu_tiles)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gaussians": gt.n, "width": cam.width, "height": cam.height,
+                   "sh_degree": 3, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "sort_mode": args.sort_mode,
+                   "visible": n_vis, "instances": K, "sum_last": int(sum_last),
+                   "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, g, gt, fr, dimg, bg, img, T, last, grads, stream, world, dev):
+    """Same metric through the public API with pinned host buffers: every step copies the
+    Gaussian parameters and dL/dimage in, runs the four stages, and copies the image and all
+    gradients out."""
+    import torch
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(getattr(g, k), dtype=np.float32)).pin_memory()
+               for k in ("means", "scales", "quats", "opacities", "sh")}
+    host_dimg = torch.from_numpy(dimg).pin_memory()
+    dev_dimg = torch.empty_like(host_dimg, device=dev)
+    host_out = {"image": torch.empty(img.shape, dtype=torch.float32).pin_memory()}
+    for k, v in grads.items():
+        host_out[k] = torch.empty(v.shape, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * 4 for v in host_in.values()) + host_dimg.numel() * 4
+    d2h = sum(v.numel() * 4 for v in host_out.values())
+    steps = max(3, min(args.steps, 10))
+
+    def step():
+        for k, v in host_in.items():
+            getattr(gt, k).copy_(v, non_blocking=True)
+        dev_dimg.copy_(host_dimg, non_blocking=True)
+        fr.preprocess(gt)
+        fr.bin_sort()
+        fr.render_forward(bg, img, T, last)
+        fr.render_backward(gt, bg, dev_dimg, T, last, grads)
+        host_out["image"].copy_(img, non_blocking=True)
+        for k, v in grads.items():
+            host_out[k].copy_(v, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
+    val = world * steps / (float(ms.item()) / 1e3)
+    return {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_frame_estimate(g, cam, bg, dimg, n_tiles, seed=0):
+    """Time the FP64 oracle on a bounded sample of one frame: preprocess of every Gaussian
+    plus forward and backward of ``n_tiles`` random 16x16 tiles (dL/dimage kept on those tiles
+    only), and the preprocess alone; extrapolate to the full frame's tile count."""
+    import oracle
+    TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
+    rng = np.random.default_rng(seed)
+    tiles = rng.choice(TX * TY, n_tiles, replace=False)
+    mask = np.zeros(TX * TY, np.uint8)
+    mask[tiles] = 1
+    empty = np.zeros(TX * TY, np.uint8)
+    pix = np.repeat(np.repeat(mask.reshape(TY, TX), 16, 0), 16, 1)[:cam.height, :cam.width].astype(bool)
+    dm = np.where(pix[None], dimg, 0.0)
+    t = time.perf_counter()
+    oracle.render_forward(g, cam, bg, tile_mask=empty)
+    t_pre = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.render_forward(g, cam, bg, tile_mask=mask)
+    oracle.render_backward(g, cam, dm, bg, tile_mask=mask)
+    t_s = time.perf_counter() - t
+    per_tile = max(t_s - 2 * t_pre, 0.0) / n_tiles
+    frame_s = 2 * t_pre + per_tile * TX * TY
+    return frame_s, t_s, t_pre
+
+
+def cpu_baseline(g, cam, bg, dimg, n_tiles):
+    import oracle
+    frame_s, t_s, t_pre = oracle_frame_estimate(g, cam, bg, dimg, n_tiles)
+    return {"value": round(1.0 / frame_s, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle: preprocess of all {g.n} Gaussians + forward+backward of {n_tiles} random "
+                      f"16x16 tiles of the 1080p frame ({t_s:.1f} s), extrapolated to 8160 tiles "
+                      f"(preprocess {t_pre:.1f} s counted twice, as forward and backward each run it)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    import synthetic as S
+    g, cam, bg, dimg = S.config3()
+    bg = tuple(float(x) for x in bg)
+    g64 = S.Gaussians(*(np.asarray(a, np.float64) for a in (g.means, g.scales, g.quats, g.opacities, g.sh)),
+                      g.sh_degree)
+    n_tiles = max(1, args.ref_tiles)
+    for w in range(args.warmup):
+        oracle_frame_estimate(g64, cam, bg, dimg, n_tiles, seed=1000 + w)
+    est = []
+    t = time.perf_counter()
+    for k in range(args.steps):
+        frame_s, _, _ = oracle_frame_estimate(g64, cam, bg, dimg, n_tiles, seed=k)
+        est.append(frame_s)
+    wall = time.perf_counter() - t
+    frame_s = float(np.mean(est))
+    value = 1.0 / frame_s
+    cores = oracle.num_threads()
+    sample = (f"each step: FP64 oracle preprocess of all {g.n} Gaussians + forward+backward of {n_tiles} random "
+              f"16x16 tiles, extrapolated to the 8160-tile 1080p frame")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(frame_s * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": g.n, "width": cam.width, "height": cam.height},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sort-mode", choices=["two_phase", "key64"], default="two_phase")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-tiles", type=int, default=128)
+    ap.add_argument("--ref-tiles", type=int, default=32)
+    args = ap.parse_args()
+    rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        # The CPU oracle runs on rank 0 only; other ranks exit without work.
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) differentiable tile rasterizer for 3D Gaussian
+ * Splatting (Kerbl et al., "3D Gaussian Splatting for Real-Time Radiance Field
+ * Rendering", SIGGRAPH 2023).
+ *
+ * The paper states the problem as Rasterize(w, h, M, S, C, A, V) (Algorithm 2): image size,
+ * Gaussian means M, covariances S = (scales s, rotations q) (Sec. 4), colours C as
+ * spherical-harmonic coefficients (Sec. 4, Sec. 7.1), opacities A and the view
+ * configuration V.  This header splits Algorithm 2 into four stages:
+ *
+ *   gs_preprocess      CullGaussian + ScreenspaceGaussians   (Sec. 4, Sec. 6, App. C)
+ *   gs_bin_sort        DuplicateWithKeys + SortByKeys + IdentifyTileRanges (Sec. 6, App. C)
+ *   gs_render_forward  per-tile BlendInOrder, eq. (front-to-back) with the App. C rules
+ *   gs_render_backward back-to-front traversal (Sec. 6) + chain rule of App. A
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented as "device" point to CUDA global memory on the current device.  The
+ *     library never allocates or frees memory and keeps no state between calls.  Every call
+ *     except gs_read_status is asynchronous on the given stream and issues only kernels and
+ *     cudaMemsetAsync (no host synchronisation, no host copies), so a sequence of calls can be
+ *     captured into a CUDA graph.
+ *   - Floating-point arrays are fp32, contiguous, row-major.  Images are planar [3, H, W].
+ *   - Inputs are activated values: scales s > 0 (exp already applied), opacities in (0, 1)
+ *     (sigmoid already applied); quaternions (q_r, q_i, q_j, q_k) need not be unit length
+ *     (they are normalised inside, Sec. 4).
+ *   - Synchronous errors (bad arguments, launch failures) are returned.  Conditions found on
+ *     the device (instance capacity exceeded, a bounded spin-wait that gave up, non-finite
+ *     inputs) are recorded in the workspace status block and read with gs_read_status.
+ */
+#ifndef GS_GB300_H
+#define GS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,   /* a null pointer, a non-positive size, a workspace too small   */
+    GS_ERR_CAPACITY = 2,      /* more (Gaussian, tile) instances than the workspace holds      */
+    GS_ERR_TIMEOUT = 3,       /* a bounded device spin-wait gave up (results are invalid)      */
+    GS_ERR_CUDA = 4,          /* a CUDA launch or memset failed                                */
+    GS_ERR_NUMERIC = 5        /* non-finite inputs were found and culled (results are valid)   */
+} gs_status;
+
+/* Pinhole camera (the paper's view configuration V, Algorithm 2; viewing transformation W
+ * of eq. volume-render).  x_cam = R x_world + t; camera x right, y down, z forward;
+ * pixel (px, py) is sampled at (px + 0.5, py + 0.5). */
+typedef struct gs_camera {
+    int width, height;        /* image size in pixels                                     */
+    float fx, fy, cx, cy;     /* focal lengths and principal point, pixels               */
+    float R[9];               /* world -> camera rotation, row-major                      */
+    float t[3];               /* world -> camera translation                              */
+    float near_z;             /* near plane: Gaussians with z <= near_z are rejected      */
+} gs_camera;
+
+/* Sort schedule of gs_bin_sort; both give bit-identical instance order and tile ranges. */
+enum {
+    GS_SORT_TWO_PHASE = 0,    /* depth sort of the N Gaussians, then a stable tile sort of the instances */
+    GS_SORT_KEY64 = 1         /* one LSD sort of the 64-bit (tile << 32 | depth) keys, as in App. C      */
+};
+
+/* Rasterizer constants.  gs_default_config() fills the paper's values. */
+typedef struct gs_raster_config {
+    int tile_w, tile_h;       /* tile size in pixels: 16 x 16 (Sec. 6); 8 x 8 and 16 x 8 also supported */
+    int batch_depth;          /* Gaussians staged in shared memory per batch; <= tile_w * tile_h   */
+    int sort_mode;            /* GS_SORT_TWO_PHASE or GS_SORT_KEY64                                */
+    float alpha_min;          /* 1/255: skip blending updates with smaller alpha (App. C)          */
+    float alpha_max;          /* 0.99: clamp alpha from above (App. C)                             */
+    float T_min;              /* 1e-4: stop before the accumulated opacity exceeds 0.9999 (App. C) */
+    float dilation;           /* 0.3 px^2 low-pass filter added to the diagonal of Sigma'          */
+    float guard;              /* 1.3: reject |x/z| > guard * tan(fov_x/2) or |y/z| > guard * tan(fov_y/2) */
+    float extent;             /* 3: screen radius = ceil(extent * sqrt(lambda_max(Sigma')))        */
+} gs_raster_config;
+
+/* Gaussian parameters (Sec. 4): device pointers, n rows each. */
+typedef struct gs_gaussians {
+    const float* means;       /* [n, 3] world-space means mu                                      */
+    const float* scales;      /* [n, 3] s > 0                                                     */
+    const float* quats;       /* [n, 4] (q_r, q_i, q_j, q_k), 16-byte aligned                      */
+    const float* opacities;   /* [n]    o in (0, 1)                                               */
+    const float* sh;          /* [n, sh_stride, 3] SH coefficients, bands 0..sh_degree used       */
+    int n;                    /* number of Gaussians, >= 0                                        */
+    int sh_degree;            /* 0..3                                                             */
+    int sh_stride;            /* coefficients per Gaussian in the buffer, >= (sh_degree + 1)^2    */
+} gs_gaussians;
+
+/* Gradient outputs of gs_render_backward: device pointers shaped like gs_gaussians. */
+typedef struct gs_gradients {
+    float* means;             /* [n, 3]                                                         */
+    float* scales;            /* [n, 3]                                                         */
+    float* quats;             /* [n, 4]                                                         */
+    float* opacities;         /* [n]                                                            */
+    float* sh;                /* [n, sh_stride, 3]; coefficients beyond the degree get 0         */
+    float* mean2d;            /* [n, 2] dL/d(u, v) in pixels (view-space position gradient used
+                                 by densification, Sec. 5.2); may be NULL                        */
+} gs_gradients;
+
+/* One frame: the Gaussian count, the camera, the constants and the caller-owned device
+ * workspace that holds every intermediate of Algorithm 2 (screen-space Gaussians, instance
+ * keys and values, tile ranges, sort state, gradient accumulators, status block).  The same
+ * frame (same workspace contents) must be passed to all four stages of one render, and the
+ * workspace must stay untouched between gs_render_forward and gs_render_backward. */
+typedef struct gs_frame {
+    int n;                    /* number of Gaussians                                           */
+    gs_camera cam;
+    gs_raster_config cfg;
+    uint64_t capacity;        /* instance capacity: max (Gaussian, tile) pairs, <= 2^30 - 1      */
+    void* ws;                 /* device workspace, 256-byte aligned                            */
+    size_t ws_bytes;          /* >= gs_workspace_size(n, width, height, capacity, &cfg)          */
+} gs_frame;
+
+/* Offsets (bytes from the workspace start) of the named sub-buffers; for inspection and
+ * tests.  Screen-space Gaussians (Algorithm 2 M', S'):
+ *   xy            float4[n]  screen mean as a double-float (u_hi, v_hi, u_lo, v_lo), u = u_hi + u_lo
+ *   depth         float[n]   camera-space z
+ *   conic_opacity float4[n]  (l11, l21, l22, o): lower Cholesky factor L of the conic
+ *                            Q = Sigma'^-1 = L L^T (power = -|L^T d|^2 / 2) and the opacity
+ *   rgb           float4[n]  (r, g, b, bits of the channels clamped at 0)
+ *   radius        int32[n]   screen radius in pixels, 0 = culled
+ * Instances: sorted Gaussian indices uint32[capacity] at vals_sorted; tile ranges
+ * uint32[2 * tiles] ([start, end) into vals_sorted, [0, 0) for empty tiles); keys_sorted: the
+ * sorted keys as uint64[capacity] (KEY64 mode) or the sorted tile ids as uint32[capacity]
+ * (TWO_PHASE mode). */
+typedef struct gs_layout {
+    uint64_t xy, depth, conic_opacity, rgb, radius;
+    uint64_t vals_sorted, keys_sorted, ranges;
+    uint64_t grad2d;          /* float[n, 12] per-Gaussian screen-space gradient accumulators */
+    uint64_t status;          /* gs_device_status                                           */
+    uint64_t total_bytes;
+    int tiles_x, tiles_y;
+    int key_passes;           /* radix passes over the instance keys                         */
+    int depth_passes;         /* radix passes over the Gaussian depths (TWO_PHASE), else 0    */
+} gs_layout;
+
+/* Device-side status block (in the workspace). */
+typedef struct gs_device_status {
+    uint32_t flags;           /* bit 0: capacity exceeded, bit 1: spin-wait timeout            */
+    uint32_t num_instances;   /* (Gaussian, tile) pairs (may exceed capacity, see flags)       */
+    uint32_t num_visible;     /* Gaussians that survived culling                               */
+    uint32_t num_nonfinite;   /* Gaussians culled because an input was NaN or Inf              */
+    uint32_t reserved[4];
+} gs_device_status;
+
+/* Fill cfg with the paper's constants: 16x16 tiles, batch 256, alpha in [1/255, 0.99],
+ * T_min 1e-4, dilation 0.3, guard 1.3, extent 3, GS_SORT_TWO_PHASE. */
+void gs_default_config(gs_raster_config* cfg);
+
+/* Workspace bytes for a frame; 0 if the arguments are invalid. */
+size_t gs_workspace_size(int n, int width, int height, uint64_t capacity, const gs_raster_config* cfg);
+
+/* Sub-buffer offsets of the workspace (see gs_layout). */
+gs_status gs_workspace_layout(int n, int width, int height, uint64_t capacity, const gs_raster_config* cfg,
+                              gs_layout* out);
+
+/* Algorithm 2, CullGaussian + ScreenspaceGaussians, one thread per Gaussian:
+ * camera-space mean, near-plane / guard-band rejection (Sec. 6), Sigma = R S S^T R^T with
+ * R from the normalised quaternion (Sec. 4, eq. quat), Sigma' = J W Sigma W^T J^T
+ * (eq. volume-render) plus the 0.3 px^2 dilation, conic = Sigma'^-1, radius
+ * ceil(3 sqrt(lambda_max)), screen mean, tile rectangle, SH colour max(0, sum_k c_k Y_k(d)).
+ * Writes the screen-space Gaussians into the workspace and resets the status block.
+ * Errors: GS_ERR_INVALID_ARG for a bad frame or Gaussian description, GS_ERR_CUDA. */
+gs_status gs_preprocess(const gs_frame* frame, const gs_gaussians* g, cudaStream_t stream);
+
+/* Algorithm 2, DuplicateWithKeys + SortByKeys + IdentifyTileRanges (App. C): one instance per
+ * (visible Gaussian, overlapped tile) with key (tile id << 32) | fp32 bits of depth, ordered
+ * as one stable sort of those keys emitted in (Gaussian index, row-major tile) order, and the
+ * [start, end) range of every tile.  The instance count stays on the device (status block);
+ * if it exceeds frame->capacity, no instance is written past the capacity and the status
+ * flag GS_ERR_CAPACITY is raised (the caller grows the workspace and re-runs).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_bin_sort(const gs_frame* frame, cudaStream_t stream);
+
+/* Algorithm 2, BlendInOrder, one thread block per tile: every pixel blends its tile's list
+ * front to back, C = sum_i c_i a_i prod_{j<i} (1 - a_j), a = min(0.99, o G), skipping a < 1/255
+ * and stopping before T (1 - a) < 1e-4 (App. C).  Outputs (device, caller-owned):
+ *   out_rgb  float[3, H, W]   C + T_final * bg
+ *   out_T    float[H, W]      final transmittance T_final
+ *   out_last uint32[H, W]     1 + position (in the tile list) of the last blended Gaussian, 0 if none
+ * bg is a host array of 3 floats.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_render_forward(const gs_frame* frame, const float bg[3], float* out_rgb, float* out_T,
+                            uint32_t* out_last, cudaStream_t stream);
+
+/* Backward pass (Sec. 6 and App. A): every tile is traversed back to front from its last
+ * contributor; each pixel recovers T_i = T_{i+1} / (1 - a_i) from the stored T_final and
+ * accumulates dL/d(mean2D, conic, opacity, colour) of every Gaussian it blended (reduced per
+ * warp before global atomics); then, per Gaussian, the chain rule through the conic, Sigma',
+ * Sigma = M M^T, M = R S, the quaternion normalisation, the projection Jacobian, the screen
+ * mean and the SH colour gives the gradients of every input.  dL_drgb float[3, H, W], T and
+ * last are the forward outputs.  accumulate != 0 adds into the gradient arrays (several views
+ * of one scene); accumulate == 0 overwrites them.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_render_backward(const gs_frame* frame, const gs_gaussians* g, const float bg[3],
+                             const float* dL_drgb, const float* T, const uint32_t* last,
+                             const gs_gradients* grads, int accumulate, cudaStream_t stream);
+
+/* The two halves of gs_render_backward, callable separately (gs_render_backward is exactly
+ * gs_render_backward_tiles followed by gs_render_backward_gaussians):
+ *   gs_render_backward_tiles      zeroes the workspace's per-Gaussian screen-space gradient
+ *                                 accumulators, then runs the back-to-front tile traversal (Sec. 6)
+ *                                 that fills them: dL/d(mean2D, conic, opacity, colour).
+ *   gs_render_backward_gaussians  per Gaussian, the chain rule of App. A from those accumulators to
+ *                                 the input gradients (see gs_render_backward for the arguments).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_render_backward_tiles(const gs_frame* frame, const float bg[3], const float* dL_drgb, const float* T,
+                                   const uint32_t* last, cudaStream_t stream);
+gs_status gs_render_backward_gaussians(const gs_frame* frame, const gs_gaussians* g, const gs_gradients* grads,
+                                       int accumulate, cudaStream_t stream);
+
+/* Copy the workspace status block to the host (synchronises the stream) and return the first
+ * device-side error as a status: GS_ERR_TIMEOUT, GS_ERR_CAPACITY, GS_ERR_NUMERIC or GS_OK. */
+gs_status gs_read_status(const gs_frame* frame, gs_device_status* out, cudaStream_t stream);
+
+/* Human-readable name of a status code (static string). */
+const char* gs_status_string(gs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_GB300_H */

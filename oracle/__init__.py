@@ -37,6 +37,7 @@ AMB_CLAMP = 16
 # per-pixel ambiguity bits
 PIX_DECISION = 1
 PIX_CLAMP = 2
+PIX_ANY = 4
 
 DEFAULT_CFG = dict(
     tile_w=16, tile_h=16,          # Sec. 6 / App. C: 16x16 tiles
@@ -48,7 +49,10 @@ DEFAULT_CFG = dict(
     extent=3.0,                    # 3-sigma screen extent (Sec. 6, 99% interval)
     radius_max=1 << 24,            # radius clamp (pixels)
     eps_geom=2e-6,                 # ambiguity margin, geometric decisions (relative)
-    eps_alpha=1e-4,                # ambiguity margin, alpha / transmittance decisions (relative)
+    eps_alpha=3e-5,                # ambiguity margin, alpha skip / clamp decisions (relative)
+    eps_T=1e-3,                    # ambiguity margin, transmittance stop decision (relative)
+    T_impact=1e-4 / (2.0 / 255.0), # skip flips behind less light cannot move a pixel by 1e-4
+    T_grad=1e-3,                   # flips behind less light are negligible for gradients
 )
 
 _lib = None
@@ -115,7 +119,7 @@ def cfg_array(**overrides) -> np.ndarray:
         c[k] = v
     return np.array([c["tile_w"], c["tile_h"], c["alpha_min"], c["alpha_max"], c["T_min"],
                      c["dilation"], c["guard"], c["extent"], c["radius_max"], c["eps_geom"],
-                     c["eps_alpha"]], dtype=np.float64)
+                     c["eps_alpha"], c["eps_T"], c["T_impact"], c["T_grad"]], dtype=np.float64)
 
 
 def _gauss_args(g):

@@ -62,8 +62,12 @@ typedef struct {
     double guard;       /* guard band factor on the view-frustum tangents (Sec. 6) */
     double extent;      /* 3 (sigma multiple of the screen extent, Sec. 6) */
     int radius_max;     /* radius clamp in pixels */
-    double eps_geom;    /* relative margin for geometric decisions (cull, floor, ceil, depth ties) */
-    double eps_alpha;   /* relative margin for alpha / transmittance decisions */
+    double eps_geom;    /* relative margin for geometric decisions (cull, floor, ceil) */
+    double eps_alpha;   /* relative margin for the alpha skip / clamp decisions */
+    double eps_T;       /* relative margin for the transmittance stop decision */
+    double T_impact;    /* skip flips in front of which less light than this remains cannot move
+                           the pixel by the image tolerance: alpha_min * T * 2 < tolerance */
+    double T_grad;      /* a flipped decision behind less light than this is negligible for gradients */
 } ocfg;
 
 static void read_cam(const double* c, ocam* o) {
@@ -79,18 +83,24 @@ static void read_cfg(const double* c, ocfg* o) {
     o->alpha_min = c[2]; o->alpha_max = c[3]; o->T_min = c[4];
     o->dilation = c[5]; o->guard = c[6]; o->extent = c[7];
     o->radius_max = (int)c[8]; o->eps_geom = c[9]; o->eps_alpha = c[10];
+    o->eps_T = c[11]; o->T_impact = c[12]; o->T_grad = c[13];
 }
 
 /* Ambiguity bits (per Gaussian). */
-#define AMB_CULL   1u   /* a cull decision lies within eps_geom of its threshold            */
-#define AMB_RECT   2u   /* floor(u), floor(v) or the radius ceiling may round the other way */
-#define AMB_RGB    4u   /* an SH colour channel lies within eps_alpha of the 0 clamp        */
-#define AMB_PIXEL  8u   /* relevant to at least one ambiguous pixel                          */
-#define AMB_CLAMP 16u   /* o*G within eps_alpha of the 0.99 clamp at some pixel (grad only)  */
+#define AMB_CULL   1u   /* a cull decision lies within eps_geom of its threshold                */
+#define AMB_RECT   2u   /* floor(u), floor(v) or the radius ceiling may round the other way     */
+#define AMB_RGB    4u   /* an SH colour channel lies within eps_geom (relative) of the 0 clamp  */
+#define AMB_PIXEL  8u   /* its own skip / order / membership decision is near a threshold at a  */
+                        /* pixel with transmittance >= T_grad                                   */
+#define AMB_CLAMP 16u   /* o*G within eps_alpha of the 0.99 clamp at a pixel with T >= T_grad   */
 
 /* Ambiguity bits (per pixel). */
-#define PIX_DECISION 1u /* skip / stop / order / tile-membership decision near threshold */
-#define PIX_CLAMP    2u /* clamp decision near threshold: value is continuous, gradient is not */
+#define PIX_DECISION 1u /* a decision near its threshold that can move the pixel by more than   */
+                        /* the tolerance: skip (with T >= T_impact), stop, depth order, tile    */
+                        /* membership                                                           */
+#define PIX_CLAMP    2u /* clamp decision near threshold: value is continuous, gradient is not  */
+#define PIX_ANY      4u /* any skip / stop / order / membership decision near its threshold     */
+                        /* (the last-contributor index may differ)                              */
 
 /* ------------------------------------------------------------------------- */
 /* Small linear algebra.                                                       */
@@ -533,85 +543,93 @@ static double eval_power(const ogauss* g, double pxc, double pyc, double* dx, do
     return -0.5 * (g->conic[0] * (*dx) * (*dx) + g->conic[2] * (*dy) * (*dy)) - g->conic[1] * (*dx) * (*dy);
 }
 
+static void mark(unsigned* gamb, int32_t i, unsigned bit) {
+    if (!gamb) return;
+#pragma omp atomic
+    gamb[i] |= bit;
+}
+
 /*
  * Forward walk of one pixel over its tile's list (eq. front-to-back, App. C rules).
- * Returns the number of contributors written to rec (rec may be NULL).
+ * Returns the number of contributors written to rec (rec may be NULL).  Sets the pixel's
+ * ambiguity flags and, if gamb is given, marks the Gaussians whose own decision is near a
+ * threshold (see the AMB_* / PIX_* bits).
  */
 static int pixel_forward(const oscene* S, int t, int px, int py, const double* bg, double* out_rgb, double* out_T,
-                         int* out_last, unsigned* out_flags, contrib_t* rec, unsigned* gflags_touch) {
+                         int* out_last, unsigned* out_flags, contrib_t* rec, unsigned* gamb) {
     const ocfg* cfg = &S->cfg;
     double pxc = px + 0.5, pyc = py + 0.5;
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     int last = 0, nrec = 0;
     unsigned flags = 0;
     int64_t a = S->tile_start[t], b = S->tile_start[t + 1];
-    double prev_key_z = -1.0;
-    int prev_idx = -1;
-    int stopped = 0;
+    uint32_t prev_key = 0;
+    int32_t prev_idx = -1;
+    const int tx = t % S->TX, ty = t / S->TX;
     for (int64_t k = a; k < b; ++k) {
-        const ogauss* g = &S->g[S->tile_list[k]];
+        const int32_t gi = S->tile_list[k];
+        const ogauss* g = &S->g[gi];
         double dx, dy;
         double power = eval_power(g, pxc, pyc, &dx, &dy);
         double G = exp(power);
-        double oG = S->opac[S->tile_list[k]] * G;
-        int relevant = oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha);
-        if (!stopped && relevant) {
-            /* depth ties: an fp32 implementation orders equal fp32 depths by index */
-            if (prev_idx >= 0 && fabs(g->tcam[2] - prev_key_z) <= cfg->eps_geom * g->tcam[2]) flags |= PIX_DECISION;
-            prev_key_z = g->tcam[2]; prev_idx = S->tile_list[k];
-            if (g->amb & (AMB_CULL | AMB_RECT)) {
-                if (!in_rect(g->rect_in, t % S->TX, t / S->TX)) flags |= PIX_DECISION;
+        double oG = S->opac[gi] * G;
+        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha)) {
+            /* tile membership that an fp32 binning may decide differently */
+            if ((g->amb & (AMB_CULL | AMB_RECT)) && !in_rect(g->rect_in, tx, ty)) {
+                flags |= PIX_ANY;
+                if (T >= cfg->T_impact) flags |= PIX_DECISION;
+                if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);
             }
+            /* equal or adjacent fp32 depth keys: the two may swap */
+            uint32_t key = depth_key(g->tcam[2]);
+            if (prev_idx >= 0 && key - prev_key <= 1u) {
+                flags |= PIX_ANY;
+                if (T >= cfg->T_impact) flags |= PIX_DECISION;
+                if (T >= cfg->T_grad) { mark(gamb, gi, AMB_PIXEL); mark(gamb, prev_idx, AMB_PIXEL); }
+            }
+            prev_key = key;
+            prev_idx = gi;
         }
-        if (stopped) continue;
-        if (near_threshold(oG, cfg->alpha_min, cfg->eps_alpha)) flags |= PIX_DECISION;
-        if (near_threshold(oG, cfg->alpha_max, cfg->eps_alpha)) flags |= PIX_CLAMP;
+        if (near_threshold(oG, cfg->alpha_min, cfg->eps_alpha)) {
+            flags |= PIX_ANY;
+            if (T >= cfg->T_impact) flags |= PIX_DECISION;
+            if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);
+        }
+        if (near_threshold(oG, cfg->alpha_max, cfg->eps_alpha)) {
+            flags |= PIX_CLAMP;
+            if (T >= cfg->T_grad) mark(gamb, gi, AMB_CLAMP);
+        }
         int clamped = oG > cfg->alpha_max;
         double alpha = clamped ? cfg->alpha_max : oG;
         if (alpha < cfg->alpha_min) continue;                   /* skip (App. C) */
         double test_T = T * (1.0 - alpha);
-        if (near_threshold(test_T, cfg->T_min, cfg->eps_alpha)) flags |= PIX_DECISION;
-        if (test_T < cfg->T_min) { stopped = 1; continue; }      /* stop before exceeding 0.9999 */
+        if (near_threshold(test_T, cfg->T_min, cfg->eps_T)) flags |= PIX_DECISION | PIX_ANY;
+        if (test_T < cfg->T_min) break;                         /* stop before exceeding 0.9999 */
         for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * alpha * T;
         if (rec) {
-            rec[nrec].idx = S->tile_list[k]; rec[nrec].alpha = alpha; rec[nrec].G = G; rec[nrec].T = T;
+            rec[nrec].idx = gi; rec[nrec].alpha = alpha; rec[nrec].G = G; rec[nrec].T = T;
             rec[nrec].dx = dx; rec[nrec].dy = dy; rec[nrec].clamped = clamped;
         }
         nrec++;
         T = test_T;
         last = (int)(k - a) + 1;
     }
-    /* Uncertain tile membership: a Gaussian that an fp32 binning may add to this tile. */
+    /* Gaussians outside this tile's list that an fp32 binning may add to it. */
     for (int64_t k = S->shadow_start[t]; k < S->shadow_start[t + 1]; ++k) {
-        const ogauss* g = &S->g[S->shadow_list[k]];
+        const int32_t gi = S->shadow_list[k];
+        const ogauss* g = &S->g[gi];
         double dx, dy;
-        double oG = S->opac[S->shadow_list[k]] * exp(eval_power(g, pxc, pyc, &dx, &dy));
-        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha)) flags |= PIX_DECISION;
+        double oG = S->opac[gi] * exp(eval_power(g, pxc, pyc, &dx, &dy));
+        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha)) {
+            flags |= PIX_DECISION | PIX_ANY;
+            mark(gamb, gi, AMB_PIXEL);
+        }
     }
     for (int ch = 0; ch < 3; ++ch) out_rgb[ch] = C[ch] + T * bg[ch];
     *out_T = T;
     *out_last = last;
     *out_flags = flags;
-    (void)gflags_touch;
     return nrec;
-}
-
-/* Mark every Gaussian relevant at an ambiguous pixel (its gradient is uncertain). */
-static void mark_pixel_gaussians(const oscene* S, int t, int px, int py, unsigned* gamb, unsigned bit) {
-    double pxc = px + 0.5, pyc = py + 0.5;
-    for (int64_t k = S->tile_start[t]; k < S->tile_start[t + 1]; ++k) {
-        const ogauss* g = &S->g[S->tile_list[k]];
-        double dx, dy;
-        double oG = S->opac[S->tile_list[k]] * exp(eval_power(g, pxc, pyc, &dx, &dy));
-        if (oG >= S->cfg.alpha_min * (1.0 - S->cfg.eps_alpha)) {
-#pragma omp atomic
-            gamb[S->tile_list[k]] |= bit;
-        }
-    }
-    for (int64_t k = S->shadow_start[t]; k < S->shadow_start[t + 1]; ++k) {
-#pragma omp atomic
-        gamb[S->shadow_list[k]] |= bit;
-    }
 }
 
 static void scene_init(oscene* S, long n, const double* means, const double* scales, const double* quats,
@@ -671,13 +689,12 @@ void orc_render_forward(long n, const double* means, const double* scales, const
                 int px = tx * S.cfg.tile_w + lx, py = ty * S.cfg.tile_h + ly;
                 if (px >= W || py >= H) continue;
                 double rgb[3], Tf; int last; unsigned flags;
-                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &flags, NULL, NULL);
+                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &flags, NULL, out_gauss_amb);
                 size_t p = (size_t)py * W + px;
                 for (int ch = 0; ch < 3; ++ch) out_img[ch * P + p] = rgb[ch];
                 out_T[p] = Tf;
                 out_last[p] = last;
                 if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
-                if (out_gauss_amb && flags) mark_pixel_gaussians(&S, t, px, py, out_gauss_amb, (flags & PIX_DECISION) ? AMB_PIXEL : AMB_CLAMP);
             }
     }
     scene_free(&S);
@@ -727,9 +744,8 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                     if (px >= W || py >= H) continue;
                     size_t p = (size_t)py * W + px;
                     double rgb[3], Tf; int last; unsigned flags;
-                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &flags, rec, NULL);
+                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &flags, rec, out_gauss_amb);
                     if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
-                    if (out_gauss_amb && flags) mark_pixel_gaussians(&S, t, px, py, out_gauss_amb, (flags & PIX_DECISION) ? AMB_PIXEL : AMB_CLAMP);
                     double dC[3] = {dL_dimg[p], dL_dimg[P + p], dL_dimg[2 * P + p]};
                     /* R = colour accumulated behind the current Gaussian, normalised by the
                        transmittance in front of it; starts with the background. */

@@ -1,0 +1,186 @@
+"""ctypes binding of the C ABI in include/gs.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and forwards its arguments
+unchanged; the work happens in the sm_103a kernels of libgs_gb300.so.  Loading fails loudly
+when the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_float, c_void_p, c_uint32, c_uint64, c_size_t = (ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t)
+
+GS_OK = 0
+GS_ERR_INVALID_ARG = 1
+GS_ERR_CAPACITY = 2
+GS_ERR_TIMEOUT = 3
+GS_ERR_CUDA = 4
+GS_ERR_NUMERIC = 5
+
+GS_SORT_TWO_PHASE = 0
+GS_SORT_KEY64 = 1
+
+FLAG_CAPACITY = 1
+FLAG_TIMEOUT = 2
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("width", c_int), ("height", c_int), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float), ("R", c_float * 9), ("t", c_float * 3), ("near_z", c_float)]
+
+
+class gs_raster_config(ctypes.Structure):
+    _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("batch_depth", c_int), ("sort_mode", c_int),
+                ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float), ("dilation", c_float),
+                ("guard", c_float), ("extent", c_float)]
+
+
+class gs_gaussians(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p), ("opacities", c_void_p),
+                ("sh", c_void_p), ("n", c_int), ("sh_degree", c_int), ("sh_stride", c_int)]
+
+
+class gs_gradients(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p), ("opacities", c_void_p),
+                ("sh", c_void_p), ("mean2d", c_void_p)]
+
+
+class gs_frame(ctypes.Structure):
+    _fields_ = [("n", c_int), ("cam", gs_camera), ("cfg", gs_raster_config), ("capacity", c_uint64),
+                ("ws", c_void_p), ("ws_bytes", c_size_t)]
+
+
+class gs_layout(ctypes.Structure):
+    _fields_ = [("xy", c_uint64), ("depth", c_uint64), ("conic_opacity", c_uint64), ("rgb", c_uint64),
+                ("radius", c_uint64), ("vals_sorted", c_uint64), ("keys_sorted", c_uint64), ("ranges", c_uint64),
+                ("grad2d", c_uint64), ("status", c_uint64), ("total_bytes", c_uint64), ("tiles_x", c_int),
+                ("tiles_y", c_int), ("key_passes", c_int), ("depth_passes", c_int)]
+
+
+class gs_device_status(ctypes.Structure):
+    _fields_ = [("flags", c_uint32), ("num_instances", c_uint32), ("num_visible", c_uint32),
+                ("num_nonfinite", c_uint32), ("reserved", c_uint32 * 4)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/gs.h
+SIGNATURES = [
+    ("gs_default_config", None, [ctypes.POINTER(gs_raster_config)]),
+    ("gs_workspace_size", c_size_t, [c_int, c_int, c_int, c_uint64, ctypes.POINTER(gs_raster_config)]),
+    ("gs_workspace_layout", c_int, [c_int, c_int, c_int, c_uint64, ctypes.POINTER(gs_raster_config),
+                                    ctypes.POINTER(gs_layout)]),
+    ("gs_preprocess", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians), c_void_p]),
+    ("gs_bin_sort", c_int, [ctypes.POINTER(gs_frame), c_void_p]),
+    ("gs_render_forward", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(c_float * 3), c_void_p, c_void_p,
+                                  c_void_p, c_void_p]),
+    ("gs_render_backward", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians),
+                                   ctypes.POINTER(c_float * 3), c_void_p, c_void_p, c_void_p,
+                                   ctypes.POINTER(gs_gradients), c_int, c_void_p]),
+    ("gs_render_backward_tiles", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(c_float * 3), c_void_p, c_void_p,
+                                         c_void_p, c_void_p]),
+    ("gs_render_backward_gaussians", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians),
+                                             ctypes.POINTER(gs_gradients), c_int, c_void_p]),
+    ("gs_read_status", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_device_status), c_void_p]),
+    ("gs_status_string", ctypes.c_char_p, [c_int]),
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libgs_gb300.so.  Raises if it is missing (build it with __graft_entry__.build()
+    or ``python -m paper_2308_04079_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing and _build.needs_build():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA rasterizer library not built: {path} is missing")
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class GSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (code {code})")
+
+
+def status_string(code: int) -> str:
+    return load().gs_status_string(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != GS_OK:
+        raise GSError(code, where)
+
+
+def gs_default_config() -> gs_raster_config:
+    cfg = gs_raster_config()
+    load().gs_default_config(ctypes.byref(cfg))
+    return cfg
+
+
+def gs_workspace_size(n: int, width: int, height: int, capacity: int, cfg: gs_raster_config) -> int:
+    return int(load().gs_workspace_size(n, width, height, capacity, ctypes.byref(cfg)))
+
+
+def gs_workspace_layout(n: int, width: int, height: int, capacity: int, cfg: gs_raster_config) -> gs_layout:
+    out = gs_layout()
+    _check(load().gs_workspace_layout(n, width, height, capacity, ctypes.byref(cfg), ctypes.byref(out)),
+           "gs_workspace_layout")
+    return out
+
+
+def gs_preprocess(frame: gs_frame, g: gs_gaussians, stream: int) -> None:
+    _check(load().gs_preprocess(ctypes.byref(frame), ctypes.byref(g), stream), "gs_preprocess")
+
+
+def gs_bin_sort(frame: gs_frame, stream: int) -> None:
+    _check(load().gs_bin_sort(ctypes.byref(frame), stream), "gs_bin_sort")
+
+
+def gs_render_forward(frame: gs_frame, bg, out_rgb: int, out_T: int, out_last: int, stream: int) -> None:
+    b = (c_float * 3)(*[float(x) for x in bg])
+    _check(load().gs_render_forward(ctypes.byref(frame), ctypes.byref(b), out_rgb, out_T, out_last, stream),
+           "gs_render_forward")
+
+
+def gs_render_backward(frame: gs_frame, g: gs_gaussians, bg, dL_drgb: int, T: int, last: int,
+                       grads: gs_gradients, accumulate: bool, stream: int) -> None:
+    b = (c_float * 3)(*[float(x) for x in bg])
+    _check(load().gs_render_backward(ctypes.byref(frame), ctypes.byref(g), ctypes.byref(b), dL_drgb, T, last,
+                                     ctypes.byref(grads), int(bool(accumulate)), stream), "gs_render_backward")
+
+
+def gs_render_backward_tiles(frame: gs_frame, bg, dL_drgb: int, T: int, last: int, stream: int) -> None:
+    b = (c_float * 3)(*[float(x) for x in bg])
+    _check(load().gs_render_backward_tiles(ctypes.byref(frame), ctypes.byref(b), dL_drgb, T, last, stream),
+           "gs_render_backward_tiles")
+
+
+def gs_render_backward_gaussians(frame: gs_frame, g: gs_gaussians, grads: gs_gradients, accumulate: bool,
+                                 stream: int) -> None:
+    _check(load().gs_render_backward_gaussians(ctypes.byref(frame), ctypes.byref(g), ctypes.byref(grads),
+                                               int(bool(accumulate)), stream), "gs_render_backward_gaussians")
+
+
+def gs_read_status(frame: gs_frame, stream: int):
+    st = gs_device_status()
+    code = load().gs_read_status(ctypes.byref(frame), ctypes.byref(st), stream)
+    if code in (GS_ERR_INVALID_ARG, GS_ERR_CUDA):
+        raise GSError(code, "gs_read_status")
+    return code, st

@@ -1,0 +1,184 @@
+// gs_kernels.h -- kernel argument blocks and launch constants shared by the kernel files and
+// the host-side C ABI implementation (gs_api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+#include "gs_device.cuh"
+
+namespace gs {
+
+// Radix sort: 256 threads, 16 keys per thread, 8-bit digits.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxKeyPasses = 8;
+constexpr int kDepthPasses = 4;
+
+// Scan + duplicate: 256 threads, 4 Gaussians per thread.
+constexpr int kDupThreads = 256;
+constexpr int kDupChunk = 1024;
+
+// Render: one block per tile, at most 256 pixels (threads) per tile.
+constexpr int kMaxTilePixels = 256;
+
+// Control block at the start of the workspace.
+struct Control {
+    gs_device_status status;
+    uint32_t counters[32];                      // chunk-claim counters: [0] scan, [1..4] depth, [8..15] keys;
+                                                // [31] visible Gaussians counted by the binning stage
+    uint32_t hist_depth[kDepthPasses][256];     // digit histograms, depth sort
+    uint32_t hist_keys[kMaxKeyPasses][256];     // digit histograms, instance sort
+};
+
+struct PreprocessArgs {
+    int n;
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacities;
+    const float* sh;
+    int sh_degree, sh_stride;
+    CamK cam;
+    CfgK cfg;
+    float4* xy;               // (u_hi, v_hi, u_lo, v_lo): screen mean as a double-float
+    float* depth;
+    float4* conic_opacity;
+    float4* rgb;
+    int* radius;
+    gs_device_status* status;
+};
+
+struct PreprocessBwdArgs {
+    int n;
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacities;
+    const float* sh;
+    int sh_degree, sh_stride;
+    CamK cam;
+    CfgK cfg;
+    const float* grad2d;     // [n, 12]
+    const float4* rgb;
+    const int* radius;
+    float* g_means;
+    float* g_scales;
+    float* g_quats;
+    float* g_opacities;
+    float* g_sh;
+    float* g_mean2d;
+    int accumulate;
+};
+
+struct DepthHistArgs {
+    int n;
+    const float* depth;
+    const int* radius;
+    uint32_t* hist;            // [4][256]
+    uint32_t* lookback_first;  // rows for the first depth pass
+    uint32_t* num_visible;     // count of radius > 0 (zeroed)
+};
+
+template <typename KeyT>
+struct SortPassArgs {
+    const KeyT* keys_in;       // null: keys from (depth_src, radius_src), values = index
+    const uint32_t* vals_in;
+    const float* depth_src;
+    const int* radius_src;
+    KeyT* keys_out;
+    uint32_t* vals_out;
+    const uint32_t* count_dev; // null: count_host
+    uint32_t count_host;       // element count bound (capacity)
+    int shift;
+    const uint32_t* hist;      // [256] digit counts of this pass
+    uint32_t* lookback;        // [chunks][256], zeroed
+    uint32_t* lookback_next;   // rows to zero for the next pass, or null
+    uint32_t* chunk_counter;   // zeroed
+    gs_device_status* status;
+};
+
+struct DupArgs {
+    const uint32_t* order;     // depth-sorted Gaussian ids (TWO_PHASE) or null (identity)
+    const uint32_t* count_dev; // number of entries of `order` to use, or null (n)
+    int n;
+    const float4* xy;
+    const int* radius;
+    const float* depth;
+    CamK cam;
+    void* keys_out;
+    uint32_t* vals_out;
+    unsigned long long capacity;
+    uint32_t* hist;            // [passes][256]
+    int passes;
+    unsigned long long* lookback;  // [chunks], zeroed
+    uint32_t* chunk_counter;
+    gs_device_status* status;
+};
+
+struct SortPrepareArgs {
+    uint32_t* lookback;
+    const gs_device_status* status;
+    unsigned long long capacity;
+};
+
+template <typename KeyT>
+struct RangesArgs {
+    const KeyT* keys;
+    uint32_t* ranges;
+    uint32_t tiles;
+    const gs_device_status* status;
+    unsigned long long capacity;
+};
+
+struct RenderFwdArgs {
+    int n;
+    CamK cam;
+    CfgK cfg;
+    float bg[3];
+    int batch;
+    const uint32_t* ranges;
+    const uint32_t* vals;
+    const float4* xy;
+    const float4* conic_opacity;
+    const float4* rgb;
+    float* out_rgb;
+    float* out_T;
+    uint32_t* out_last;
+};
+
+struct RenderBwdArgs {
+    int n;
+    CamK cam;
+    CfgK cfg;
+    float bg[3];
+    int batch;
+    const uint32_t* ranges;
+    const uint32_t* vals;
+    const float4* xy;
+    const float4* conic_opacity;
+    const float4* rgb;
+    const float* dL_drgb;
+    const float* T_final;
+    const uint32_t* last;
+    float* grad2d;             // [n, 12] accumulators, zeroed
+};
+
+// Host-side launchers (defined next to their kernels).  Each returns the launch status.
+// Persistent kernels size their grid as SM count x resident blocks per SM.
+int persistent_grid(const void* kernel, int threads);
+cudaError_t launch_preprocess(const PreprocessArgs& a, cudaStream_t s);
+cudaError_t launch_preprocess_backward(const PreprocessBwdArgs& a, cudaStream_t s);
+cudaError_t launch_depth_hist(const DepthHistArgs& a, cudaStream_t s);
+cudaError_t launch_onesweep(const SortPassArgs<uint32_t>& a, int max_chunks, cudaStream_t s);
+cudaError_t launch_onesweep(const SortPassArgs<unsigned long long>& a, int max_chunks, cudaStream_t s);
+cudaError_t launch_scan_duplicate(const DupArgs& a, bool key64, cudaStream_t s);
+cudaError_t launch_sort_prepare(const SortPrepareArgs& a, cudaStream_t s);
+cudaError_t launch_ranges(const RangesArgs<uint32_t>& a, cudaStream_t s);
+cudaError_t launch_ranges(const RangesArgs<unsigned long long>& a, cudaStream_t s);
+cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, int threads, cudaStream_t s);
+cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, int threads, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,334 @@
+// preprocess.cu -- per-Gaussian forward (Algorithm 2: CullGaussian + ScreenspaceGaussians)
+// and backward (chain rule of App. A) kernels, one thread per Gaussian.
+//
+// Forward, per Gaussian (Sec. 4, Sec. 6):
+//   t = W mu + t_w; reject z <= near, |x/z| > guard tan_x, |y/z| > guard tan_y;
+//   R = R(q / |q|) (eq. quat), M = R diag(s), Sigma = M M^T;
+//   Sigma' = J W Sigma W^T J^T (eq. volume-render) evaluated as V V^T with V = (J W) M, so the
+//   determinant comes from the cross product |v0 x v1|^2 (no cancellation), plus 0.3 I;
+//   conic = Sigma'^-1 (stored as its Cholesky factor); radius = ceil(3 sqrt(lambda_max));
+//   mean2D = (fx x/z + cx, fy y/z + cy) in double-float;
+//   tile rectangle (culled when empty); rgb = max(0, sum_k c_k Y_k((mu - C)/|mu - C|)).
+// Backward: the same quantities recomputed, then dL/dconic -> dL/dSigma' = -Q G Q ->
+//   dL/dV = 2 H V -> dL/dM = (J W)^T dL/dV -> (s, R) -> q_hat -> q (normalisation Jacobian);
+//   dL/d(J W) -> dL/dJ -> dL/dt; dL/dmean2D -> dL/dt; dL/dt -> dL/dmu = W^T dL/dt;
+//   dL/drgb (clamp mask) -> dL/dSH = Y dL/drgb and -> dL/d dir -> dL/dmu.
+#include "gs_device.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+namespace {
+
+struct Proj {
+    float tx, ty, tz;     // camera-space mean (rounded)
+    float xz, yz;         // x/z, y/z (rounded)
+    DF u, v;              // screen mean, double-float
+    float qn[4];          // normalised quaternion
+    float qinv;           // 1 / |q|
+    float R[9];           // R(q_hat)
+    float M[9];           // R diag(s)
+    float T2[6];          // J W (2 x 3)
+    float V[6];           // J W M (2 x 3)
+    float A, B, C;        // Sigma' with dilation
+    float det;
+};
+
+__device__ __forceinline__ void rot_from_quat(const float* q, float* R) {
+    const float r = q[0], i = q[1], j = q[2], k = q[3];
+    R[0] = 1.f - 2.f * (j * j + k * k); R[1] = 2.f * (i * j - r * k);       R[2] = 2.f * (i * k + r * j);
+    R[3] = 2.f * (i * j + r * k);       R[4] = 1.f - 2.f * (i * i + k * k); R[5] = 2.f * (j * k - r * i);
+    R[6] = 2.f * (i * k - r * j);       R[7] = 2.f * (j * k + r * i);       R[8] = 1.f - 2.f * (i * i + j * j);
+}
+
+// Camera-space mean, guard-band test and screen mean.  The mean is carried in double-float
+// (compensated dot product and division) so that u, v and the depth are accurate to about
+// 1e-12 relative: fp32 alone would leave errors of ~1e-4 px at the far side of a 1080p image.
+// Returns false when rejected.
+__device__ __forceinline__ bool project_mean(const float* mu, const CamK& c, Proj& p) {
+    const DF x = dot3_plus(c.R, mu, c.t[0]);
+    const DF y = dot3_plus(c.R + 3, mu, c.t[1]);
+    const DF z = dot3_plus(c.R + 6, mu, c.t[2]);
+    p.tx = x.hi;
+    p.ty = y.hi;
+    p.tz = z.hi;
+    if (!(p.tz > c.near_z) || !isfinite(p.tz)) return false;
+    const DF xz = df_div(x, z), yz = df_div(y, z);
+    p.xz = xz.hi;
+    p.yz = yz.hi;
+    if (fabsf(p.xz) > c.lim_x || fabsf(p.yz) > c.lim_y) return false;
+    p.u = df_mul_add(c.fx, xz, c.cx);
+    p.v = df_mul_add(c.fy, yz, c.cy);
+    return true;
+}
+
+// Covariance projection; requires project_mean first.
+__device__ __forceinline__ void project_cov(const float* s, const float4 q, const CamK& c, float dilation,
+                                            Proj& p) {
+    const float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    p.qinv = rsqrtf(qq);
+    p.qn[0] = q.x * p.qinv; p.qn[1] = q.y * p.qinv; p.qn[2] = q.z * p.qinv; p.qn[3] = q.w * p.qinv;
+    rot_from_quat(p.qn, p.R);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p.M[3 * r + k] = p.R[3 * r + k] * s[k];
+    // J W: row0 = fx/z (W0 - x/z W2), row1 = fy/z (W1 - y/z W2)
+    const float fz = c.fx / p.tz, gz = c.fy / p.tz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p.T2[k] = fz * (c.R[k] - p.xz * c.R[6 + k]);
+        p.T2[3 + k] = gz * (c.R[3 + k] - p.yz * c.R[6 + k]);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            p.V[3 * r + k] = p.T2[3 * r] * p.M[k] + p.T2[3 * r + 1] * p.M[3 + k] + p.T2[3 * r + 2] * p.M[6 + k];
+    const float a = p.V[0] * p.V[0] + p.V[1] * p.V[1] + p.V[2] * p.V[2];
+    const float b = p.V[0] * p.V[3] + p.V[1] * p.V[4] + p.V[2] * p.V[5];
+    const float cc = p.V[3] * p.V[3] + p.V[4] * p.V[4] + p.V[5] * p.V[5];
+    // det(V V^T) = |v0 x v1|^2 (Cauchy-Binet)
+    const float cx = p.V[1] * p.V[5] - p.V[2] * p.V[4];
+    const float cy = p.V[2] * p.V[3] - p.V[0] * p.V[5];
+    const float cz = p.V[0] * p.V[4] - p.V[1] * p.V[3];
+    const float det_raw = cx * cx + cy * cy + cz * cz;
+    p.A = a + dilation;
+    p.B = b;
+    p.C = cc + dilation;
+    p.det = det_raw + dilation * (a + cc) + dilation * dilation;
+}
+
+__device__ __forceinline__ bool finite3(const float* v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_preprocess(PreprocessArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool visible = false;
+    if (i < a.n) {
+        const CamK& c = a.cam;
+        float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
+        float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
+        const float4 q = reinterpret_cast<const float4*>(a.quats)[i];
+        const float o = a.opacities[i];
+        const bool finite = finite3(mu) && finite3(s) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
+                            isfinite(q.w) && isfinite(o);
+        int radius = 0;
+        float4 xy = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 co = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 rgb = make_float4(0.f, 0.f, 0.f, 0.f);
+        float depth = 0.f;
+        Proj p;
+        if (!finite) {
+            atomicAdd(&a.status->num_nonfinite, 1u);
+        } else if (project_mean(mu, c, p) && (q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w) > 0.f) {
+            project_cov(s, q, c, a.cfg.dilation, p);
+            if (p.det > 0.f) {
+                // Cholesky factor of the conic (see splat_power).
+                co = make_float4(sqrtf(p.C / p.det), -p.B / sqrtf(p.C * p.det), 1.0f / sqrtf(p.C), o);
+                const float m = 0.5f * (p.A + p.C);
+                const float h = 0.5f * (p.A - p.C);
+                const float lam = m + sqrtf(h * h + p.B * p.B);
+                const float rr = a.cfg.extent * sqrtf(lam);
+                radius = rr >= (float)a.cfg.radius_max ? a.cfg.radius_max : (int)ceilf(rr);
+                xy = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
+                int x0, x1, y0, y1;
+                if (!tile_rect(xy, radius, c, x0, x1, y0, y1)) radius = 0;
+                depth = p.tz;
+            }
+        }
+        if (radius > 0) {
+            // View-dependent colour from the SH coefficients.
+            float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];
+            const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+            dx *= inv; dy *= inv; dz *= inv;
+            float Y[16];
+            sh_basis(a.sh_degree, dx, dy, dz, Y);
+            const int D = (a.sh_degree + 1) * (a.sh_degree + 1);
+            const float* sh = a.sh + (size_t)i * a.sh_stride * 3;
+            float r = 0.f, g = 0.f, b = 0.f;
+            for (int k = 0; k < D; ++k) {
+                r += sh[3 * k] * Y[k];
+                g += sh[3 * k + 1] * Y[k];
+                b += sh[3 * k + 2] * Y[k];
+            }
+            if (!(isfinite(r) && isfinite(g) && isfinite(b))) {
+                atomicAdd(&a.status->num_nonfinite, 1u);
+                radius = 0;
+            } else {
+                const uint32_t mask = (r < 0.f ? 1u : 0u) | (g < 0.f ? 2u : 0u) | (b < 0.f ? 4u : 0u);
+                rgb = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(b, 0.f), __uint_as_float(mask));
+            }
+        }
+        visible = radius > 0;
+        a.xy[i] = xy;
+        a.depth[i] = depth;
+        a.conic_opacity[i] = co;
+        a.rgb[i] = rgb;
+        a.radius[i] = radius;
+    }
+    const uint32_t vis = __ballot_sync(0xffffffffu, visible);
+    if ((threadIdx.x & 31) == 0 && vis) atomicAdd(&a.status->num_visible, (uint32_t)__popc(vis));
+}
+
+__global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int D = (a.sh_degree + 1) * (a.sh_degree + 1);
+    float* gsh = a.g_sh + (size_t)i * a.sh_stride * 3;
+    const int radius = a.radius[i];
+    if (radius <= 0) {
+        if (!a.accumulate) {
+            for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = 0.f; a.g_scales[3 * i + k] = 0.f; }
+            reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.g_opacities[i] = 0.f;
+            for (int k = 0; k < a.sh_stride * 3; ++k) gsh[k] = 0.f;
+            if (a.g_mean2d) { a.g_mean2d[2 * i] = 0.f; a.g_mean2d[2 * i + 1] = 0.f; }
+        }
+        return;
+    }
+    const CamK& c = a.cam;
+    const float4 g0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i];       // du dv da db
+    const float4 g1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];   // dc do dr dg
+    const float g2 = a.grad2d[12 * i + 8];                                    // db(rgb)
+    const float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
+    const float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
+    const float4 q = reinterpret_cast<const float4*>(a.quats)[i];
+    Proj p;
+    project_mean(mu, c, p);
+    project_cov(s, q, c, a.cfg.dilation, p);
+    const float inv = 1.0f / p.det;
+    const float ca = p.C * inv, cb = -p.B * inv, cc = p.A * inv;   // conic Q = [[ca, cb], [cb, cc]]
+
+    // dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]] (b enters the exponent once).
+    const float da = g0.z, db = g0.w, dc = g1.x;
+    const float H00 = -(ca * ca * da + ca * cb * db + cb * cb * dc);
+    const float H01 = -(ca * cb * da + 0.5f * (cb * cb + ca * cc) * db + cb * cc * dc);
+    const float H11 = -(cb * cb * da + cb * cc * db + cc * cc * dc);
+    // Sigma'_raw = V V^T: dL/dV = 2 H V.
+    float dV[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dV[k] = 2.f * (H00 * p.V[k] + H01 * p.V[3 + k]);
+        dV[3 + k] = 2.f * (H01 * p.V[k] + H11 * p.V[3 + k]);
+    }
+    // V = T2 M: dL/dM = T2^T dV, dL/dT2 = dV M^T.
+    float dM[9], dT2[6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dM[3 * r + k] = p.T2[r] * dV[k] + p.T2[3 + r] * dV[3 + k];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dT2[3 * r + k] = dV[3 * r] * p.M[3 * k] + dV[3 * r + 1] * p.M[3 * k + 1] + dV[3 * r + 2] * p.M[3 * k + 2];
+    // M = R diag(s).
+    float gs3[3], dR[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gs3[k] = dM[k] * p.R[k] + dM[3 + k] * p.R[3 + k] + dM[6 + k] * p.R[6 + k];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dR[3 * r + k] = dM[3 * r + k] * s[k];
+    // R(q_hat), eq. quat.
+    const float qr = p.qn[0], qi = p.qn[1], qj = p.qn[2], qk = p.qn[3];
+    float dq[4];
+    dq[0] = 2.f * (-qk * dR[1] + qj * dR[2] + qk * dR[3] - qi * dR[5] - qj * dR[6] + qi * dR[7]);
+    dq[1] = 2.f * (qj * dR[1] + qk * dR[2] + qj * dR[3] - 2.f * qi * dR[4] - qr * dR[5] + qk * dR[6] + qr * dR[7] -
+                   2.f * qi * dR[8]);
+    dq[2] = 2.f * (-2.f * qj * dR[0] + qi * dR[1] + qr * dR[2] + qi * dR[3] + qk * dR[5] - qr * dR[6] + qk * dR[7] -
+                   2.f * qj * dR[8]);
+    dq[3] = 2.f * (-2.f * qk * dR[0] - qr * dR[1] + qi * dR[2] + qr * dR[3] - 2.f * qk * dR[4] + qj * dR[5] +
+                   qi * dR[6] + qj * dR[7]);
+    const float proj = dq[0] * qr + dq[1] * qi + dq[2] * qj + dq[3] * qk;
+    float4 gq = make_float4((dq[0] - qr * proj) * p.qinv, (dq[1] - qi * proj) * p.qinv, (dq[2] - qj * proj) * p.qinv,
+                            (dq[3] - qk * proj) * p.qinv);
+    // T2 = J W with J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]].
+    float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dJ00 += dT2[k] * c.R[k];
+        dJ02 += dT2[k] * c.R[6 + k];
+        dJ11 += dT2[3 + k] * c.R[3 + k];
+        dJ12 += dT2[3 + k] * c.R[6 + k];
+    }
+    const float du = g0.x, dv = g0.y;
+    const float iz = 1.0f / p.tz, iz2 = iz * iz;
+    const float fx = c.fx, fy = c.fy;
+    float dt0 = du * fx * iz - dJ02 * fx * iz2;
+    float dt1 = dv * fy * iz - dJ12 * fy * iz2;
+    float dt2 = -du * fx * p.xz * iz - dv * fy * p.yz * iz - dJ00 * fx * iz2 + dJ02 * 2.f * fx * p.xz * iz2 -
+                dJ11 * fy * iz2 + dJ12 * 2.f * fy * p.yz * iz2;
+    float gm[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gm[k] = c.R[k] * dt0 + c.R[3 + k] * dt1 + c.R[6 + k] * dt2;
+
+    // Colour: dL/dSH and the view-direction term.
+    const float4 rgbm = a.rgb[i];
+    const uint32_t mask = __float_as_uint(rgbm.w);
+    const float dr = (mask & 1u) ? 0.f : g1.z;
+    const float dg = (mask & 2u) ? 0.f : g1.w;
+    const float dbl = (mask & 4u) ? 0.f : g2;
+    float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];
+    const float ninv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= ninv; dy *= ninv; dz *= ninv;
+    float Y[16];
+    float3 dY[16];
+    sh_basis(a.sh_degree, dx, dy, dz, Y);
+    sh_basis_grad(a.sh_degree, dx, dy, dz, dY);
+    const float* sh = a.sh + (size_t)i * a.sh_stride * 3;
+    float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+    for (int k = 0; k < D; ++k) {
+        const float w = sh[3 * k] * dr + sh[3 * k + 1] * dg + sh[3 * k + 2] * dbl;
+        ddx += w * dY[k].x; ddy += w * dY[k].y; ddz += w * dY[k].z;
+        float g3[3] = {Y[k] * dr, Y[k] * dg, Y[k] * dbl};
+        for (int ch = 0; ch < 3; ++ch) {
+            if (a.accumulate) gsh[3 * k + ch] += g3[ch];
+            else gsh[3 * k + ch] = g3[ch];
+        }
+    }
+    if (!a.accumulate)
+        for (int k = 3 * D; k < a.sh_stride * 3; ++k) gsh[k] = 0.f;
+    const float dp = ddx * dx + ddy * dy + ddz * dz;
+    gm[0] += (ddx - dx * dp) * ninv;
+    gm[1] += (ddy - dy * dp) * ninv;
+    gm[2] += (ddz - dz * dp) * ninv;
+
+    if (a.accumulate) {
+        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] += gm[k]; a.g_scales[3 * i + k] += gs3[k]; }
+        float4 o4 = reinterpret_cast<float4*>(a.g_quats)[i];
+        reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(o4.x + gq.x, o4.y + gq.y, o4.z + gq.z, o4.w + gq.w);
+        a.g_opacities[i] += g1.y;
+        if (a.g_mean2d) { a.g_mean2d[2 * i] += du; a.g_mean2d[2 * i + 1] += dv; }
+    } else {
+        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = gm[k]; a.g_scales[3 * i + k] = gs3[k]; }
+        reinterpret_cast<float4*>(a.g_quats)[i] = gq;
+        a.g_opacities[i] = g1.y;
+        if (a.g_mean2d) { a.g_mean2d[2 * i] = du; a.g_mean2d[2 * i + 1] = dv; }
+    }
+}
+
+int persistent_grid(const void* kernel, int threads) {
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_preprocess(const PreprocessArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    k_preprocess<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward(const PreprocessBwdArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    k_preprocess_backward<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,140 @@
+"""The C ABI library loads on a machine without a GPU, exports every entry point that
+include/gs.h declares, and its host-only functions (configuration, workspace sizing and
+layout, argument validation) behave as documented.  No kernel is launched here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_04079_gb300 import _abi, build
+    build.build()
+    return _abi.load()
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_four_stages():
+    names = _declared_functions()
+    for n in ("gs_preprocess", "gs_bin_sort", "gs_render_forward", "gs_render_backward"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2308_04079_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gs_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [n for n in _declared_functions() if n not in exported]
+    assert not missing, missing
+    from paper_2308_04079_gb300 import _abi
+    assert sorted(n for n, _, _ in _abi.SIGNATURES) == _declared_functions()
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    """ctypes mirrors of the ABI structs have the sizes the C compiler gives them."""
+    from paper_2308_04079_gb300 import _abi
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "gs.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gs_camera), sizeof(gs_raster_config), sizeof(gs_gaussians),
+         sizeof(gs_gradients), sizeof(gs_frame), sizeof(gs_layout), sizeof(gs_device_status),
+         offsetof(gs_frame, capacity), offsetof(gs_frame, ws_bytes));
+  return 0;
+}'''
+    src = str(tmp_path / "layout.c")
+    exe = str(tmp_path / "layout")
+    open(src, "w").write(code)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include", src, "-o", exe],
+                   check=True)
+    got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(_abi.gs_camera), ctypes.sizeof(_abi.gs_raster_config), ctypes.sizeof(_abi.gs_gaussians),
+            ctypes.sizeof(_abi.gs_gradients), ctypes.sizeof(_abi.gs_frame), ctypes.sizeof(_abi.gs_layout),
+            ctypes.sizeof(_abi.gs_device_status), _abi.gs_frame.capacity.offset, _abi.gs_frame.ws_bytes.offset]
+    assert got == want
+
+
+def test_default_config_is_the_papers(lib):
+    from paper_2308_04079_gb300 import _abi
+    c = _abi.gs_default_config()
+    assert (c.tile_w, c.tile_h, c.batch_depth, c.sort_mode) == (16, 16, 256, _abi.GS_SORT_TWO_PHASE)
+    assert c.alpha_min == pytest.approx(1 / 255) and c.alpha_max == pytest.approx(0.99)
+    assert c.T_min == pytest.approx(1e-4) and c.dilation == pytest.approx(0.3)
+    assert c.guard == pytest.approx(1.3) and c.extent == pytest.approx(3.0)
+
+
+def test_workspace_size_and_layout(lib):
+    from paper_2308_04079_gb300 import _abi
+    c = _abi.gs_default_config()
+    s1 = _abi.gs_workspace_size(1000, 1920, 1080, 1 << 20, c)
+    s2 = _abi.gs_workspace_size(1000, 1920, 1080, 1 << 21, c)
+    assert 0 < s1 < s2
+    L = _abi.gs_workspace_layout(1000, 1920, 1080, 1 << 20, c)
+    assert L.total_bytes == s1
+    assert (L.tiles_x, L.tiles_y) == (120, 68)
+    assert L.key_passes == 2 and L.depth_passes == 4          # 8160 tiles -> 13 bits
+    offs = [L.xy, L.depth, L.conic_opacity, L.rgb, L.radius, L.vals_sorted, L.keys_sorted, L.ranges, L.grad2d,
+            L.status]
+    assert all(o % 16 == 0 for o in offs) and all(o < s1 for o in offs)
+    c.sort_mode = _abi.GS_SORT_KEY64
+    L64 = _abi.gs_workspace_layout(1000, 1920, 1080, 1 << 20, c)
+    assert L64.key_passes == 6 and L64.depth_passes == 0       # 32 + 13 bits
+    assert _abi.gs_workspace_size(0, 64, 64, 0, c) > 0         # empty scenes are valid
+
+
+@pytest.mark.parametrize("bad", [dict(tile_w=12), dict(batch_depth=0), dict(batch_depth=257), dict(sort_mode=7),
+                                 dict(alpha_min=0.0), dict(alpha_max=1.5), dict(T_min=0.0)])
+def test_invalid_config_rejected(lib, bad):
+    from paper_2308_04079_gb300 import _abi
+    c = _abi.gs_default_config()
+    for k, v in bad.items():
+        setattr(c, k, v)
+    assert _abi.gs_workspace_size(10, 64, 64, 100, c) == 0
+    with pytest.raises(_abi.GSError):
+        _abi.gs_workspace_layout(10, 64, 64, 100, c)
+
+
+def test_invalid_sizes_rejected(lib):
+    from paper_2308_04079_gb300 import _abi
+    c = _abi.gs_default_config()
+    assert _abi.gs_workspace_size(-1, 64, 64, 100, c) == 0
+    assert _abi.gs_workspace_size(10, 0, 64, 100, c) == 0
+    assert _abi.gs_workspace_size(10, 64, 64, 1 << 31, c) == 0
+
+
+def test_stage_calls_validate_before_touching_the_device(lib):
+    """Null / undersized / misaligned descriptions return GS_ERR_INVALID_ARG synchronously."""
+    from paper_2308_04079_gb300 import _abi
+    L = _abi.load()
+    assert L.gs_preprocess(None, None, None) == _abi.GS_ERR_INVALID_ARG
+    assert L.gs_bin_sort(None, None) == _abi.GS_ERR_INVALID_ARG
+    f = _abi.gs_frame()
+    f.n = 10
+    f.cam.width, f.cam.height, f.cam.fx, f.cam.fy, f.cam.near_z = 64, 64, 50.0, 50.0, 0.2
+    f.cfg = _abi.gs_default_config()
+    f.capacity = 100
+    f.ws = 256
+    f.ws_bytes = 16            # far too small
+    assert L.gs_bin_sort(ctypes.byref(f), None) == _abi.GS_ERR_INVALID_ARG
+    f.ws_bytes = _abi.gs_workspace_size(10, 64, 64, 100, f.cfg)
+    f.ws = 257                 # misaligned
+    assert L.gs_bin_sort(ctypes.byref(f), None) == _abi.GS_ERR_INVALID_ARG
+    f.ws = 256
+    g = _abi.gs_gaussians()
+    g.n = 9                    # does not match the frame
+    assert L.gs_preprocess(ctypes.byref(f), ctypes.byref(g), None) == _abi.GS_ERR_INVALID_ARG
+    bg = (ctypes.c_float * 3)(0, 0, 0)
+    assert L.gs_render_forward(ctypes.byref(f), ctypes.byref(bg), None, None, None, None) == _abi.GS_ERR_INVALID_ARG
+    assert _abi.status_string(_abi.GS_ERR_CAPACITY) == "instance capacity exceeded"

@@ -1,0 +1,101 @@
+"""gs_render_backward (Sec. 6 traversal, App. A chain rule) vs the oracle's analytic FP64
+gradients, for the screen-space accumulators and for every input tensor; the oracle's
+analytic gradients are themselves pinned to finite differences on the CPU.  Gaussians that
+are relevant to a pixel with an ambiguous decision are excluded and counted."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from gpu_util import compare_grads, gpu_backward, gpu_forward
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(g, cam, bg, dimg, tile_mask=None, max_excluded=0.05, cfg=None):
+    run = gpu_forward(g, cam, bg, cfg)
+    gg = gpu_backward(run, bg, dimg)
+    ob = oracle.render_backward(g, cam, dimg, bg, tile_mask=tile_mask)
+    touched = np.abs(ob["opacities"]) > 0
+    keep = touched & (ob["gauss_amb"] == 0)
+    excluded = float((touched & ~keep).sum()) / max(1, touched.sum())
+    assert touched.sum() > 10
+    assert excluded <= max_excluded, excluded
+    ob2 = dict(ob)
+    ob2["opac2d"] = ob["opacities"]
+    s2 = compare_grads(gg, ob2, keep, names=("uv", "conic", "opac2d", "rgb"))
+    s3 = compare_grads(gg, ob, keep)
+    # Gaussians that received no gradient in FP64 receive none on the GPU either
+    untouched = ~touched & (ob["gauss_amb"] == 0)
+    assert np.all(gg["opacities"][untouched] == 0)
+    return s2, s3, excluded
+
+
+@pytest.mark.parametrize("seed,kw", [(301, dict(n=200, width=100, height=37)),
+                                     (302, dict(n=300, width=64, height=64, deg=0)),
+                                     (303, dict(n=400, width=90, height=70, deg=3, log_scale_mean=-3.0)),
+                                     (304, dict(n=300, width=48, height=48, deg=1, opacity_logit_std=2.5))])
+def test_tiny_scene_gradients(seed, kw):
+    g, cam = S.tiny_scene(seed, **kw)
+    dimg = S.upstream_grad(seed + 1, cam.height, cam.width)
+    _check(g, cam, (0.1, 0.3, 0.2), dimg, max_excluded=0.1)
+
+
+def test_config2_crop_gradients():
+    """The config-2 gradient-check case: 5k Gaussians, 64x64 window of the 1080p camera."""
+    g, cam, bg, dimg = S.config2_crop()
+    _check(g, cam, bg, dimg)
+
+
+def test_config2_full_frame_gradients():
+    g, cam, bg, dimg = S.config2()
+    _check(g, cam, bg, dimg)
+
+
+def test_config3_sampled_tiles_gradients():
+    """3M Gaussians at 1080p: dL/dpixel is non-zero on 32 sampled tiles only, so the oracle
+    restricted to those tiles computes the same gradients."""
+    g, cam, bg, dimg = S.config3()
+    TX, TY = 120, 68
+    rng = np.random.default_rng(4444)
+    tiles = rng.choice(TX * TY, 32, replace=False)
+    mask = np.zeros(TX * TY, np.uint8)
+    mask[tiles] = 1
+    pix = np.repeat(np.repeat(mask.reshape(TY, TX), 16, 0), 16, 1)[:1080, :1920].astype(bool)
+    dimg = np.where(pix[None], dimg, 0.0).astype(np.float32)
+    _check(g, cam, bg, dimg, tile_mask=mask)
+
+
+def test_accumulate_over_views_sums_gradients():
+    import torch
+    g, cam1 = S.tiny_scene(305, n=200, width=64, height=48)
+    cam2 = S.orbit_camera(3.0, 0.4, 0.2, 64, 48)
+    d1, d2 = S.upstream_grad(1, 48, 64), S.upstream_grad(2, 48, 64)
+    bg = (0.0, 0.0, 0.0)
+    r1, r2 = gpu_forward(g, cam1, bg), gpu_forward(g, cam2, bg)
+    g1, g2 = gpu_backward(r1, bg, d1), gpu_backward(r2, bg, d2)
+    # accumulate view 2 into view 1's gradients
+    from paper_2308_04079_gb300 import GaussianTensors
+    grads = {k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in g1.items()
+             if k in ("means", "scales", "quats", "opacities", "sh", "mean2d")}
+    r2["frame"].render_backward(r2["g"], bg, torch.from_numpy(d2).cuda(), r2["T_t"], r2["last_t"], grads,
+                                accumulate=True)
+    for k in ("means", "scales", "quats", "opacities", "sh"):
+        np.testing.assert_allclose(grads[k].cpu().numpy(), g1[k] + g2[k], rtol=1e-5, atol=1e-6)
+
+
+def test_autograd_function_matches_direct_calls():
+    import torch
+    from paper_2308_04079_gb300 import rasterize
+    g, cam = S.tiny_scene(306, n=200, width=64, height=48)
+    dimg = S.upstream_grad(7, 48, 64)
+    bg = (0.1, 0.1, 0.1)
+    t = {k: torch.tensor(getattr(g, k), device="cuda", requires_grad=True)
+         for k in ("means", "scales", "quats", "opacities", "sh")}
+    img = rasterize(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], g.sh_degree, cam, bg)
+    (img * torch.from_numpy(dimg).cuda()).sum().backward()
+    run = gpu_forward(g, cam, bg)
+    direct = gpu_backward(run, bg, dimg)
+    np.testing.assert_array_equal(img.detach().cpu().numpy(), run["img"].astype(np.float32))
+    for k in t:
+        np.testing.assert_allclose(t[k].grad.cpu().numpy(), direct[k], rtol=1e-5, atol=1e-7)

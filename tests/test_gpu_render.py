@@ -1,0 +1,86 @@
+"""gs_render_forward (eq. front-to-back, App. C rules) vs the FP64 oracle's per-pixel
+definition: image, final transmittance and last contributor, element by element on every
+pixel whose decisions are not within the ambiguity margin of a threshold."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from gpu_util import compare_images, gpu_forward
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg_pair(tile, mode="two_phase", batch=None):
+    from paper_2308_04079_gb300 import make_config
+    return make_config(tile=tile, sort_mode=mode, batch_depth=batch), oracle.cfg_array(tile_w=tile[0], tile_h=tile[1])
+
+
+TINY = [
+    (201, dict(n=200, width=100, height=37)),
+    (202, dict(n=400, width=64, height=64, deg=0)),
+    (203, dict(n=300, width=81, height=47, deg=2, log_scale_mean=-2.0)),
+    (204, dict(n=600, width=130, height=70, deg=3, log_scale_mean=-3.0, opacity_logit_std=2.5)),
+]
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (16, 8), (8, 8)])
+@pytest.mark.parametrize("seed,kw", TINY)
+def test_tiny_scenes(seed, kw, tile):
+    g, cam = S.tiny_scene(seed, **kw)
+    bg = (0.2, 0.4, 0.6)
+    gcfg, ocfg = _cfg_pair(tile)
+    run = gpu_forward(g, cam, bg, gcfg)
+    orc = oracle.render_forward(g, cam, bg, ocfg)
+    compare_images(run, orc, max_amb_frac=0.05)
+
+
+@pytest.mark.parametrize("mode,batch", [("two_phase", None), ("key64", None), ("two_phase", 32), ("key64", 100)])
+def test_config1(mode, batch):
+    """1,000 Gaussians, SH degree 0, 128x128, black background (config 1)."""
+    g, cam, bg = S.config1()
+    gcfg, ocfg = _cfg_pair((16, 16), mode, batch)
+    run = gpu_forward(g, cam, bg, gcfg)
+    orc = oracle.render_forward(g, cam, bg, ocfg)
+    st = compare_images(run, orc, max_amb_frac=0.03)
+    assert (run["last"] > 0).mean() > 0.3
+
+
+def test_config2_full_frame():
+    """200k Gaussians, SH degree 3, 1920x1080 (config 2), every pixel."""
+    g, cam, bg, _ = S.config2()
+    gcfg, ocfg = _cfg_pair((16, 16))
+    run = gpu_forward(g, cam, bg, gcfg)
+    orc = oracle.render_forward(g, cam, bg, ocfg)
+    st = compare_images(run, orc, max_amb_frac=0.03)
+    assert st["pixels"] > 0.97 * 1920 * 1080
+
+
+def test_config3_sampled_tiles():
+    """3M Gaussians, 1920x1080 (config 3): every pixel of 48 sampled tiles (plus the image
+    centre and the ragged bottom row of tiles) against the oracle restricted to those tiles."""
+    g, cam, bg, _ = S.config3()
+    gcfg, ocfg = _cfg_pair((16, 16))
+    run = gpu_forward(g, cam, bg, gcfg)
+    TX, TY = 120, 68
+    rng = np.random.default_rng(3333)
+    tiles = set(rng.choice(TX * TY, 48, replace=False).tolist())
+    tiles |= {34 * TX + 60, 67 * TX + 5, 67 * TX + 119}
+    mask = np.zeros(TX * TY, np.uint8)
+    mask[list(tiles)] = 1
+    orc = oracle.render_forward(g, cam, bg, ocfg, tile_mask=mask)
+    pix = np.zeros((1080, 1920), bool)
+    for t in tiles:
+        ty, tx = divmod(t, TX)
+        pix[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    gsub = dict(img=run["img"][:, pix], T=run["T"][pix], last=run["last"][pix])
+    osub = dict(img=orc["img"][:, pix], T=orc["T"][pix], last=orc["last"][pix], pix_amb=orc["pix_amb"][pix])
+    compare_images(gsub, osub, max_amb_frac=0.04)
+    assert (run["last"][pix] > 0).mean() > 0.2
+
+
+def test_forward_is_deterministic():
+    g, cam, bg, _ = S.config2(n=50_000)
+    a = gpu_forward(g, cam, bg)
+    b = gpu_forward(g, cam, bg)
+    assert np.array_equal(a["img"], b["img"]) and np.array_equal(a["last"], b["last"])
