@@ -129,7 +129,9 @@ typedef struct gs_frame {
 typedef struct gs_layout {
     uint64_t xy, depth, conic_opacity, rgb, radius;
     uint64_t vals_sorted, keys_sorted, ranges;
-    uint64_t grad2d;          /* float[n, 12] per-Gaussian screen-space gradient accumulators */
+    uint64_t grad2d;          /* float[n, 12] per-Gaussian screen-space gradient accumulators:
+                                 dL/du, dL/dv, dL/dSigma'_00, dL/dSigma'_01, dL/dSigma'_11 (full-
+                                 matrix convention), dL/do, dL/d(r, g, b), 3 unused */
     uint64_t status;          /* gs_device_status                                           */
     uint64_t total_bytes;
     int tiles_x, tiles_y;
@@ -187,8 +189,8 @@ gs_status gs_render_forward(const gs_frame* frame, const float bg[3], float* out
 
 /* Backward pass (Sec. 6 and App. A): every tile is traversed back to front from its last
  * contributor; each pixel recovers T_i = T_{i+1} / (1 - a_i) from the stored T_final and
- * accumulates dL/d(mean2D, conic, opacity, colour) of every Gaussian it blended (reduced per
- * warp before global atomics); then, per Gaussian, the chain rule through the conic, Sigma',
+ * accumulates dL/d(mean2D, Sigma', opacity, colour) of every Gaussian it blended (reduced per
+ * warp before global atomics); then, per Gaussian, the chain rule through Sigma',
  * Sigma = M M^T, M = R S, the quaternion normalisation, the projection Jacobian, the screen
  * mean and the SH colour gives the gradients of every input.  dL_drgb float[3, H, W], T and
  * last are the forward outputs.  accumulate != 0 adds into the gradient arrays (several views
@@ -201,7 +203,7 @@ gs_status gs_render_backward(const gs_frame* frame, const gs_gaussians* g, const
  * gs_render_backward_tiles followed by gs_render_backward_gaussians):
  *   gs_render_backward_tiles      zeroes the workspace's per-Gaussian screen-space gradient
  *                                 accumulators, then runs the back-to-front tile traversal (Sec. 6)
- *                                 that fills them: dL/d(mean2D, conic, opacity, colour).
+ *                                 that fills them: dL/d(mean2D, Sigma', opacity, colour).
  *   gs_render_backward_gaussians  per Gaussian, the chain rule of App. A from those accumulators to
  *                                 the input gradients (see gs_render_backward for the arguments).
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */

@@ -77,7 +77,7 @@ def _load():
         lib.orc_render_forward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
                                            D, U8, D, D, I32, U8, U32]
         lib.orc_render_backward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
-                                            D, U8, D, D, D, D, D, D, D, D, D, U8, U32]
+                                            D, U8, D, D, D, D, D, D, D, D, D, D, U8, U32]
         lib.orc_bin.argtypes = [L, F, F, I32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 L, U64, U32, U32]
         lib.orc_bin.restype = L
@@ -205,8 +205,8 @@ def render_forward(g, cam, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, ti
 
 def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
     """Analytic FP64 gradients of L = <dL_dimg, image> w.r.t. every input, plus the
-    screen-space gradients (mean2D, conic, opacity, colour) that the backward walk
-    accumulates."""
+    screen-space gradients that the backward walk accumulates: mean2D (uv), conic, opacity,
+    colour, and dL/dSigma' (cov2d: entries 00, 01, 11, full-matrix convention)."""
     cfg = cfg_array() if cfg is None else cfg
     n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
     ca = cam_array(cam)
@@ -216,13 +216,14 @@ def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None 
     m = _mask_arg(cam, cfg, tile_mask)
     out = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacities=np.zeros(n), sh=np.zeros_like(sh), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
-               rgb=np.zeros((n, 3)), pix_amb=np.zeros((H, W), np.uint8), gauss_amb=np.zeros(n, np.uint32))
+               rgb=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), pix_amb=np.zeros((H, W), np.uint8),
+               gauss_amb=np.zeros(n, np.uint32))
     D = ctypes.c_double
     _load().orc_render_backward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
                                 _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(dimg, D),
                                 _p(out["means"], D), _p(out["scales"], D), _p(out["quats"], D),
                                 _p(out["opacities"], D), _p(out["sh"], D), _p(out["uv"], D), _p(out["conic"], D),
-                                _p(out["rgb"], D), _p(out["pix_amb"], ctypes.c_uint8),
+                                _p(out["rgb"], D), _p(out["cov2d"], D), _p(out["pix_amb"], ctypes.c_uint8),
                                 _p(out["gauss_amb"], ctypes.c_uint32))
     return out
 

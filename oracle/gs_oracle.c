@@ -603,7 +603,10 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         double alpha = clamped ? cfg->alpha_max : oG;
         if (alpha < cfg->alpha_min) continue;                   /* skip (App. C) */
         double test_T = T * (1.0 - alpha);
-        if (near_threshold(test_T, cfg->T_min, cfg->eps_T)) flags |= PIX_DECISION | PIX_ANY;
+        if (near_threshold(test_T, cfg->T_min, cfg->eps_T)) {
+            flags |= PIX_DECISION | PIX_ANY;
+            if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);   /* its inclusion may flip */
+        }
         if (test_T < cfg->T_min) break;                         /* stop before exceeding 0.9999 */
         for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * alpha * T;
         if (rec) {
@@ -714,7 +717,7 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                          const double* sh, int deg, int sh_stride, const double* cam, const double* cfg,
                          const double* bg, const uint8_t* tile_mask, const double* dL_dimg,
                          double* d_means, double* d_scales, double* d_quats, double* d_opac, double* d_sh,
-                         double* d_uv, double* d_conic, double* d_rgb,
+                         double* d_uv, double* d_conic, double* d_rgb, double* d_cov2d,
                          uint8_t* out_pix_amb, uint32_t* out_gauss_amb) {
     oscene S;
     scene_init(&S, n, means, scales, quats, opac, sh, deg, sh_stride, cam, cfg);
@@ -786,6 +789,7 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
         for (int k = 0; k < 3; ++k) { dmu[k] = 0.0; ds[k] = 0.0; }
         for (int k = 0; k < 4; ++k) dq[k] = 0.0;
         for (int k = 0; k < sh_stride * 3; ++k) dsh[k] = 0.0;
+        d_cov2d[3 * i] = d_cov2d[3 * i + 1] = d_cov2d[3 * i + 2] = 0.0;
         if (!g->visible) { d_opac[i] = 0.0; continue; }
         const double* s = scales + 3 * i;
 
@@ -798,6 +802,9 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
             for (int c = 0; c < 2; ++c) QG[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
         for (int r = 0; r < 2; ++r)
             for (int c = 0; c < 2; ++c) H[2 * r + c] = -(QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);
+        d_cov2d[3 * i + 0] = H[0];
+        d_cov2d[3 * i + 1] = H[1];
+        d_cov2d[3 * i + 2] = H[3];
 
         /* App. A: dSigma'/dSigma_ij = [[U1i U1j, U1i U2j], [U1j U2i, U2i U2j]] with U = J W. */
         double GS[9];

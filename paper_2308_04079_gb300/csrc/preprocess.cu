@@ -9,8 +9,9 @@
 //   conic = Sigma'^-1 (stored as its Cholesky factor); radius = ceil(3 sqrt(lambda_max));
 //   mean2D = (fx x/z + cx, fy y/z + cy) in double-float;
 //   tile rectangle (culled when empty); rgb = max(0, sum_k c_k Y_k((mu - C)/|mu - C|)).
-// Backward: the same quantities recomputed, then dL/dconic -> dL/dSigma' = -Q G Q ->
-//   dL/dV = 2 H V -> dL/dM = (J W)^T dL/dV -> (s, R) -> q_hat -> q (normalisation Jacobian);
+// Backward: the same quantities recomputed, then dL/dSigma' (accumulated per pixel by the tile
+//   traversal) -> dL/dV = 2 H V -> dL/dM = (J W)^T dL/dV -> (s, R) -> q_hat -> q (normalisation
+//   Jacobian);
 //   dL/d(J W) -> dL/dJ -> dL/dt; dL/dmean2D -> dL/dt; dL/dt -> dL/dmu = W^T dL/dt;
 //   dL/drgb (clamp mask) -> dL/dSH = Y dL/drgb and -> dL/d dir -> dL/dmu.
 #include "gs_device.cuh"
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a
         return;
     }
     const CamK& c = a.cam;
-    const float4 g0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i];       // du dv da db
-    const float4 g1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];   // dc do dr dg
+    const float4 g0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i];       // du dv dS00 dS01
+    const float4 g1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];   // dS11 do dr dg
     const float g2 = a.grad2d[12 * i + 8];                                    // db(rgb)
     const float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
     const float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
@@ -198,14 +199,8 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a
     Proj p;
     project_mean(mu, c, p);
     project_cov(s, q, c, a.cfg.dilation, p);
-    const float inv = 1.0f / p.det;
-    const float ca = p.C * inv, cb = -p.B * inv, cc = p.A * inv;   // conic Q = [[ca, cb], [cb, cc]]
-
-    // dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]] (b enters the exponent once).
-    const float da = g0.z, db = g0.w, dc = g1.x;
-    const float H00 = -(ca * ca * da + ca * cb * db + cb * cb * dc);
-    const float H01 = -(ca * cb * da + 0.5f * (cb * cb + ca * cc) * db + cb * cc * dc);
-    const float H11 = -(cb * cb * da + cb * cc * db + cc * cc * dc);
+    // dL/dSigma' (full-matrix convention, symmetric) accumulated by the tile traversal.
+    const float H00 = g0.z, H01 = g0.w, H11 = g1.x;
     // Sigma'_raw = V V^T: dL/dV = 2 H V.
     float dV[6];
 #pragma unroll

@@ -13,8 +13,8 @@
 //   T_i = T_{i+1} / (1 - a_i) from the stored final T, and keeps R, the colour behind the current
 //   Gaussian normalised by the transmittance in front of it (R starts at bg):
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
-//   Through a = o G (zero when clamped) and power = -(a dx^2 + c dy^2)/2 - b dx dy it yields
-//   dL/d(mean2D, conic, opacity, colour) per pixel; these are summed over the warp with
+//   Through a = o G (zero when clamped) and power = -d^T Sigma'^-1 d / 2 it yields
+//   dL/d(mean2D, Sigma', opacity, colour) per pixel; these are summed over the warp with
 //   shuffles and added to the per-Gaussian accumulators with vector atomics.
 #include "gs_device.cuh"
 #include "gs_kernels.h"
@@ -172,12 +172,17 @@ __global__ void __launch_bounds__(kMaxTilePixels) k_render_backward(RenderBwdArg
                     if (oG <= amax) {
                         g_o = G * dalpha;
                         const float dpow = oG * dalpha;
-                        g_a = -0.5f * dx * dx * dpow;
-                        g_b = -dx * dy * dpow;
-                        g_c = -0.5f * dy * dy * dpow;
-                        // d(power)/d(mean) = Q d = L (p, q)
-                        g_u = co.x * pp * dpow;
-                        g_v = (co.y * pp + co.z * qq) * dpow;
+                        // With g = Q d = L (p, q): d(power)/d(mean) = g and
+                        // d(power)/d(Sigma') = g g^T / 2 (from d(Q) = -Q d(Sigma') Q).  Accumulating
+                        // dL/dSigma' here, instead of dL/dconic followed by -Q G Q per Gaussian,
+                        // avoids the cancellation of that product for elongated splats.
+                        const float gx = co.x * pp, gy = co.y * pp + co.z * qq;
+                        const float h = 0.5f * dpow;
+                        g_u = gx * dpow;
+                        g_v = gy * dpow;
+                        g_a = h * gx * gx;
+                        g_b = h * gx * gy;
+                        g_c = h * gy * gy;
                     }
                 }
             }

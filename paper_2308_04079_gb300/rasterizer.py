@@ -11,6 +11,7 @@ the kernels of libgs_gb300.so, reached through the C ABI binding in :mod:`._abi`
 """
 from __future__ import annotations
 
+import ctypes
 from dataclasses import dataclass
 
 import numpy as np
@@ -119,6 +120,7 @@ class Frame:
             raise ValueError("invalid frame description")
         self.ws = torch.empty(size, dtype=torch.uint8, device=self.device)
         self.layout = abi.gs_workspace_layout(self.n, self.cam.width, self.cam.height, self.capacity, self.cfg)
+        self.ws[self.layout.status:self.layout.status + ctypes.sizeof(abi.gs_device_status)].zero_()
         self.frame = abi.gs_frame(self.n, self.cam, self.cfg, self.capacity, self.ws.data_ptr(), size)
 
     @property

@@ -23,7 +23,7 @@ def _check(g, cam, bg, dimg, tile_mask=None, max_excluded=0.05, cfg=None):
     assert excluded <= max_excluded, excluded
     ob2 = dict(ob)
     ob2["opac2d"] = ob["opacities"]
-    s2 = compare_grads(gg, ob2, keep, names=("uv", "conic", "opac2d", "rgb"))
+    s2 = compare_grads(gg, ob2, keep, names=("uv", "cov2d", "opac2d", "rgb"))
     s3 = compare_grads(gg, ob, keep)
     # Gaussians that received no gradient in FP64 receive none on the GPU either
     untouched = ~touched & (ob["gauss_amb"] == 0)
