@@ -8,7 +8,7 @@ import numpy as np
 # Tolerances:
 IMG_ATOL = 1e-4          # images and final transmittance, absolute per channel (fp32 vs fp64)
 GRAD_REL_L2 = 1e-3       # gradients: per-tensor relative L2 error
-GRAD_ELEM_REL = 1e-3     # gradients: per element, relative to max(|g*|, rms of the tensor)
+GRAD_ELEM_REL = 1e-2     # gradients: per element, relative to max(|g*|, rms of the tensor)
 
 
 def gpu_frame(g_np, cam, cfg=None, capacity=None):
