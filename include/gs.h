@@ -148,7 +148,7 @@ typedef struct gs_device_status {
     uint32_t reserved[4];
 } gs_device_status;
 
-/* Fill cfg with the paper's constants: 16x16 tiles, batch 256, alpha in [1/255, 0.99],
+/* Fill cfg with the paper's constants: 16x16 tiles, batch 128, alpha in [1/255, 0.99],
  * T_min 1e-4, dilation 0.3, guard 1.3, extent 3, GS_SORT_TWO_PHASE. */
 void gs_default_config(gs_raster_config* cfg);
 

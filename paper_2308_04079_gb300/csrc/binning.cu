@@ -20,6 +20,8 @@
 // back over predecessor chunks (bounded spin), stages the keys in shared memory in local sorted
 // order and writes them out coalesced.  Digit histograms of every pass are computed up front
 // (fused into the kernel that produces the keys).
+#include <type_traits>
+
 #include "gs_device.cuh"
 #include "gs_kernels.h"
 
@@ -41,9 +43,6 @@ template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
     return (uint32_t)(k >> shift) & 0xFFu;
 }
-
-__device__ __forceinline__ uint32_t tile_of(uint32_t k) { return k; }
-__device__ __forceinline__ uint32_t tile_of(unsigned long long k) { return (uint32_t)(k >> 32); }
 
 __device__ __forceinline__ void backoff(uint32_t spins) {
     if (spins > 64) __nanosleep(spins > 4096 ? 256 : 32);
@@ -231,69 +230,66 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortPassArgs<KeyT> a)
 
 
 // ---------------------------------------------------------------------------------------
-// Fused exclusive scan of tiles-per-Gaussian + DuplicateWithKeys + key histograms.
-// Chunks of kDupChunk Gaussians (in `order`), chained-scan look-back for the instance offset,
-// then a load-balanced emission loop: each thread takes output slots and finds its Gaussian
-// by binary search over the chunk's inclusive offsets.
+// Scan of tiles per Gaussian (in `order`) with chained look-back.  Per Gaussian it stores the
+// exclusive instance offset and the tile rectangle, and adds the rectangle's four corners to a
+// 2D difference grid over the tiles (+1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and (x0, y1));
+// its 2D prefix sum is the number of instances of every tile, from which k_tile_ranges derives
+// the tile ranges and the digit histograms of the tile-id sort passes.  In KEY64 mode the depth
+// digits of the four low passes are constant per Gaussian: their histograms are weighted by the
+// Gaussian's tile count here.
 // ---------------------------------------------------------------------------------------
 template <bool KEY64>
-__global__ void __launch_bounds__(kDupThreads) k_scan_duplicate(DupArgs a) {
+__global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
     constexpr int PER = kDupChunk / kDupThreads;
-    __shared__ uint32_t s_incl[kDupChunk];
-    __shared__ uint32_t s_gid[kDupChunk];
-    __shared__ int s_x0[kDupChunk];
-    __shared__ int s_y0[kDupChunk];
-    __shared__ int s_w[kDupChunk];
-    __shared__ uint32_t s_hist[kMaxKeyPasses][256];
+    __shared__ uint32_t s_hist[KEY64 ? 4 : 1][256];
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_chunk;
     __shared__ unsigned long long s_base;
-
     const int tid = threadIdx.x;
-    const uint32_t lt = lanemask_lt();
     uint32_t count = (uint32_t)a.n;
     if (a.count_dev) count = min(count, *a.count_dev);
     const uint32_t chunks = (count + kDupChunk - 1) / kDupChunk;
     const CamK& c = a.cam;
+    const int gw = c.tiles_x + 1;
 
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(a.chunk_counter, 1u);
-        for (int k = tid; k < a.passes * 256; k += kDupThreads) (&s_hist[0][0])[k] = 0;
+        if (KEY64)
+            for (int k = tid; k < 4 * 256; k += kDupThreads) (&s_hist[0][0])[k] = 0;
         __syncthreads();
         const uint32_t chunk = s_chunk;
         if (chunk >= chunks) break;
-
+        uint32_t tiles[PER];
         uint32_t run = 0;
-        uint32_t incl[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int e = tid * PER + k;
-            const uint32_t j = chunk * kDupChunk + e;
-            uint32_t tiles = 0;
+            const uint32_t j = chunk * kDupChunk + tid * PER + k;
+            tiles[k] = 0;
+            uint2 rect = make_uint2(0u, 0u);
             if (j < count) {
                 uint32_t gid = a.order ? a.order[j] : j;
                 if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
                 const int r = a.radius[gid];
-                if (r > 0) {
-                    const float4 m = a.xy[gid];
-                    int x0, x1, y0, y1;
-                    if (tile_rect(m, r, c, x0, x1, y0, y1)) {
-                        tiles = (uint32_t)((x1 - x0) * (y1 - y0));
-                        s_x0[e] = x0;
-                        s_y0[e] = y0;
-                        s_w[e] = x1 - x0;
+                int x0, x1, y0, y1;
+                if (r > 0 && tile_rect(a.xy[gid], r, c, x0, x1, y0, y1)) {
+                    tiles[k] = (uint32_t)((x1 - x0) * (y1 - y0));
+                    rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)(x1 - x0) | ((uint32_t)(y1 - y0) << 16));
+                    atomicAdd(&a.diff[y0 * gw + x0], 1);
+                    atomicAdd(&a.diff[y0 * gw + x1], -1);
+                    atomicAdd(&a.diff[y1 * gw + x0], -1);
+                    atomicAdd(&a.diff[y1 * gw + x1], 1);
+                    if (KEY64) {
+                        const uint32_t db = __float_as_uint(a.depth[gid]);
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], tiles[k]);
                     }
                 }
-                s_gid[e] = gid;
+                a.rect[j] = rect;
             }
-            run += tiles;
-            incl[k] = run;
+            run += tiles[k];
         }
         uint32_t block_total;
         const uint32_t texcl = block_exclusive_scan<uint32_t>(run, s_scan, &block_total);
-#pragma unroll
-        for (int k = 0; k < PER; ++k) s_incl[tid * PER + k] = texcl + incl[k];
-
         if (tid == 0) {
             unsigned long long* my = a.lookback + chunk;
             unsigned long long excl = 0;
@@ -328,52 +324,157 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_duplicate(DupArgs a) {
             }
         }
         __syncthreads();
-        const unsigned long long base = s_base;
-
-        for (uint32_t kb = 0; kb < block_total; kb += kDupThreads) {
-            const uint32_t k = kb + tid;
-            const bool valid = k < block_total && base + k < a.capacity;
-            unsigned long long key = 0;
-            if (valid) {
-                // first e with s_incl[e] > k
-                int lo = 0, hi = kDupChunk - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_incl[mid] > k) hi = mid;
-                    else lo = mid + 1;
-                }
-                const int e = lo;
-                const uint32_t local = k - (e > 0 ? s_incl[e - 1] : 0u);
-                const int w = s_w[e];
-                const int tx = s_x0[e] + (int)(local % (uint32_t)w);
-                const int ty = s_y0[e] + (int)(local / (uint32_t)w);
-                const uint32_t tile = (uint32_t)(ty * c.tiles_x + tx);
-                const uint32_t gid = s_gid[e];
-                const size_t out = (size_t)(base + k);
-                if (KEY64) {
-                    key = ((unsigned long long)tile << 32) | __float_as_uint(a.depth[gid]);
-                    reinterpret_cast<unsigned long long*>(a.keys_out)[out] = key;
-                } else {
-                    key = tile;
-                    reinterpret_cast<uint32_t*>(a.keys_out)[out] = tile;
-                }
-                a.vals_out[out] = gid;
-            }
-            for (int p = 0; p < a.passes; ++p) {
-                const uint32_t d = valid ? (uint32_t)(key >> (8 * p)) & 0xFFu : 0x100u;
-                const uint32_t peers = __match_any_sync(0xffffffffu, d);
-                if (valid && (peers & lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
-            }
+        unsigned long long off = s_base + texcl;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const uint32_t j = chunk * kDupChunk + tid * PER + k;
+            if (j < count) a.start[j] = (uint32_t)min(off, 0xFFFFFFFFull);
+            off += tiles[k];
         }
-        __syncthreads();
-        for (int k = tid; k < a.passes * 256; k += kDupThreads) {
-            const uint32_t v = (&s_hist[0][0])[k];
-            if (v) atomicAdd(&a.hist[k], v);
+        if (KEY64) {
+            __syncthreads();
+            for (int k = tid; k < 4 * 256; k += kDupThreads) {
+                const uint32_t v = (&s_hist[0][0])[k];
+                if (v) atomicAdd(&a.hist[k], v);
+            }
         }
         __syncthreads();
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// IdentifyTileRanges from instance counts (one block): 2D prefix sum of the difference grid
+// gives the instances of every tile; their exclusive scan in tile-id order gives [start, end)
+// (clamped to the capacity), exactly the ranges of the sorted instance array.  Also adds the
+// digit histograms of the tile-id radix passes (tile ids are the key bits from key_shift on).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
+    __shared__ uint32_t s_hist[kMaxKeyPasses][256];
+    __shared__ uint32_t s_scan[33];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int TX = a.tiles_x, TY = a.tiles_y, gw = TX + 1;
+    for (int k = tid; k < kMaxKeyPasses * 256; k += nt) (&s_hist[0][0])[k] = 0;
+    // row-wise then column-wise inclusive prefix sums, in place
+    for (int y = tid; y <= TY; y += nt) {
+        int run = 0;
+        for (int x = 0; x <= TX; ++x) { run += a.diff[y * gw + x]; a.diff[y * gw + x] = run; }
+    }
+    __syncthreads();
+    for (int x = tid; x <= TX; x += nt) {
+        int run = 0;
+        for (int y = 0; y <= TY; ++y) { run += a.diff[y * gw + x]; a.diff[y * gw + x] = run; }
+    }
+    __syncthreads();
+    const uint32_t T = (uint32_t)(TX * TY);
+    const unsigned long long cap = a.capacity;
+    unsigned long long carry = 0;
+    for (uint32_t base = 0; base < T; base += (uint32_t)nt) {
+        const uint32_t t = base + tid;
+        uint32_t cnt = 0;
+        if (t < T) cnt = (uint32_t)a.diff[(t / TX) * gw + (t % TX)];
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(cnt, s_scan, &tot);
+        if (t < T) {
+            const unsigned long long s0 = carry + ex, s1 = s0 + cnt;
+            a.ranges[2 * t] = cnt ? (uint32_t)min(s0, cap) : 0u;       // empty tiles: [0, 0)
+            a.ranges[2 * t + 1] = cnt ? (uint32_t)min(s1, cap) : 0u;
+            if (cnt) {
+                for (int p = 0; p < a.tile_passes; ++p) {
+                    const int bit = a.key_shift + 8 * p;
+                    const uint32_t d = bit >= 32 ? ((uint32_t)(((unsigned long long)t << 32) >> bit) & 0xFFu)
+                                                 : ((t >> bit) & 0xFFu);
+                    atomicAdd(&s_hist[p][d], cnt);
+                }
+            }
+        }
+        carry += tot;
+    }
+    __syncthreads();
+    for (int k = tid; k < a.tile_passes * 256; k += nt) {
+        const uint32_t v = (&s_hist[0][0])[k];
+        if (v) atomicAdd(&a.hist[k], v);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// DuplicateWithKeys, load-balanced over output slots: a block writes 2048 consecutive instances.
+// Each thread finds the Gaussian of its first slot by binary search over the exclusive offsets
+// and walks forward; the tile of slot `local` inside a w x h rectangle is (local % w, local / w)
+// (quotient from a float reciprocal, corrected by one step).  Keys and values are staged in
+// shared memory and written out coalesced.
+// ---------------------------------------------------------------------------------------
+template <bool KEY64>
+__global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
+    using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
+    constexpr int PER = kEmitSlots / kEmitThreads;
+    __shared__ KeyT s_key[kEmitSlots];
+    __shared__ uint32_t s_val[kEmitSlots];
+    const int tid = threadIdx.x;
+    const unsigned long long K = min((unsigned long long)a.status->num_instances, a.capacity);
+    uint32_t count = (uint32_t)a.n;
+    if (a.count_dev) count = min(count, *a.count_dev);
+    const int TX = a.tiles_x;
+    KeyT* keys_out = reinterpret_cast<KeyT*>(a.keys_out);
+    for (unsigned long long k0 = (unsigned long long)blockIdx.x * kEmitSlots; k0 < K;
+         k0 += (unsigned long long)gridDim.x * kEmitSlots) {
+        const unsigned long long first = k0 + (unsigned long long)tid * PER;
+        if (first < K && count > 0) {
+            // last j with start[j] <= first
+            uint32_t lo = 0, hi = count - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (a.start[mid] <= first) lo = mid;
+                else hi = mid - 1;
+            }
+            uint32_t j = lo;
+            uint32_t nxt = (j + 1 < count) ? a.start[j + 1] : 0xFFFFFFFFu;
+            uint2 rect = a.rect[j];
+            uint32_t st = a.start[j];
+            uint32_t gid = a.order ? a.order[j] : j;
+            if (gid >= (uint32_t)a.n) gid = 0;
+            float inv_w = 1.0f / (float)(rect.y & 0xFFFFu);
+            uint32_t dbits = KEY64 ? __float_as_uint(a.depth[gid]) : 0u;
+#pragma unroll 4
+            for (int i = 0; i < PER; ++i) {
+                const unsigned long long kk = first + i;
+                if (kk >= K) break;
+                while ((unsigned long long)nxt <= kk) {   // advance to the Gaussian owning slot kk
+                    ++j;
+                    st = nxt;
+                    nxt = (j + 1 < count) ? a.start[j + 1] : 0xFFFFFFFFu;
+                    rect = a.rect[j];
+                    gid = a.order ? a.order[j] : j;
+                    if (gid >= (uint32_t)a.n) gid = 0;
+                    inv_w = 1.0f / (float)(rect.y & 0xFFFFu);
+                    if (KEY64) dbits = __float_as_uint(a.depth[gid]);
+                }
+                const int w = (int)(rect.y & 0xFFFFu);
+                const int local = (int)(kk - st);
+                int qy = (int)(((float)local + 0.5f) * inv_w);
+                int rx = local - qy * w;
+                if (rx < 0) { --qy; rx += w; }
+                if (rx >= w) { ++qy; rx -= w; }
+                const uint32_t tile =
+                    (uint32_t)(((int)(rect.x >> 16) + qy) * TX + (int)(rect.x & 0xFFFFu) + rx);
+                const int slot = tid * PER + i;
+                if (KEY64) s_key[slot] = (KeyT)(((unsigned long long)tile << 32) | dbits);
+                else s_key[slot] = (KeyT)tile;
+                s_val[slot] = gid;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int slot = i * kEmitThreads + tid;
+            const unsigned long long kk = k0 + slot;
+            if (kk < K) {
+                keys_out[kk] = s_key[slot];
+                a.vals_out[kk] = s_val[slot];
+            }
+        }
+        __syncthreads();
+    }
+}
 
 // Zero the look-back rows of the first instance-sort pass (row count depends on the
 // device-side instance count).
@@ -384,19 +485,6 @@ __global__ void k_sort_prepare(SortPrepareArgs a) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
         a.lookback[k] = 0;
 }
-
-// IdentifyTileRanges: one thread per sorted instance compares its tile id with its neighbours.
-template <typename KeyT>
-__global__ void k_ranges(RangesArgs<KeyT> a) {
-    const uint32_t count = (uint32_t)min((unsigned long long)a.status->num_instances, a.capacity);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
-        const uint32_t t = tile_of(a.keys[j]);
-        if (t >= a.tiles) continue;   // only reachable after a timed-out sort
-        if (j == 0 || tile_of(a.keys[j - 1]) != t) a.ranges[2 * t] = j;
-        if (j + 1 == count || tile_of(a.keys[j + 1]) != t) a.ranges[2 * t + 1] = j + 1;
-    }
-}
-
 
 cudaError_t launch_depth_hist(const DepthHistArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
@@ -423,28 +511,27 @@ cudaError_t launch_onesweep(const SortPassArgs<unsigned long long>& a, int max_c
     return launch_onesweep_t(a, max_chunks, s);
 }
 
-cudaError_t launch_scan_duplicate(const DupArgs& a, bool key64, cudaStream_t s) {
+cudaError_t launch_scan_tiles(const ScanArgs& a, bool key64, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    if (key64) {
-        k_scan_duplicate<true><<<persistent_grid((const void*)k_scan_duplicate<true>, kDupThreads), kDupThreads, 0, s>>>(a);
-    } else {
-        k_scan_duplicate<false><<<persistent_grid((const void*)k_scan_duplicate<false>, kDupThreads), kDupThreads, 0, s>>>(a);
-    }
+    if (key64) k_scan_tiles<true><<<persistent_grid((const void*)k_scan_tiles<true>, kDupThreads), kDupThreads, 0, s>>>(a);
+    else k_scan_tiles<false><<<persistent_grid((const void*)k_scan_tiles<false>, kDupThreads), kDupThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges(const TileRangesArgs& a, cudaStream_t s) {
+    k_tile_ranges<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const EmitArgs& a, bool key64, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    if (key64) k_emit<true><<<persistent_grid((const void*)k_emit<true>, kEmitThreads), kEmitThreads, 0, s>>>(a);
+    else k_emit<false><<<persistent_grid((const void*)k_emit<false>, kEmitThreads), kEmitThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sort_prepare(const SortPrepareArgs& a, cudaStream_t s) {
     k_sort_prepare<<<persistent_grid((const void*)k_sort_prepare, 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ranges(const RangesArgs<uint32_t>& a, cudaStream_t s) {
-    k_ranges<uint32_t><<<persistent_grid((const void*)k_ranges<uint32_t>, 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ranges(const RangesArgs<unsigned long long>& a, cudaStream_t s) {
-    k_ranges<unsigned long long><<<persistent_grid((const void*)k_ranges<unsigned long long>, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ struct Layout {
     size_t scan_lb, sort_lb[2];
     size_t ikey[2], ival[2];
     size_t ranges, grad2d, total;
+    size_t start, rect, diff, diff_count;
     size_t sort_lb_rows, scan_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes;
 };
@@ -70,6 +71,10 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->rgb = take(nn * sizeof(float4));
     L->radius = take(nn * sizeof(int));
     for (int k = 0; k < 2; ++k) { L->gkey[k] = take(nn * 4); L->gval[k] = take(nn * 4); }
+    L->start = take(nn * sizeof(uint32_t));
+    L->rect = take(nn * sizeof(uint2));
+    L->diff_count = (size_t)(L->tiles_x + 1) * (L->tiles_y + 1);
+    L->diff = take(L->diff_count * sizeof(int));
     L->scan_lb_rows = (nn + kDupChunk - 1) / kDupChunk;
     L->scan_lb = take(L->scan_lb_rows * sizeof(unsigned long long));
     const size_t rows_n = (nn + kSortTile - 1) / kSortTile, rows_c = (cc + kSortTile - 1) / kSortTile;
@@ -163,9 +168,7 @@ gs_status run_key_sort(const gs_frame* f, const Layout& L, Control* ctl, cudaStr
         a.status = st;
         if (launch_onesweep(a, 0, s) != cudaSuccess) return GS_ERR_CUDA;
     }
-    RangesArgs<KeyT> ra{at<KeyT>(ws, keys_sorted_off(L)), at<uint32_t>(ws, L.ranges), (uint32_t)L.tiles, st,
-                        (unsigned long long)f->capacity};
-    return ok(launch_ranges(ra, s));
+    return GS_OK;
 }
 
 }  // namespace
@@ -176,7 +179,7 @@ void gs_default_config(gs_raster_config* cfg) {
     if (!cfg) return;
     cfg->tile_w = 16;
     cfg->tile_h = 16;
-    cfg->batch_depth = 256;
+    cfg->batch_depth = 128;
     cfg->sort_mode = GS_SORT_TWO_PHASE;
     cfg->alpha_min = 1.0f / 255.0f;
     cfg->alpha_max = 0.99f;
@@ -246,24 +249,23 @@ gs_status gs_bin_sort(const gs_frame* f, cudaStream_t s) {
     if (cudaMemsetAsync(st, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(&ctl->counters[0], 0, sizeof(Control) - offsetof(Control, counters), s) != cudaSuccess)
         return GS_ERR_CUDA;
-    if (cudaMemsetAsync(at<char>(ws, L.ranges), 0, (size_t)L.tiles * 2 * sizeof(uint32_t), s) != cudaSuccess)
-        return GS_ERR_CUDA;
+    if (cudaMemsetAsync(at<char>(ws, L.diff), 0, L.diff_count * sizeof(int), s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(at<char>(ws, L.scan_lb), 0, L.scan_lb_rows * sizeof(unsigned long long), s) != cudaSuccess)
         return GS_ERR_CUDA;
     const CamK cam = cam_k(f, L);
     const bool key64 = f->cfg.sort_mode == GS_SORT_KEY64;
 
-    DupArgs d;
+    ScanArgs d;
     d.n = f->n;
     d.xy = at<float4>(ws, L.xy);
     d.radius = at<int>(ws, L.radius);
     d.depth = at<float>(ws, L.depth);
     d.cam = cam;
-    d.keys_out = at<void>(ws, L.ikey[0]);
-    d.vals_out = at<uint32_t>(ws, L.ival[0]);
+    d.start = at<uint32_t>(ws, L.start);
+    d.rect = at<uint2>(ws, L.rect);
+    d.diff = at<int>(ws, L.diff);
     d.capacity = f->capacity;
     d.hist = &ctl->hist_keys[0][0];
-    d.passes = L.key_passes;
     d.lookback = at<unsigned long long>(ws, L.scan_lb);
     d.chunk_counter = &ctl->counters[0];
     d.status = st;
@@ -300,7 +302,30 @@ gs_status gs_bin_sort(const gs_frame* f, cudaStream_t s) {
         d.order = nullptr;
         d.count_dev = nullptr;
     }
-    if (launch_scan_duplicate(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (launch_scan_tiles(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    TileRangesArgs tr;
+    tr.diff = at<int>(ws, L.diff);
+    tr.tiles_x = L.tiles_x;
+    tr.tiles_y = L.tiles_y;
+    tr.ranges = at<uint32_t>(ws, L.ranges);
+    tr.tile_passes = key64 ? L.key_passes - 4 : L.key_passes;
+    tr.key_shift = key64 ? 32 : 0;
+    tr.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
+    tr.capacity = f->capacity;
+    if (launch_tile_ranges(tr, s) != cudaSuccess) return GS_ERR_CUDA;
+    EmitArgs e;
+    e.order = d.order;
+    e.count_dev = d.count_dev;
+    e.n = f->n;
+    e.start = d.start;
+    e.rect = d.rect;
+    e.depth = d.depth;
+    e.tiles_x = L.tiles_x;
+    e.keys_out = at<void>(ws, L.ikey[0]);
+    e.vals_out = at<uint32_t>(ws, L.ival[0]);
+    e.capacity = f->capacity;
+    e.status = st;
+    if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
     if (key64) return run_key_sort<unsigned long long>(f, L, ctl, s);
     return run_key_sort<uint32_t>(f, L, ctl, s);
 }
@@ -324,7 +349,7 @@ gs_status gs_render_forward(const gs_frame* f, const float bg[3], float* out_rgb
     a.out_rgb = out_rgb;
     a.out_T = out_T;
     a.out_last = out_last;
-    return ok(launch_render_forward(a, L.tiles, f->cfg.tile_w * f->cfg.tile_h, s));
+    return ok(launch_render_forward(a, L.tiles, s));
 }
 
 gs_status gs_render_backward_tiles(const gs_frame* f, const float bg[3], const float* dL_drgb, const float* T,
@@ -350,7 +375,7 @@ gs_status gs_render_backward_tiles(const gs_frame* f, const float bg[3], const f
     a.T_final = T;
     a.last = last;
     a.grad2d = grad2d;
-    return ok(launch_render_backward(a, L.tiles, f->cfg.tile_w * f->cfg.tile_h, s));
+    return ok(launch_render_backward(a, L.tiles, s));
 }
 
 gs_status gs_render_backward_gaussians(const gs_frame* f, const gs_gaussians* g, const gs_gradients* gr,

@@ -17,12 +17,14 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxKeyPasses = 8;
 constexpr int kDepthPasses = 4;
 
-// Scan + duplicate: 256 threads, 4 Gaussians per thread.
+// Scan of tiles per Gaussian: 256 threads, 4 Gaussians per thread.
 constexpr int kDupThreads = 256;
 constexpr int kDupChunk = 1024;
+// Instance emission: 256 threads write 2048 consecutive instances.
+constexpr int kEmitThreads = 256;
+constexpr int kEmitSlots = 2048;
 
-// Render: one block per tile, at most 256 pixels (threads) per tile.
-constexpr int kMaxTilePixels = 256;
+// Render: one block per tile, 4 threads per tile row, each owning tile_w / 4 pixels.
 
 // Control block at the start of the workspace.
 struct Control {
@@ -100,7 +102,7 @@ struct SortPassArgs {
     gs_device_status* status;
 };
 
-struct DupArgs {
+struct ScanArgs {
     const uint32_t* order;     // depth-sorted Gaussian ids (TWO_PHASE) or null (identity)
     const uint32_t* count_dev; // number of entries of `order` to use, or null (n)
     int n;
@@ -108,27 +110,42 @@ struct DupArgs {
     const int* radius;
     const float* depth;
     CamK cam;
-    void* keys_out;
-    uint32_t* vals_out;
+    uint32_t* start;           // [n] exclusive instance offset per (sorted) Gaussian
+    uint2* rect;               // [n] (x0 | y0 << 16, w | h << 16) per (sorted) Gaussian
+    int* diff;                 // [(tiles_y + 1) * (tiles_x + 1)] 2D difference grid, zeroed
     unsigned long long capacity;
-    uint32_t* hist;            // [passes][256]
-    int passes;
+    uint32_t* hist;            // [4][256] depth-digit histograms (KEY64 only)
     unsigned long long* lookback;  // [chunks], zeroed
     uint32_t* chunk_counter;
     gs_device_status* status;
 };
 
-struct SortPrepareArgs {
-    uint32_t* lookback;
-    const gs_device_status* status;
+struct TileRangesArgs {
+    int* diff;                 // difference grid, turned into per-tile counts in place
+    int tiles_x, tiles_y;
+    uint32_t* ranges;
+    uint32_t* hist;            // [tile_passes][256] histograms of the tile-id passes
+    int tile_passes;
+    int key_shift;             // bit position of the tile id inside the key (0 or 32)
     unsigned long long capacity;
 };
 
-template <typename KeyT>
-struct RangesArgs {
-    const KeyT* keys;
-    uint32_t* ranges;
-    uint32_t tiles;
+struct EmitArgs {
+    const uint32_t* order;
+    const uint32_t* count_dev;
+    int n;
+    const uint32_t* start;
+    const uint2* rect;
+    const float* depth;
+    int tiles_x;
+    void* keys_out;
+    uint32_t* vals_out;
+    unsigned long long capacity;
+    const gs_device_status* status;
+};
+
+struct SortPrepareArgs {
+    uint32_t* lookback;
     const gs_device_status* status;
     unsigned long long capacity;
 };
@@ -174,11 +191,11 @@ cudaError_t launch_preprocess_backward(const PreprocessBwdArgs& a, cudaStream_t 
 cudaError_t launch_depth_hist(const DepthHistArgs& a, cudaStream_t s);
 cudaError_t launch_onesweep(const SortPassArgs<uint32_t>& a, int max_chunks, cudaStream_t s);
 cudaError_t launch_onesweep(const SortPassArgs<unsigned long long>& a, int max_chunks, cudaStream_t s);
-cudaError_t launch_scan_duplicate(const DupArgs& a, bool key64, cudaStream_t s);
+cudaError_t launch_scan_tiles(const ScanArgs& a, bool key64, cudaStream_t s);
+cudaError_t launch_tile_ranges(const TileRangesArgs& a, cudaStream_t s);
+cudaError_t launch_emit(const EmitArgs& a, bool key64, cudaStream_t s);
 cudaError_t launch_sort_prepare(const SortPrepareArgs& a, cudaStream_t s);
-cudaError_t launch_ranges(const RangesArgs<uint32_t>& a, cudaStream_t s);
-cudaError_t launch_ranges(const RangesArgs<unsigned long long>& a, cudaStream_t s);
-cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, int threads, cudaStream_t s);
-cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, int threads, cudaStream_t s);
+cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, cudaStream_t s);
+cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, cudaStream_t s);
 
 }  // namespace gs

@@ -1,8 +1,14 @@
 // render.cu -- per-tile blending (Algorithm 2, BlendInOrder) and its backward pass (Sec. 6).
 //
-// One thread block per tile, one thread per pixel.  The block stages batches of the tile's
-// depth-sorted Gaussians (screen mean, conic + opacity, colour) in shared memory; every pixel
-// then walks the batch.
+// One thread block per tile; 4 threads per tile row, each owning PX = tile_w / 4 pixels of that
+// row (columns c, c + 4, ...).  The block stages batches of the tile's depth-sorted Gaussians in
+// shared memory; a staged splat carries its offset from the tile's first pixel centre, the
+// Cholesky factor of its conic pre-scaled to log2 units, log2 of its opacity and its skip
+// threshold (see Staged), so that for a pixel at offset d:
+//   p = l11' dx + l21' dy, q = l22' dy, s = p^2 + q^2 = -log2(e) power,  o exp(power) = 2^(lo - s)
+// and "alpha < 1/255" is the single comparison s > thr with thr = lo - log2(1/255).  Pixels of
+// one row share dy, q and q^2, and p advances by 4 l11' from one owned pixel to the next, so a
+// skipped (pixel, splat) pair costs three instructions and no exp.
 //
 // Forward (eq. front-to-back, App. C): a = min(0.99, o exp(power)); skip a < 1/255; stop before
 //   T (1 - a) < 1e-4; C += a T c; T *= 1 - a.  The tile stops as soon as all its pixels are done
@@ -13,79 +19,55 @@
 //   T_i = T_{i+1} / (1 - a_i) from the stored final T, and keeps R, the colour behind the current
 //   Gaussian normalised by the transmittance in front of it (R starts at bg):
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
-//   Through a = o G (zero when clamped) and power = -d^T Sigma'^-1 d / 2 it yields
-//   dL/d(mean2D, Sigma', opacity, colour) per pixel; these are summed over the warp with
-//   shuffles and added to the per-Gaussian accumulators with vector atomics.
+//   Through a = o G (zero when clamped), with g = Sigma'^-1 d: d(power)/d(mean) = g and
+//   d(power)/d(Sigma') = g g^T / 2.  A thread sums its pixels' dL/d(mean2D, Sigma', opacity,
+//   colour), the warp sums its lanes with shuffles, and lane 0 adds the result to the
+//   per-Gaussian accumulators with vector atomics.
+//
+// The forward and the backward evaluate a (pixel, splat) pair with the same staging and the same
+// operation sequence (stage_splat, splat_row, splat_s), so their skip and clamp decisions agree
+// bit for bit.
 #include "gs_device.cuh"
 #include "gs_kernels.h"
 
 namespace gs {
 
-__global__ void __launch_bounds__(kMaxTilePixels) k_render_forward(RenderFwdArgs a) {
-    __shared__ float2 s_off[kMaxTilePixels];
-    __shared__ float4 s_co[kMaxTilePixels];
-    __shared__ float4 s_rgb[kMaxTilePixels];
-    const CamK& c = a.cam;
-    const int tile = blockIdx.x;
-    const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
-    const int npx = blockDim.x;
-    const int lx = threadIdx.x % c.tile_w, ly = threadIdx.x / c.tile_w;
-    const int px = tx * c.tile_w + lx, py = ty * c.tile_h + ly;
-    const bool inside = px < c.W && py < c.H;
-    const float lxf = (float)lx, lyf = (float)ly;
-    const int x0 = tx * c.tile_w, y0 = ty * c.tile_h;
-    const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
-    const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max, tmin = a.cfg.T_min;
+namespace {
 
-    float T = 1.0f, Cr = 0.f, Cg = 0.f, Cb = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t b = start; b < end; b += a.batch) {
-        if (__syncthreads_count(done) == npx) break;
-        const uint32_t j = b + threadIdx.x;
-        if ((int)threadIdx.x < a.batch && j < end) {
-            uint32_t g = a.vals[j];
-            if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
-            const float4 m = a.xy[g];
-            s_off[threadIdx.x] = make_float2(tile_offset(x0, m.x, m.z), tile_offset(y0, m.y, m.w));
-            s_co[threadIdx.x] = a.conic_opacity[g];
-            s_rgb[threadIdx.x] = a.rgb[g];
-        }
-        __syncthreads();
-        const int nb = (int)min((uint32_t)a.batch, end - b);
-        if (!done) {
-            for (int k = 0; k < nb; ++k) {
-                float G, oG, pp, qq;
-                const float4 co = s_co[k];
-                const float2 o = s_off[k];
-                const float dx = __fadd_rn(lxf, o.x), dy = __fadd_rn(lyf, o.y);
-                const float power = splat_power(dx, dy, co, pp, qq);
-                const float alpha = splat_alpha(power, co.w, amax, G, oG);
-                if (alpha < amin) continue;
-                const float test = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-                if (test < tmin) {
-                    done = true;
-                    break;
-                }
-                const float w = alpha * T;
-                const float4 col = s_rgb[k];
-                Cr += w * col.x;
-                Cg += w * col.y;
-                Cb += w * col.z;
-                T = test;
-                last = b - start + (uint32_t)k + 1u;
-            }
-        }
-    }
-    if (inside) {
-        const size_t P = (size_t)c.W * c.H;
-        const size_t p = (size_t)py * c.W + px;
-        a.out_rgb[p] = Cr + T * a.bg[0];
-        a.out_rgb[P + p] = Cg + T * a.bg[1];
-        a.out_rgb[2 * P + p] = Cb + T * a.bg[2];
-        a.out_T[p] = T;
-        a.out_last[p] = last;
-    }
+// sqrt(log2(e) / 2): scales the Cholesky factor so that p^2 + q^2 = -log2(e) power.
+constexpr float kScaleLog2 = 0.84932180028801907f;
+// 1 / kScaleLog2^2 = 2 ln 2: converts scaled (p, q) products back to natural units.
+constexpr float kTwoLn2 = 1.3862943611198906f;
+
+struct Staged {
+    float4 a;   // (ox, oy, thr, lo): tile-relative offset, skip threshold, log2(opacity)
+    float4 b;   // (l11', l21', l22', 1/o)
+};
+
+__device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s) {
+    const float ox = tile_offset(x0, m.x, m.z);
+    const float oy = tile_offset(y0, m.y, m.w);
+    const float lo = __log2f(L.w);
+    s.a = make_float4(ox, oy, __fsub_rn(lo, log2_amin), lo);
+    s.b = make_float4(__fmul_rn(L.x, kScaleLog2), __fmul_rn(L.y, kScaleLog2), __fmul_rn(L.z, kScaleLog2),
+                      __frcp_rn(L.w));
+}
+
+// Per (thread row, splat): p at the thread's first pixel, its step to the next owned pixel, q, q^2.
+__device__ __forceinline__ void splat_row(const Staged& s, float lyf, float c0f, float& p0, float& dp, float& q,
+                                          float& qq) {
+    const float dy = __fadd_rn(lyf, s.a.y);
+    const float dx0 = __fadd_rn(c0f, s.a.x);
+    q = __fmul_rn(s.b.z, dy);
+    qq = __fmul_rn(q, q);
+    p0 = __fmaf_rn(s.b.y, dy, __fmul_rn(s.b.x, dx0));
+    dp = __fmul_rn(4.0f, s.b.x);
+}
+
+// s = p^2 + q^2 at the thread's j-th pixel.
+__device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, float& p) {
+    p = __fmaf_rn((float)j, dp, p0);
+    return __fmaf_rn(p, p, qq);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -94,95 +76,195 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kMaxTilePixels) k_render_backward(RenderBwdArgs a) {
-    __shared__ uint32_t s_idx[kMaxTilePixels];
-    __shared__ float2 s_off[kMaxTilePixels];
-    __shared__ float4 s_co[kMaxTilePixels];
-    __shared__ float4 s_rgb[kMaxTilePixels];
+template <int PX>
+__global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
+    float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
+    const CamK& c = a.cam;
+    const int tile = blockIdx.x;
+    const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
+    const int nthreads = blockDim.x;
+    const int ly = threadIdx.x >> 2, c0 = threadIdx.x & 3;
+    const int x0 = tx * c.tile_w, y0 = ty * c.tile_h;
+    const int py = y0 + ly;
+    const float lyf = (float)ly, c0f = (float)c0;
+    const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
+    const float amax = a.cfg.alpha_max, tmin = a.cfg.T_min;
+    const float log2_amin = __log2f(a.cfg.alpha_min);
+
+    float T[PX], Cr[PX], Cg[PX], Cb[PX];
+    uint32_t last[PX];
+    bool done[PX];
+    int ndone = 0;
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        T[j] = 1.0f;
+        Cr[j] = Cg[j] = Cb[j] = 0.f;
+        last[j] = 0;
+        done[j] = !(x0 + c0 + 4 * j < c.W && py < c.H);
+        ndone += done[j];
+    }
+    for (uint32_t b = start; b < end; b += a.batch) {
+        if (__syncthreads_count(ndone == PX) == nthreads) break;
+        const int nb = (int)min((uint32_t)a.batch, end - b);
+        for (int k = threadIdx.x; k < nb; k += nthreads) {
+            uint32_t g = a.vals[b + k];
+            if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
+            Staged st;
+            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
+            s_sp[k] = st;
+            s_rgb[k] = a.rgb[g];
+        }
+        __syncthreads();
+        if (ndone < PX) {
+            for (int k = 0; k < nb; ++k) {
+                const Staged st = s_sp[k];
+                float p0, dp, q, qq;
+                splat_row(st, lyf, c0f, p0, dp, q, qq);
+#pragma unroll
+                for (int j = 0; j < PX; ++j) {
+                    float p;
+                    const float s = splat_s(p0, dp, qq, j, p);
+                    if (done[j] || s > st.a.z) continue;           // alpha < 1/255: skip
+                    const float oG = exp2f(__fsub_rn(st.a.w, s));
+                    const float alpha = fminf(amax, oG);
+                    const float test = __fmul_rn(T[j], __fsub_rn(1.0f, alpha));
+                    if (test < tmin) {                             // stop before exceeding 0.9999
+                        done[j] = true;
+                        ++ndone;
+                        continue;
+                    }
+                    const float w = alpha * T[j];
+                    const float4 col = s_rgb[k];
+                    Cr[j] += w * col.x;
+                    Cg[j] += w * col.y;
+                    Cb[j] += w * col.z;
+                    T[j] = test;
+                    last[j] = b - start + (uint32_t)k + 1u;
+                }
+                if (ndone == PX) break;
+            }
+        }
+    }
+    const size_t P = (size_t)c.W * c.H;
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        const int px = x0 + c0 + 4 * j;
+        if (px < c.W && py < c.H) {
+            const size_t p = (size_t)py * c.W + px;
+            a.out_rgb[p] = Cr[j] + T[j] * a.bg[0];
+            a.out_rgb[P + p] = Cg[j] + T[j] * a.bg[1];
+            a.out_rgb[2 * P + p] = Cb[j] + T[j] * a.bg[2];
+            a.out_T[p] = T[j];
+            a.out_last[p] = last[j];
+        }
+    }
+}
+
+template <int PX>
+__global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
+    float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
     __shared__ uint32_t s_max;
     const CamK& c = a.cam;
     const int tile = blockIdx.x;
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
-    const int lx = threadIdx.x % c.tile_w, ly = threadIdx.x / c.tile_w;
-    const int px = tx * c.tile_w + lx, py = ty * c.tile_h + ly;
-    const bool inside = px < c.W && py < c.H;
-    const float lxf = (float)lx, lyf = (float)ly;
+    const int nthreads = blockDim.x;
+    const int ly = threadIdx.x >> 2, c0 = threadIdx.x & 3;
     const int x0 = tx * c.tile_w, y0 = ty * c.tile_h;
+    const int py = y0 + ly;
+    const float lyf = (float)ly, c0f = (float)c0;
     const uint32_t start = a.ranges[2 * tile], len = a.ranges[2 * tile + 1] - start;
-    const float amin = a.cfg.alpha_min, amax = a.cfg.alpha_max;
+    const float amax = a.cfg.alpha_max;
+    const float log2_amin = __log2f(a.cfg.alpha_min);
     const size_t P = (size_t)c.W * c.H;
-    const size_t p = (size_t)py * c.W + px;
 
-    uint32_t my_last = 0;
-    float T = 1.0f, dLr = 0.f, dLg = 0.f, dLb = 0.f;
-    if (inside) {
-        my_last = a.last[p];
-        T = a.T_final[p];
-        dLr = a.dL_drgb[p];
-        dLg = a.dL_drgb[P + p];
-        dLb = a.dL_drgb[2 * P + p];
+    float T[PX], Rr[PX], Rg[PX], Rb[PX], dLr[PX], dLg[PX], dLb[PX];
+    uint32_t mylast[PX];
+    uint32_t tmax = 0;
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        const int px = x0 + c0 + 4 * j;
+        mylast[j] = 0;
+        T[j] = 1.0f;
+        dLr[j] = dLg[j] = dLb[j] = 0.f;
+        if (px < c.W && py < c.H) {
+            const size_t p = (size_t)py * c.W + px;
+            mylast[j] = a.last[p];
+            T[j] = a.T_final[p];
+            dLr[j] = a.dL_drgb[p];
+            dLg[j] = a.dL_drgb[P + p];
+            dLb[j] = a.dL_drgb[2 * P + p];
+        }
+        Rr[j] = a.bg[0];
+        Rg[j] = a.bg[1];
+        Rb[j] = a.bg[2];
+        tmax = max(tmax, mylast[j]);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_last);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, tmax);
     if ((threadIdx.x & 31) == 0) atomicMax(&s_max, wmax);
     __syncthreads();
     const uint32_t count = min(s_max, len);   // last positions never exceed the tile's list
 
-    float Rr = a.bg[0], Rg = a.bg[1], Rb = a.bg[2];
     for (int bend = (int)count; bend > 0; bend -= a.batch) {
-        const int bstart = max(bend - a.batch, 0);
-        const int nb = bend - bstart;
+        const int nb = min(a.batch, bend);
         __syncthreads();
-        if ((int)threadIdx.x < nb) {
-            uint32_t g = a.vals[start + (uint32_t)(bend - 1 - (int)threadIdx.x)];
+        for (int k = threadIdx.x; k < nb; k += nthreads) {
+            uint32_t g = a.vals[start + (uint32_t)(bend - 1 - k)];
             if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
-            s_idx[threadIdx.x] = g;
-            const float4 m = a.xy[g];
-            s_off[threadIdx.x] = make_float2(tile_offset(x0, m.x, m.z), tile_offset(y0, m.y, m.w));
-            s_co[threadIdx.x] = a.conic_opacity[g];
-            s_rgb[threadIdx.x] = a.rgb[g];
+            Staged st;
+            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
+            s_sp[k] = st;
+            s_rgb[k] = a.rgb[g];
+            s_idx[k] = g;
         }
         __syncthreads();
         for (int k = 0; k < nb; ++k) {
             const uint32_t pos = (uint32_t)(bend - 1 - k);
             float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_bl = 0.f;
             bool contrib = false;
-            if (pos < my_last) {
-                float G, oG, pp, qq;
-                const float4 co = s_co[k];
-                const float2 o = s_off[k];
-                const float dx = __fadd_rn(lxf, o.x), dy = __fadd_rn(lyf, o.y);
-                const float power = splat_power(dx, dy, co, pp, qq);
-                const float alpha = splat_alpha(power, co.w, amax, G, oG);
-                if (alpha >= amin) {
+            if (pos < tmax) {
+                const Staged st = s_sp[k];
+                float p0, dp, q, qq;
+                splat_row(st, lyf, c0f, p0, dp, q, qq);
+#pragma unroll
+                for (int j = 0; j < PX; ++j) {
+                    float p;
+                    const float s = splat_s(p0, dp, qq, j, p);
+                    if (pos >= mylast[j] || s > st.a.z) continue;
                     contrib = true;
+                    const float oG = exp2f(__fsub_rn(st.a.w, s));
+                    const float alpha = fminf(amax, oG);
                     const float one_m = __fsub_rn(1.0f, alpha);
-                    const float Ti = T / one_m;
+                    const float Ti = T[j] / one_m;
                     const float w = alpha * Ti;
                     const float4 col = s_rgb[k];
-                    g_r = w * dLr;
-                    g_g = w * dLg;
-                    g_bl = w * dLb;
-                    const float dalpha = Ti * ((col.x - Rr) * dLr + (col.y - Rg) * dLg + (col.z - Rb) * dLb);
-                    Rr = alpha * col.x + one_m * Rr;
-                    Rg = alpha * col.y + one_m * Rg;
-                    Rb = alpha * col.z + one_m * Rb;
-                    T = Ti;
+                    g_r += w * dLr[j];
+                    g_g += w * dLg[j];
+                    g_bl += w * dLb[j];
+                    const float dalpha =
+                        Ti * ((col.x - Rr[j]) * dLr[j] + (col.y - Rg[j]) * dLg[j] + (col.z - Rb[j]) * dLb[j]);
+                    Rr[j] = alpha * col.x + one_m * Rr[j];
+                    Rg[j] = alpha * col.y + one_m * Rg[j];
+                    Rb[j] = alpha * col.z + one_m * Rb[j];
+                    T[j] = Ti;
                     if (oG <= amax) {
-                        g_o = G * dalpha;
-                        const float dpow = oG * dalpha;
-                        // With g = Q d = L (p, q): d(power)/d(mean) = g and
-                        // d(power)/d(Sigma') = g g^T / 2 (from d(Q) = -Q d(Sigma') Q).  Accumulating
-                        // dL/dSigma' here, instead of dL/dconic followed by -Q G Q per Gaussian,
-                        // avoids the cancellation of that product for elongated splats.
-                        const float gx = co.x * pp, gy = co.y * pp + co.z * qq;
+                        g_o += oG * st.b.w * dalpha;                 // G = oG / o
+                        const float dpow = oG * dalpha;              // dL/d(power)
+                        // g = Sigma'^-1 d = L (p, q) in natural units
+                        const float gx = st.b.x * p * kTwoLn2;
+                        const float gy = (st.b.y * p + st.b.z * q) * kTwoLn2;
                         const float h = 0.5f * dpow;
-                        g_u = gx * dpow;
-                        g_v = gy * dpow;
-                        g_a = h * gx * gx;
-                        g_b = h * gx * gy;
-                        g_c = h * gy * gy;
+                        g_u += gx * dpow;
+                        g_v += gy * dpow;
+                        g_a += h * gx * gx;
+                        g_b += h * gx * gy;
+                        g_c += h * gy * gy;
                     }
                 }
             }
@@ -207,15 +289,24 @@ __global__ void __launch_bounds__(kMaxTilePixels) k_render_backward(RenderBwdArg
     }
 }
 
-cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, int threads, cudaStream_t s) {
+size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4)) * (size_t)batch; }
+size_t bwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(uint32_t)) * (size_t)batch; }
+
+}  // namespace
+
+cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_render_forward<<<tiles, threads, 0, s>>>(a);
+    const int nt = 4 * a.cam.tile_h;
+    if (a.cam.tile_w == 16) k_render_forward_t<4><<<tiles, nt, fwd_smem(a.batch), s>>>(a);
+    else k_render_forward_t<2><<<tiles, nt, fwd_smem(a.batch), s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, int threads, cudaStream_t s) {
+cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, cudaStream_t s) {
     if (tiles <= 0) return cudaSuccess;
-    k_render_backward<<<tiles, threads, 0, s>>>(a);
+    const int nt = 4 * a.cam.tile_h;
+    if (a.cam.tile_w == 16) k_render_backward_t<4><<<tiles, nt, bwd_smem(a.batch), s>>>(a);
+    else k_render_backward_t<2><<<tiles, nt, bwd_smem(a.batch), s>>>(a);
     return cudaGetLastError();
 }
 

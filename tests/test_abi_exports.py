@@ -69,7 +69,7 @@ int main(void) {
 def test_default_config_is_the_papers(lib):
     from paper_2308_04079_gb300 import _abi
     c = _abi.gs_default_config()
-    assert (c.tile_w, c.tile_h, c.batch_depth, c.sort_mode) == (16, 16, 256, _abi.GS_SORT_TWO_PHASE)
+    assert (c.tile_w, c.tile_h, c.batch_depth, c.sort_mode) == (16, 16, 128, _abi.GS_SORT_TWO_PHASE)
     assert c.alpha_min == pytest.approx(1 / 255) and c.alpha_max == pytest.approx(0.99)
     assert c.T_min == pytest.approx(1e-4) and c.dilation == pytest.approx(0.3)
     assert c.guard == pytest.approx(1.3) and c.extent == pytest.approx(3.0)
