@@ -33,6 +33,7 @@ constexpr uint32_t kLbAgg = 0x40000000u;   // look-back word: aggregate of this 
 constexpr uint32_t kLbInc = 0x80000000u;   // look-back word: inclusive prefix up to this chunk
 constexpr uint32_t kLbFlags = 0xC0000000u;
 constexpr uint32_t kLbValue = 0x3FFFFFFFu;
+constexpr int kLbWindow = 8;                // predecessors read per look-back round
 
 constexpr unsigned long long kScanAgg = 1ull << 62;
 constexpr unsigned long long kScanInc = 2ull << 62;
@@ -89,18 +90,18 @@ __global__ void __launch_bounds__(256) k_depth_hist(DepthHistArgs a) {
 // One LSD digit pass (8 bits at `shift`), stable.
 // ---------------------------------------------------------------------------------------
 template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortPassArgs<KeyT> a) {
-    constexpr int ITEMS = kSortItems;
-    constexpr int TILE = kSortTile;
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(SortPassArgs<KeyT> a) {
+    constexpr int ITEMS = SortTile<KeyT>::items;
+    constexpr int TILE = SortTile<KeyT>::keys;
     constexpr int WARPS = kSortThreads / 32;
     __shared__ __align__(16) KeyT s_keys[TILE];
+    __shared__ uint32_t s_vals[TILE];
     __shared__ uint32_t s_hist[WARPS][256];
     __shared__ uint32_t s_block_start[256];
     __shared__ uint32_t s_global[256];
     __shared__ uint32_t s_digit_off[256];
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_chunk;
-    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = lanemask_lt();
@@ -154,16 +155,18 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortPassArgs<KeyT> a)
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) {
-            const uint32_t c = s_hist[w][d];
+            const uint32_t cnt = s_hist[w][d];
             s_hist[w][d] = run;
-            run += c;
+            run += cnt;
         }
         const uint32_t block_cnt = run;
         {
             uint32_t tot;
             s_block_start[d] = block_exclusive_scan<uint32_t>(block_cnt, s_scan, &tot);
         }
-        // Decoupled look-back over predecessor chunks for digit d.
+        // Decoupled look-back over predecessor chunks for digit d, kLbWindow predecessors per
+        // round of loads: chunks start together, so a one-at-a-time walk would serialise the
+        // first wave of blocks into a chain of dependent loads.
         uint32_t* my = a.lookback + (size_t)chunk * 256 + d;
         uint32_t excl = 0;
         if (chunk == 0) {
@@ -173,61 +176,61 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortPassArgs<KeyT> a)
             int j = (int)chunk - 1;
             uint32_t spins = 0;
             while (j >= 0) {
-                const uint32_t v = ld_relaxed(a.lookback + (size_t)j * 256 + d);
-                const uint32_t f = v & kLbFlags;
-                if (f == 0) {
+                uint32_t v[kLbWindow];
+#pragma unroll
+                for (int w = 0; w < kLbWindow; ++w)
+                    v[w] = (j - w >= 0) ? ld_relaxed(a.lookback + (size_t)(j - w) * 256 + d) : kLbInc;
+                int used = 0;
+                bool stop = false, wait = false;
+#pragma unroll
+                for (int w = 0; w < kLbWindow; ++w) {
+                    if (stop || wait) continue;
+                    const uint32_t f = v[w] & kLbFlags;
+                    if (f == 0) { wait = true; continue; }
+                    excl += v[w] & kLbValue;
+                    ++used;
+                    if (f == kLbInc) stop = true;
+                }
+                if (stop) break;
+                j -= used;
+                if (wait) {
                     if (++spins > kSpinLimit) {
                         atomicOr(&a.status->flags, kFlagTimeout);
                         break;
                     }
                     backoff(spins);
-                    continue;
                 }
-                excl += v & kLbValue;
-                if (f == kLbInc) break;
-                --j;
             }
             st_relaxed(my, kLbInc | ((excl + block_cnt) & kLbValue));
         }
         s_global[d] = s_digit_off[d] + excl;
         __syncthreads();
-        // Stage keys in local sorted order.
+        // Stage keys and values in local sorted order.
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const uint32_t dd = digit_of(key[i], a.shift);
             const uint32_t p = s_block_start[dd] + s_hist[warp][dd] + pos_local[i];
             s_keys[p] = key[i];
-            pos_local[i] = p;
+            const uint32_t pos = wbase + i * 32 + lane;
+            uint32_t v = 0;
+            if (pos < count) v = a.vals_in ? a.vals_in[pos] : pos;
+            s_vals[p] = v;
         }
         __syncthreads();
-        uint32_t dst[ITEMS];
-#pragma unroll
+#pragma unroll 4
         for (int k = 0; k < ITEMS; ++k) {
             const uint32_t s = tid + k * kSortThreads;
             const KeyT kk = s_keys[s];
             const uint32_t dd = digit_of(kk, a.shift);
             const uint32_t dest = s_global[dd] + (s - s_block_start[dd]);
-            dst[k] = dest;
-            if (dest < count) a.keys_out[dest] = kk;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t pos = wbase + i * 32 + lane;
-            uint32_t v = 0;
-            if (pos < count) v = a.vals_in ? a.vals_in[pos] : pos;
-            s_vals[pos_local[i]] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            const uint32_t s = tid + k * kSortThreads;
-            if (dst[k] < count) a.vals_out[dst[k]] = s_vals[s];
+            if (dest < count) {
+                a.keys_out[dest] = kk;
+                a.vals_out[dest] = s_vals[s];
+            }
         }
         __syncthreads();
     }
 }
-
 
 // ---------------------------------------------------------------------------------------
 // Scan of tiles per Gaussian (in `order`) with chained look-back.  Per Gaussian it stores the
@@ -260,18 +263,34 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
         const uint32_t chunk = s_chunk;
         if (chunk >= chunks) break;
         uint32_t tiles[PER];
+        uint32_t gids[PER];
+        int rad[PER];
+        float4 mean[PER];
         uint32_t run = 0;
+        // gather first (independent loads in flight together), then compute
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const uint32_t j = chunk * kDupChunk + tid * PER + k;
+            uint32_t gid = j < count ? (a.order ? a.order[j] : j) : 0u;
+            if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
+            gids[k] = gid;
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const uint32_t j = chunk * kDupChunk + tid * PER + k;
+            rad[k] = j < count ? a.radius[gids[k]] : 0;
+            mean[k] = a.xy[gids[k]];
+        }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             const uint32_t j = chunk * kDupChunk + tid * PER + k;
             tiles[k] = 0;
             uint2 rect = make_uint2(0u, 0u);
             if (j < count) {
-                uint32_t gid = a.order ? a.order[j] : j;
-                if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
-                const int r = a.radius[gid];
+                const uint32_t gid = gids[k];
+                const int r = rad[k];
                 int x0, x1, y0, y1;
-                if (r > 0 && tile_rect(a.xy[gid], r, c, x0, x1, y0, y1)) {
+                if (r > 0 && tile_rect(mean[k], r, c, x0, x1, y0, y1)) {
                     tiles[k] = (uint32_t)((x1 - x0) * (y1 - y0));
                     rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)(x1 - x0) | ((uint32_t)(y1 - y0) << 16));
                     atomicAdd(&a.diff[y0 * gw + x0], 1);
@@ -290,37 +309,46 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
         }
         uint32_t block_total;
         const uint32_t texcl = block_exclusive_scan<uint32_t>(run, s_scan, &block_total);
-        if (tid == 0) {
+        // Decoupled look-back by warp 0, 32 predecessors per round of loads.
+        if (tid < 32) {
             unsigned long long* my = a.lookback + chunk;
             unsigned long long excl = 0;
-            if (chunk == 0) {
-                st_relaxed64(my, kScanInc | block_total);
-            } else {
-                st_relaxed64(my, kScanAgg | block_total);
+            if (tid == 0) st_relaxed64(my, (chunk == 0 ? kScanInc : kScanAgg) | block_total);
+            if (chunk > 0) {
                 int j = (int)chunk - 1;
                 uint32_t spins = 0;
-                while (j >= 0) {
-                    const unsigned long long v = ld_relaxed64(a.lookback + j);
+                while (true) {
+                    const int idx = j - tid;
+                    const unsigned long long v = idx >= 0 ? ld_relaxed64(a.lookback + idx) : kScanInc;
                     const unsigned long long f = v & kScanFlags;
-                    if (f == 0) {
+                    const uint32_t inc = __ballot_sync(0xffffffffu, f == kScanInc);
+                    const uint32_t zero = __ballot_sync(0xffffffffu, f == 0);
+                    const int first_inc = inc ? __ffs(inc) - 1 : 32;
+                    const uint32_t upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
+                    if (zero & upto) {   // a predecessor in front of the first prefix is not ready
                         if (++spins > kSpinLimit) {
-                            atomicOr(&a.status->flags, kFlagTimeout);
+                            if (tid == 0) atomicOr(&a.status->flags, kFlagTimeout);
                             break;
                         }
                         backoff(spins);
                         continue;
                     }
-                    excl += v & kScanValue;
-                    if (f == kScanInc) break;
-                    --j;
+                    unsigned long long part = (tid <= first_inc) ? (v & kScanValue) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                    excl += part;
+                    if (first_inc < 32) break;
+                    j -= 32;
                 }
-                st_relaxed64(my, kScanInc | ((excl + block_total) & kScanValue));
+                if (tid == 0) st_relaxed64(my, kScanInc | ((excl + block_total) & kScanValue));
             }
-            s_base = excl;
-            if (chunk == chunks - 1) {
-                const unsigned long long total = excl + block_total;
-                a.status->num_instances = (uint32_t)min(total, 0xFFFFFFFFull);
-                if (total > a.capacity) atomicOr(&a.status->flags, kFlagCapacity);
+            if (tid == 0) {
+                s_base = excl;
+                if (chunk == chunks - 1) {
+                    const unsigned long long total = excl + block_total;
+                    a.status->num_instances = (uint32_t)min(total, 0xFFFFFFFFull);
+                    if (total > a.capacity) atomicOr(&a.status->flags, kFlagCapacity);
+                }
             }
         }
         __syncthreads();
@@ -407,8 +435,11 @@ template <bool KEY64>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
     using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
     constexpr int PER = kEmitSlots / kEmitThreads;
+    constexpr int WIN = kEmitSlots + 1;         // offsets of the Gaussians that can own the block's slots
     __shared__ KeyT s_key[kEmitSlots];
     __shared__ uint32_t s_val[kEmitSlots];
+    __shared__ uint32_t s_start[WIN];
+    __shared__ uint32_t s_j0;
     const int tid = threadIdx.x;
     const unsigned long long K = min((unsigned long long)a.status->num_instances, a.capacity);
     uint32_t count = (uint32_t)a.n;
@@ -417,19 +448,46 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
     KeyT* keys_out = reinterpret_cast<KeyT*>(a.keys_out);
     for (unsigned long long k0 = (unsigned long long)blockIdx.x * kEmitSlots; k0 < K;
          k0 += (unsigned long long)gridDim.x * kEmitSlots) {
-        const unsigned long long first = k0 + (unsigned long long)tid * PER;
-        if (first < K && count > 0) {
-            // last j with start[j] <= first
+        if (tid == 0) {
+            // last j with start[j] <= k0 (one global binary search per block)
             uint32_t lo = 0, hi = count - 1;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi + 1) >> 1;
-                if (a.start[mid] <= first) lo = mid;
+                if (a.start[mid] <= k0) lo = mid;
                 else hi = mid - 1;
             }
-            uint32_t j = lo;
+            s_j0 = lo;
+        }
+        __syncthreads();
+        const uint32_t j0 = s_j0;
+        // Window of offsets start[j0 .. j0 + WIN - 1]; entries past the end act as +infinity.
+        for (int w = tid; w < WIN; w += kEmitThreads)
+            s_start[w] = (j0 + w < count) ? a.start[j0 + w] : 0xFFFFFFFFu;
+        __syncthreads();
+        const unsigned long long first = k0 + (unsigned long long)tid * PER;
+        if (first < K) {
+            // last w with s_start[w] <= first, within the window (a Gaussian owning a slot has at
+            // least one tile, so the owners of the block's 2048 slots start inside the window
+            // unless Gaussians without tiles sit in between)
+            int lo = 0, hi = WIN - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((unsigned long long)s_start[mid] <= first) lo = mid;
+                else hi = mid - 1;
+            }
+            uint32_t j = j0 + (uint32_t)lo;
+            if (lo == WIN - 1) {   // window exhausted: continue the search in global memory
+                uint32_t glo = j, ghi = count - 1;
+                while (glo < ghi) {
+                    const uint32_t mid = (glo + ghi + 1) >> 1;
+                    if (a.start[mid] <= first) glo = mid;
+                    else ghi = mid - 1;
+                }
+                j = glo;
+            }
+            uint32_t st = a.start[j];
             uint32_t nxt = (j + 1 < count) ? a.start[j + 1] : 0xFFFFFFFFu;
             uint2 rect = a.rect[j];
-            uint32_t st = a.start[j];
             uint32_t gid = a.order ? a.order[j] : j;
             if (gid >= (uint32_t)a.n) gid = 0;
             float inv_w = 1.0f / (float)(rect.y & 0xFFFFu);
@@ -480,7 +538,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
 // device-side instance count).
 __global__ void k_sort_prepare(SortPrepareArgs a) {
     const uint32_t count = min((unsigned long long)a.status->num_instances, a.capacity);
-    const uint32_t rows = (count + kSortTile - 1) / kSortTile;
+    const uint32_t rows = (count + a.tile_keys - 1) / a.tile_keys;
     const size_t total = (size_t)rows * 256;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
         a.lookback[k] = 0;

@@ -77,7 +77,7 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->diff = take(L->diff_count * sizeof(int));
     L->scan_lb_rows = (nn + kDupChunk - 1) / kDupChunk;
     L->scan_lb = take(L->scan_lb_rows * sizeof(unsigned long long));
-    const size_t rows_n = (nn + kSortTile - 1) / kSortTile, rows_c = (cc + kSortTile - 1) / kSortTile;
+    const size_t rows_n = (nn + kSortTile - 1) / kSortTile, rows_c = (cc + kSortTileMin - 1) / kSortTileMin;
     L->sort_lb_rows = rows_n > rows_c ? rows_n : rows_c;
     for (int k = 0; k < 2; ++k) L->sort_lb[k] = take(L->sort_lb_rows * 256 * sizeof(uint32_t));
     for (int k = 0; k < 2; ++k) { L->ikey[k] = take(cc * 8); L->ival[k] = take(cc * 4); }
@@ -148,7 +148,7 @@ template <typename KeyT>
 gs_status run_key_sort(const gs_frame* f, const Layout& L, Control* ctl, cudaStream_t s) {
     void* ws = f->ws;
     gs_device_status* st = &ctl->status;
-    SortPrepareArgs pa{at<uint32_t>(ws, L.sort_lb[0]), st, (unsigned long long)f->capacity};
+    SortPrepareArgs pa{at<uint32_t>(ws, L.sort_lb[0]), SortTile<KeyT>::keys, st, (unsigned long long)f->capacity};
     if (launch_sort_prepare(pa, s) != cudaSuccess) return GS_ERR_CUDA;
     for (int p = 0; p < L.key_passes; ++p) {
         SortPassArgs<KeyT> a;

@@ -10,10 +10,16 @@
 
 namespace gs {
 
-// Radix sort: 256 threads, 16 keys per thread, 8-bit digits.
+// Radix sort: 256 threads, 8-bit digits; 16 keys per thread for 32-bit keys, 12 for 64-bit keys
+// (keys and values of a chunk are staged in shared memory, which must stay below 48 KB).
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
+template <typename KeyT>
+struct SortTile {
+    static constexpr int items = sizeof(KeyT) == 8 ? 12 : 16;
+    static constexpr int keys = kSortThreads * items;
+};
+constexpr int kSortTile = SortTile<uint32_t>::keys;            // 4096
+constexpr int kSortTileMin = SortTile<unsigned long long>::keys; // 3072
 constexpr int kMaxKeyPasses = 8;
 constexpr int kDepthPasses = 4;
 
@@ -146,6 +152,7 @@ struct EmitArgs {
 
 struct SortPrepareArgs {
     uint32_t* lookback;
+    int tile_keys;             // keys per chunk of the pass that follows
     const gs_device_status* status;
     unsigned long long capacity;
 };

@@ -102,15 +102,36 @@ __device__ __forceinline__ void project_cov(const float* s, const float4 q, cons
 
 __device__ __forceinline__ bool finite3(const float* v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
 
+// SH coefficients of one Gaussian, [D][3] floats.  VEC: the row starts 16-byte aligned and its
+// stride is a multiple of 4 floats, so it is read as float4 (rounded up to whole float4s, which
+// stays inside the row).
+template <int D, bool VEC>
+__device__ __forceinline__ void load_sh(const float* __restrict__ sh, float (&f)[4 * ((3 * D + 3) / 4)]) {
+    constexpr int N4 = (3 * D + 3) / 4;
+    if (VEC) {
+        const float4* p = reinterpret_cast<const float4*>(sh);
+#pragma unroll
+        for (int k = 0; k < N4; ++k) {
+            const float4 v = p[k];
+            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3 * D; ++k) f[k] = sh[k];
+    }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_preprocess(PreprocessArgs a) {
+template <int DEG, bool VEC>
+__global__ void __launch_bounds__(256) k_preprocess_t(PreprocessArgs a) {
+    constexpr int D = (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool visible = false;
     if (i < a.n) {
         const CamK& c = a.cam;
-        float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
-        float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
+        const float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
+        const float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
         const float4 q = reinterpret_cast<const float4*>(a.quats)[i];
         const float o = a.opacities[i];
         const bool finite = finite3(mu) && finite3(s) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
@@ -145,14 +166,15 @@ __global__ void __launch_bounds__(256) k_preprocess(PreprocessArgs a) {
             const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
             dx *= inv; dy *= inv; dz *= inv;
             float Y[16];
-            sh_basis(a.sh_degree, dx, dy, dz, Y);
-            const int D = (a.sh_degree + 1) * (a.sh_degree + 1);
-            const float* sh = a.sh + (size_t)i * a.sh_stride * 3;
+            sh_basis(DEG, dx, dy, dz, Y);
+            float f[4 * ((3 * D + 3) / 4)];
+            load_sh<D, VEC>(a.sh + (size_t)i * a.sh_stride * 3, f);
             float r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
             for (int k = 0; k < D; ++k) {
-                r += sh[3 * k] * Y[k];
-                g += sh[3 * k + 1] * Y[k];
-                b += sh[3 * k + 2] * Y[k];
+                r += f[3 * k] * Y[k];
+                g += f[3 * k + 1] * Y[k];
+                b += f[3 * k + 2] * Y[k];
             }
             if (!(isfinite(r) && isfinite(g) && isfinite(b))) {
                 atomicAdd(&a.status->num_nonfinite, 1u);
@@ -173,18 +195,25 @@ __global__ void __launch_bounds__(256) k_preprocess(PreprocessArgs a) {
     if ((threadIdx.x & 31) == 0 && vis) atomicAdd(&a.status->num_visible, (uint32_t)__popc(vis));
 }
 
-__global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a) {
+template <int DEG, bool VEC>
+__global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs a) {
+    constexpr int D = (DEG + 1) * (DEG + 1);
+    constexpr int NF = 4 * ((3 * D + 3) / 4);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const int D = (a.sh_degree + 1) * (a.sh_degree + 1);
     float* gsh = a.g_sh + (size_t)i * a.sh_stride * 3;
+    const int row = a.sh_stride * 3;   // floats per Gaussian in the SH buffers
     const int radius = a.radius[i];
     if (radius <= 0) {
         if (!a.accumulate) {
             for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = 0.f; a.g_scales[3 * i + k] = 0.f; }
             reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             a.g_opacities[i] = 0.f;
-            for (int k = 0; k < a.sh_stride * 3; ++k) gsh[k] = 0.f;
+            if (VEC) {
+                for (int k = 0; k < row / 4; ++k) reinterpret_cast<float4*>(gsh)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for (int k = 0; k < row; ++k) gsh[k] = 0.f;
+            }
             if (a.g_mean2d) { a.g_mean2d[2 * i] = 0.f; a.g_mean2d[2 * i + 1] = 0.f; }
         }
         return;
@@ -238,8 +267,8 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a
     dq[3] = 2.f * (-2.f * qk * dR[0] - qr * dR[1] + qi * dR[2] + qr * dR[3] - 2.f * qk * dR[4] + qj * dR[5] +
                    qi * dR[6] + qj * dR[7]);
     const float proj = dq[0] * qr + dq[1] * qi + dq[2] * qj + dq[3] * qk;
-    float4 gq = make_float4((dq[0] - qr * proj) * p.qinv, (dq[1] - qi * proj) * p.qinv, (dq[2] - qj * proj) * p.qinv,
-                            (dq[3] - qk * proj) * p.qinv);
+    const float4 gq = make_float4((dq[0] - qr * proj) * p.qinv, (dq[1] - qi * proj) * p.qinv,
+                                  (dq[2] - qj * proj) * p.qinv, (dq[3] - qk * proj) * p.qinv);
     // T2 = J W with J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]].
     float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
 #pragma unroll
@@ -252,10 +281,10 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a
     const float du = g0.x, dv = g0.y;
     const float iz = 1.0f / p.tz, iz2 = iz * iz;
     const float fx = c.fx, fy = c.fy;
-    float dt0 = du * fx * iz - dJ02 * fx * iz2;
-    float dt1 = dv * fy * iz - dJ12 * fy * iz2;
-    float dt2 = -du * fx * p.xz * iz - dv * fy * p.yz * iz - dJ00 * fx * iz2 + dJ02 * 2.f * fx * p.xz * iz2 -
-                dJ11 * fy * iz2 + dJ12 * 2.f * fy * p.yz * iz2;
+    const float dt0 = du * fx * iz - dJ02 * fx * iz2;
+    const float dt1 = dv * fy * iz - dJ12 * fy * iz2;
+    const float dt2 = -du * fx * p.xz * iz - dv * fy * p.yz * iz - dJ00 * fx * iz2 + dJ02 * 2.f * fx * p.xz * iz2 -
+                      dJ11 * fy * iz2 + dJ12 * 2.f * fy * p.yz * iz2;
     float gm[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) gm[k] = c.R[k] * dt0 + c.R[3 + k] * dt1 + c.R[6 + k] * dt2;
@@ -266,34 +295,59 @@ __global__ void __launch_bounds__(256) k_preprocess_backward(PreprocessBwdArgs a
     const float dr = (mask & 1u) ? 0.f : g1.z;
     const float dg = (mask & 2u) ? 0.f : g1.w;
     const float dbl = (mask & 4u) ? 0.f : g2;
-    float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];
-    const float ninv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    dx *= ninv; dy *= ninv; dz *= ninv;
+    float ex = mu[0] - c.campos[0], ey = mu[1] - c.campos[1], ez = mu[2] - c.campos[2];
+    const float ninv = rsqrtf(ex * ex + ey * ey + ez * ez);
+    ex *= ninv; ey *= ninv; ez *= ninv;
     float Y[16];
     float3 dY[16];
-    sh_basis(a.sh_degree, dx, dy, dz, Y);
-    sh_basis_grad(a.sh_degree, dx, dy, dz, dY);
-    const float* sh = a.sh + (size_t)i * a.sh_stride * 3;
+    sh_basis(DEG, ex, ey, ez, Y);
+    sh_basis_grad(DEG, ex, ey, ez, dY);
+    float f[NF];
+    load_sh<D, VEC>(a.sh + (size_t)i * row, f);
     float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+    float gout[NF];
+#pragma unroll
     for (int k = 0; k < D; ++k) {
-        const float w = sh[3 * k] * dr + sh[3 * k + 1] * dg + sh[3 * k + 2] * dbl;
-        ddx += w * dY[k].x; ddy += w * dY[k].y; ddz += w * dY[k].z;
-        float g3[3] = {Y[k] * dr, Y[k] * dg, Y[k] * dbl};
-        for (int ch = 0; ch < 3; ++ch) {
-            if (a.accumulate) gsh[3 * k + ch] += g3[ch];
-            else gsh[3 * k + ch] = g3[ch];
-        }
+        const float w = f[3 * k] * dr + f[3 * k + 1] * dg + f[3 * k + 2] * dbl;
+        ddx += w * dY[k].x;
+        ddy += w * dY[k].y;
+        ddz += w * dY[k].z;
+        gout[3 * k] = Y[k] * dr;
+        gout[3 * k + 1] = Y[k] * dg;
+        gout[3 * k + 2] = Y[k] * dbl;
     }
-    if (!a.accumulate)
-        for (int k = 3 * D; k < a.sh_stride * 3; ++k) gsh[k] = 0.f;
-    const float dp = ddx * dx + ddy * dy + ddz * dz;
-    gm[0] += (ddx - dx * dp) * ninv;
-    gm[1] += (ddy - dy * dp) * ninv;
-    gm[2] += (ddz - dz * dp) * ninv;
+#pragma unroll
+    for (int k = 3 * D; k < NF; ++k) gout[k] = 0.f;
+    if (VEC) {
+        float4* g4 = reinterpret_cast<float4*>(gsh);
+#pragma unroll
+        for (int k = 0; k < NF / 4; ++k) {
+            float4 v = make_float4(gout[4 * k], gout[4 * k + 1], gout[4 * k + 2], gout[4 * k + 3]);
+            if (a.accumulate) {
+                const float4 o4 = g4[k];
+                v = make_float4(o4.x + v.x, o4.y + v.y, o4.z + v.z, o4.w + v.w);
+            }
+            g4[k] = v;
+        }
+        if (!a.accumulate)
+            for (int k = NF / 4; k < row / 4; ++k) g4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3 * D; ++k) {
+            if (a.accumulate) gsh[k] += gout[k];
+            else gsh[k] = gout[k];
+        }
+        if (!a.accumulate)
+            for (int k = 3 * D; k < row; ++k) gsh[k] = 0.f;
+    }
+    const float dp = ddx * ex + ddy * ey + ddz * ez;
+    gm[0] += (ddx - ex * dp) * ninv;
+    gm[1] += (ddy - ey * dp) * ninv;
+    gm[2] += (ddz - ez * dp) * ninv;
 
     if (a.accumulate) {
         for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] += gm[k]; a.g_scales[3 * i + k] += gs3[k]; }
-        float4 o4 = reinterpret_cast<float4*>(a.g_quats)[i];
+        const float4 o4 = reinterpret_cast<float4*>(a.g_quats)[i];
         reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(o4.x + gq.x, o4.y + gq.y, o4.z + gq.z, o4.w + gq.w);
         a.g_opacities[i] += g1.y;
         if (a.g_mean2d) { a.g_mean2d[2 * i] += du; a.g_mean2d[2 * i + 1] += dv; }
@@ -314,15 +368,52 @@ int persistent_grid(const void* kernel, int threads) {
     return sms * per;
 }
 
+namespace {
+
+// SH rows can be read and written as float4 when every row starts 16-byte aligned.
+bool sh_vectorisable(const float* sh, int sh_stride, const float* gsh = nullptr) {
+    const bool base = reinterpret_cast<uintptr_t>(sh) % 16 == 0 &&
+                      (gsh == nullptr || reinterpret_cast<uintptr_t>(gsh) % 16 == 0);
+    return base && (3 * sh_stride) % 4 == 0;
+}
+
+template <int DEG>
+void preprocess_deg(const PreprocessArgs& a, bool vec, cudaStream_t s) {
+    const int grid = (a.n + 255) / 256;
+    if (vec) k_preprocess_t<DEG, true><<<grid, 256, 0, s>>>(a);
+    else k_preprocess_t<DEG, false><<<grid, 256, 0, s>>>(a);
+}
+
+template <int DEG>
+void preprocess_bwd_deg(const PreprocessBwdArgs& a, bool vec, cudaStream_t s) {
+    const int grid = (a.n + 255) / 256;
+    if (vec) k_preprocess_backward_t<DEG, true><<<grid, 256, 0, s>>>(a);
+    else k_preprocess_backward_t<DEG, false><<<grid, 256, 0, s>>>(a);
+}
+
+}  // namespace
+
 cudaError_t launch_preprocess(const PreprocessArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    k_preprocess<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    const bool vec = sh_vectorisable(a.sh, a.sh_stride);
+    switch (a.sh_degree) {
+        case 0: preprocess_deg<0>(a, vec, s); break;
+        case 1: preprocess_deg<1>(a, vec, s); break;
+        case 2: preprocess_deg<2>(a, vec, s); break;
+        default: preprocess_deg<3>(a, vec, s); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_backward(const PreprocessBwdArgs& a, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    k_preprocess_backward<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+    const bool vec = sh_vectorisable(a.sh, a.sh_stride, a.g_sh);
+    switch (a.sh_degree) {
+        case 0: preprocess_bwd_deg<0>(a, vec, s); break;
+        case 1: preprocess_bwd_deg<1>(a, vec, s); break;
+        case 2: preprocess_bwd_deg<2>(a, vec, s); break;
+        default: preprocess_bwd_deg<3>(a, vec, s); break;
+    }
     return cudaGetLastError();
 }
 

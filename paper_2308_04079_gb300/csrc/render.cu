@@ -21,8 +21,9 @@
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
 //   Through a = o G (zero when clamped), with g = Sigma'^-1 d: d(power)/d(mean) = g and
 //   d(power)/d(Sigma') = g g^T / 2.  A thread sums its pixels' dL/d(mean2D, Sigma', opacity,
-//   colour), the warp sums its lanes with shuffles, and lane 0 adds the result to the
-//   per-Gaussian accumulators with vector atomics.
+//   colour); when more than two lanes of a warp contributed, the warp sums its lanes with
+//   shuffles and lane 0 adds the result to the splat's accumulators with vector atomics,
+//   otherwise the contributing lanes add their own sums.
 //
 // The forward and the backward evaluate a (pixel, splat) pair with the same staging and the same
 // operation sequence (stage_splat, splat_row, splat_s), so their skip and clamp decisions agree
@@ -38,6 +39,8 @@ namespace {
 constexpr float kScaleLog2 = 0.84932180028801907f;
 // 1 / kScaleLog2^2 = 2 ln 2: converts scaled (p, q) products back to natural units.
 constexpr float kTwoLn2 = 1.3862943611198906f;
+// At most this many contributing lanes add their own sums instead of a warp reduction.
+constexpr int kDirectLanes = 2;
 
 struct Staged {
     float4 a;   // (ox, oy, thr, lo): tile-relative offset, skip threshold, log2(opacity)
@@ -68,12 +71,6 @@ __device__ __forceinline__ void splat_row(const Staged& s, float lyf, float c0f,
 __device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, float& p) {
     p = __fmaf_rn((float)j, dp, p0);
     return __fmaf_rn(p, p, qq);
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 template <int PX>
@@ -122,6 +119,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
                 const Staged st = s_sp[k];
                 float p0, dp, q, qq;
                 splat_row(st, lyf, c0f, p0, dp, q, qq);
+                if (qq > st.a.z) continue;                         // s >= q^2: the whole row skips
 #pragma unroll
                 for (int j = 0; j < PX; ++j) {
                     float p;
@@ -226,12 +224,14 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
         __syncthreads();
         for (int k = 0; k < nb; ++k) {
             const uint32_t pos = (uint32_t)(bend - 1 - k);
-            float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_bl = 0.f;
+            float g[9];
+#pragma unroll
+            for (int v = 0; v < 9; ++v) g[v] = 0.f;
             bool contrib = false;
-            if (pos < tmax) {
-                const Staged st = s_sp[k];
-                float p0, dp, q, qq;
-                splat_row(st, lyf, c0f, p0, dp, q, qq);
+            const Staged st = s_sp[k];
+            float p0, dp, q, qq;
+            splat_row(st, lyf, c0f, p0, dp, q, qq);
+            if (pos < tmax && qq <= st.a.z) {                      // s >= q^2: else the whole row skips
 #pragma unroll
                 for (int j = 0; j < PX; ++j) {
                     float p;
@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
                     const float Ti = T[j] / one_m;
                     const float w = alpha * Ti;
                     const float4 col = s_rgb[k];
-                    g_r += w * dLr[j];
-                    g_g += w * dLg[j];
-                    g_bl += w * dLb[j];
+                    g[6] += w * dLr[j];
+                    g[7] += w * dLg[j];
+                    g[8] += w * dLb[j];
                     const float dalpha =
                         Ti * ((col.x - Rr[j]) * dLr[j] + (col.y - Rg[j]) * dLg[j] + (col.z - Rb[j]) * dLb[j]);
                     Rr[j] = alpha * col.x + one_m * Rr[j];
@@ -254,35 +254,40 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
                     Rb[j] = alpha * col.z + one_m * Rb[j];
                     T[j] = Ti;
                     if (oG <= amax) {
-                        g_o += oG * st.b.w * dalpha;                 // G = oG / o
-                        const float dpow = oG * dalpha;              // dL/d(power)
+                        g[5] += oG * st.b.w * dalpha;                 // G = oG / o
+                        const float dpow = oG * dalpha;               // dL/d(power)
                         // g = Sigma'^-1 d = L (p, q) in natural units
                         const float gx = st.b.x * p * kTwoLn2;
                         const float gy = (st.b.y * p + st.b.z * q) * kTwoLn2;
                         const float h = 0.5f * dpow;
-                        g_u += gx * dpow;
-                        g_v += gy * dpow;
-                        g_a += h * gx * gx;
-                        g_b += h * gx * gy;
-                        g_c += h * gy * gy;
+                        g[0] += gx * dpow;
+                        g[1] += gy * dpow;
+                        g[2] += h * gx * gx;
+                        g[3] += h * gx * gy;
+                        g[4] += h * gy * gy;
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                g_u = warp_sum(g_u);
-                g_v = warp_sum(g_v);
-                g_a = warp_sum(g_a);
-                g_b = warp_sum(g_b);
-                g_c = warp_sum(g_c);
-                g_o = warp_sum(g_o);
-                g_r = warp_sum(g_r);
-                g_g = warp_sum(g_g);
-                g_bl = warp_sum(g_bl);
+            const uint32_t who = __ballot_sync(0xffffffffu, contrib);
+            if (who == 0) continue;
+            float* dst = a.grad2d + 12 * (size_t)s_idx[k];
+            if (__popc(who) <= kDirectLanes) {
+                // few contributing lanes: each adds its own sums (cheaper than a butterfly)
+                if (contrib) {
+                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(g[0], g[1], g[2], g[3]));
+                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(g[4], g[5], g[6], g[7]));
+                    atomicAdd(dst + 8, g[8]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < 9; ++v) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) g[v] += __shfl_xor_sync(0xffffffffu, g[v], o);
+                }
                 if ((threadIdx.x & 31) == 0) {
-                    float4* acc = reinterpret_cast<float4*>(a.grad2d) + 3 * (size_t)s_idx[k];
-                    atomicAdd(acc, make_float4(g_u, g_v, g_a, g_b));
-                    atomicAdd(acc + 1, make_float4(g_c, g_o, g_r, g_g));
-                    atomicAdd(reinterpret_cast<float*>(acc + 2), g_bl);
+                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(g[0], g[1], g[2], g[3]));
+                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(g[4], g[5], g[6], g[7]));
+                    atomicAdd(dst + 8, g[8]);
                 }
             }
         }
