@@ -64,6 +64,12 @@ enum {
     GS_SORT_KEY64 = 1         /* one LSD sort of the 64-bit (tile << 32 | depth) keys, as in App. C      */
 };
 
+/* Which tiles of a splat's 3-sigma rectangle get an instance (see gs_bin_sort). */
+enum {
+    GS_TILES_REACH = 0,       /* tiles holding a pixel centre the splat can reach with alpha >= alpha_min */
+    GS_TILES_RECT = 1         /* every tile of the rectangle, as in Sec. 6                               */
+};
+
 /* Rasterizer constants.  gs_default_config() fills the paper's values. */
 typedef struct gs_raster_config {
     int tile_w, tile_h;       /* tile size in pixels: 16 x 16 (Sec. 6); 8 x 8 and 16 x 8 also supported */
@@ -75,6 +81,7 @@ typedef struct gs_raster_config {
     float dilation;           /* 0.3 px^2 low-pass filter added to the diagonal of Sigma'          */
     float guard;              /* 1.3: reject |x/z| > guard * tan(fov_x/2) or |y/z| > guard * tan(fov_y/2) */
     float extent;             /* 3: screen radius = ceil(extent * sqrt(lambda_max(Sigma')))        */
+    int tile_rule;            /* GS_TILES_REACH (default) or GS_TILES_RECT; same images either way */
 } gs_raster_config;
 
 /* Gaussian parameters (Sec. 4): device pointers, n rows each. */
@@ -122,12 +129,15 @@ typedef struct gs_frame {
  *                            Q = Sigma'^-1 = L L^T (power = -|L^T d|^2 / 2) and the opacity
  *   rgb           float4[n]  (r, g, b, bits of the channels clamped at 0)
  *   radius        int32[n]   screen radius in pixels, 0 = culled
+ *   tau           float[n]   2 ln(o / alpha_min): a pixel at offset d is blended only if
+ *                            |L^T d|^2 <= tau (used by gs_bin_sort's tile rule)
  * Instances: sorted Gaussian indices uint32[capacity] at vals_sorted; tile ranges
  * uint32[2 * tiles] ([start, end) into vals_sorted, [0, 0) for empty tiles); keys_sorted: the
  * sorted keys as uint64[capacity] (KEY64 mode) or the sorted tile ids as uint32[capacity]
  * (TWO_PHASE mode). */
 typedef struct gs_layout {
     uint64_t xy, depth, conic_opacity, rgb, radius;
+    uint64_t tau;             /* float[n] alpha level 2 ln(o / alpha_min) of every splat       */
     uint64_t vals_sorted, keys_sorted, ranges;
     uint64_t grad2d;          /* float[n, 12] per-Gaussian screen-space gradient accumulators:
                                  dL/du, dL/dv, dL/dSigma'_00, dL/dSigma'_01, dL/dSigma'_11 (full-
@@ -149,7 +159,7 @@ typedef struct gs_device_status {
 } gs_device_status;
 
 /* Fill cfg with the paper's constants: 16x16 tiles, batch 128, alpha in [1/255, 0.99],
- * T_min 1e-4, dilation 0.3, guard 1.3, extent 3, GS_SORT_TWO_PHASE. */
+ * T_min 1e-4, dilation 0.3, guard 1.3, extent 3, GS_SORT_TWO_PHASE, GS_TILES_REACH. */
 void gs_default_config(gs_raster_config* cfg);
 
 /* Workspace bytes for a frame; 0 if the arguments are invalid. */
@@ -169,9 +179,14 @@ gs_status gs_workspace_layout(int n, int width, int height, uint64_t capacity, c
 gs_status gs_preprocess(const gs_frame* frame, const gs_gaussians* g, cudaStream_t stream);
 
 /* Algorithm 2, DuplicateWithKeys + SortByKeys + IdentifyTileRanges (App. C): one instance per
- * (visible Gaussian, overlapped tile) with key (tile id << 32) | fp32 bits of depth, ordered
+ * (visible Gaussian, tile it can reach) with key (tile id << 32) | fp32 bits of depth, ordered
  * as one stable sort of those keys emitted in (Gaussian index, row-major tile) order, and the
- * [start, end) range of every tile.  The instance count stays on the device (status block);
+ * [start, end) range of every tile.  The tiles are those of the paper's 3-sigma rectangle
+ * (Sec. 6) that hold at least one pixel centre where o G >= alpha_min could hold: per tile row,
+ * the interval of columns where the ellipse |L^T d|^2 <= tau (widened by 2^-10 relative and
+ * absolute, and by 0.01 px) meets the row's pixel centres, in IEEE fp32 round-to-nearest
+ * arithmetic.  Every dropped pair would be skipped by the alpha test at every pixel of its
+ * tile, so the images and gradients are those of the full rectangle.  The instance count stays on the device (status block);
  * if it exceeds frame->capacity, no instance is written past the capacity and the status
  * flag GS_ERR_CAPACITY is raised (the caller grows the workspace and re-runs).
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */

@@ -75,10 +75,10 @@ def _load():
         lib.orc_preprocess.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
                                        I32, D, D, D, D, I32, I32, D, D, U32, I32, I32]
         lib.orc_render_forward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
-                                           D, U8, D, D, I32, U8, U32]
+                                           D, U8, D, D, I32, I32, U8, U32]
         lib.orc_render_backward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
                                             D, U8, D, D, D, D, D, D, D, D, D, D, U8, U32]
-        lib.orc_bin.argtypes = [L, F, F, I32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        lib.orc_bin.argtypes = [L, F, F, I32, F, F, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 L, U64, U32, U32]
         lib.orc_bin.restype = L
         lib.orc_num_threads.restype = ctypes.c_int
@@ -184,7 +184,8 @@ def _mask_arg(cam, cfg, tile_mask):
 
 def render_forward(g, cam, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
     """Planar image [3, H, W], final transmittance [H, W], last contributor (1-based
-    position in the tile list, 0 = none) [H, W], per-pixel and per-Gaussian ambiguity."""
+    position in the tile list, 0 = none) [H, W] and its Gaussian index (-1 = none) [H, W],
+    per-pixel and per-Gaussian ambiguity."""
     cfg = cfg_array() if cfg is None else cfg
     n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
     ca = cam_array(cam)
@@ -194,13 +195,15 @@ def render_forward(g, cam, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, ti
     img = np.zeros((3, H, W))
     T = np.ones((H, W))
     last = np.zeros((H, W), np.int32)
+    last_id = np.full((H, W), -1, np.int32)
     pix = np.zeros((H, W), np.uint8)
     gamb = np.zeros(n, np.uint32)
     D = ctypes.c_double
     _load().orc_render_forward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
                                _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(img, D), _p(T, D),
-                               _p(last, ctypes.c_int32), _p(pix, ctypes.c_uint8), _p(gamb, ctypes.c_uint32))
-    return dict(img=img, T=T, last=last, pix_amb=pix, gauss_amb=gamb)
+                               _p(last, ctypes.c_int32), _p(last_id, ctypes.c_int32), _p(pix, ctypes.c_uint8),
+                               _p(gamb, ctypes.c_uint32))
+    return dict(img=img, T=T, last=last, last_id=last_id, pix_amb=pix, gauss_amb=gamb)
 
 
 def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
@@ -228,22 +231,35 @@ def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None 
     return out
 
 
-def bin_instances(uv, depth, radius, width: int, height: int, tile_w: int = 16, tile_h: int = 16,
-                  capacity: int | None = None):
-    """Binning definition on given fp32 (u, v), fp32 depth and integer radius
-    (radius <= 0: culled).  Returns (keys u64 [K], vals u32 [K], ranges u32 [T, 2])."""
+def _bin_args(uv, depth, radius, chol, tau):
     uv = np.ascontiguousarray(np.asarray(uv, dtype=np.float32).reshape(-1, 2))
-    depth = np.ascontiguousarray(np.asarray(depth, dtype=np.float32).reshape(-1))
-    radius = np.ascontiguousarray(np.asarray(radius, dtype=np.int32).reshape(-1))
     n = uv.shape[0]
+    depth = np.ascontiguousarray(np.asarray(depth if depth is not None else np.zeros(n), dtype=np.float32).reshape(-1))
+    radius = np.ascontiguousarray(np.asarray(radius, dtype=np.int32).reshape(-1))
+    if (chol is None) != (tau is None):
+        raise ValueError("chol and tau go together")
+    if chol is not None:
+        chol = np.ascontiguousarray(np.asarray(chol, dtype=np.float32).reshape(n, 3))
+        tau = np.ascontiguousarray(np.asarray(tau, dtype=np.float32).reshape(n))
+    return n, uv, depth, radius, chol, tau
+
+
+def bin_instances(uv, depth, radius, width: int, height: int, tile_w: int = 16, tile_h: int = 16,
+                  capacity: int | None = None, chol=None, tau=None):
+    """Binning definition on given fp32 (u, v), fp32 depth and integer radius
+    (radius <= 0: culled), over the 3-sigma tile rectangle, or, given the fp32 Cholesky factor
+    (l11, l21, l22) of each conic and tau = 2 ln(o / alpha_min), over the tiles the
+    reachable-tile rule keeps.  Returns (keys u64 [K], vals u32 [K], ranges u32 [T, 2])."""
+    n, uv, depth, radius, chol, tau = _bin_args(uv, depth, radius, chol, tau)
     TX, TY = (width + tile_w - 1) // tile_w, (height + tile_h - 1) // tile_h
     ranges = np.zeros((TX * TY, 2), np.uint32)
     lib = _load()
     if capacity is None:
-        capacity = instance_count(uv, radius, width, height, tile_w, tile_h)
+        capacity = instance_count(uv, radius, width, height, tile_w, tile_h, chol=chol, tau=tau)
     keys = np.zeros(max(capacity, 1), np.uint64)
     vals = np.zeros(max(capacity, 1), np.uint32)
-    K = lib.orc_bin(n, _p(uv, ctypes.c_float), _p(depth, ctypes.c_float), _p(radius, ctypes.c_int32),
+    F = ctypes.c_float
+    K = lib.orc_bin(n, _p(uv, F), _p(depth, F), _p(radius, ctypes.c_int32), _p(chol, F), _p(tau, F),
                     width, height, tile_w, tile_h, capacity, _p(keys, ctypes.c_uint64),
                     _p(vals, ctypes.c_uint32), _p(ranges, ctypes.c_uint32))
     if K < 0:
@@ -251,17 +267,12 @@ def bin_instances(uv, depth, radius, width: int, height: int, tile_w: int = 16, 
     return keys[:K], vals[:K], ranges
 
 
-def instance_count(uv, radius, width, height, tile_w=16, tile_h=16) -> int:
-    """Number of (Gaussian, overlapped tile) instances, by the same rectangle rule."""
-    uv = np.asarray(uv, dtype=np.float32).reshape(-1, 2)
-    radius = np.asarray(radius, dtype=np.int64).reshape(-1)
+def instance_count(uv, radius, width, height, tile_w=16, tile_h=16, chol=None, tau=None) -> int:
+    """Number of (Gaussian, tile) instances, by the same rule as bin_instances."""
+    n, uv, depth, radius, chol, tau = _bin_args(uv, None, radius, chol, tau)
     TX, TY = (width + tile_w - 1) // tile_w, (height + tile_h - 1) // tile_h
-    fu = np.floor(uv[:, 0]).astype(np.int64)
-    fv = np.floor(uv[:, 1]).astype(np.int64)
-    x0 = np.clip(np.floor_divide(fu - radius, tile_w), 0, TX)
-    x1 = np.clip(np.floor_divide(fu + radius, tile_w) + 1, 0, TX)
-    y0 = np.clip(np.floor_divide(fv - radius, tile_h), 0, TY)
-    y1 = np.clip(np.floor_divide(fv + radius, tile_h) + 1, 0, TY)
-    ok = (radius > 0) & (x0 < x1) & (y0 < y1)
-    return int(np.sum(np.where(ok, (x1 - x0) * (y1 - y0), 0)))
+    ranges = np.zeros((TX * TY, 2), np.uint32)
+    F = ctypes.c_float
+    return int(_load().orc_bin(n, _p(uv, F), _p(depth, F), _p(radius, ctypes.c_int32), _p(chol, F), _p(tau, F),
+                               width, height, tile_w, tile_h, 1 << 62, None, None, _p(ranges, ctypes.c_uint32)))
 

@@ -556,11 +556,11 @@ static void mark(unsigned* gamb, int32_t i, unsigned bit) {
  * threshold (see the AMB_* / PIX_* bits).
  */
 static int pixel_forward(const oscene* S, int t, int px, int py, const double* bg, double* out_rgb, double* out_T,
-                         int* out_last, unsigned* out_flags, contrib_t* rec, unsigned* gamb) {
+                         int* out_last, int* out_last_id, unsigned* out_flags, contrib_t* rec, unsigned* gamb) {
     const ocfg* cfg = &S->cfg;
     double pxc = px + 0.5, pyc = py + 0.5;
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
-    int last = 0, nrec = 0;
+    int last = 0, last_id = -1, nrec = 0;
     unsigned flags = 0;
     int64_t a = S->tile_start[t], b = S->tile_start[t + 1];
     uint32_t prev_key = 0;
@@ -616,6 +616,7 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         nrec++;
         T = test_T;
         last = (int)(k - a) + 1;
+        last_id = gi;
     }
     /* Gaussians outside this tile's list that an fp32 binning may add to it. */
     for (int64_t k = S->shadow_start[t]; k < S->shadow_start[t + 1]; ++k) {
@@ -631,6 +632,7 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
     for (int ch = 0; ch < 3; ++ch) out_rgb[ch] = C[ch] + T * bg[ch];
     *out_T = T;
     *out_last = last;
+    if (out_last_id) *out_last_id = last_id;
     *out_flags = flags;
     return nrec;
 }
@@ -675,7 +677,7 @@ void orc_preprocess(long n, const double* means, const double* scales, const dou
 void orc_render_forward(long n, const double* means, const double* scales, const double* quats, const double* opac,
                         const double* sh, int deg, int sh_stride, const double* cam, const double* cfg,
                         const double* bg, const uint8_t* tile_mask, double* out_img, double* out_T, int32_t* out_last,
-                        uint8_t* out_pix_amb, uint32_t* out_gauss_amb) {
+                        int32_t* out_last_id, uint8_t* out_pix_amb, uint32_t* out_gauss_amb) {
     oscene S;
     scene_init(&S, n, means, scales, quats, opac, sh, deg, sh_stride, cam, cfg);
     scene_build(&S, tile_mask);
@@ -691,9 +693,10 @@ void orc_render_forward(long n, const double* means, const double* scales, const
             for (int lx = 0; lx < S.cfg.tile_w; ++lx) {
                 int px = tx * S.cfg.tile_w + lx, py = ty * S.cfg.tile_h + ly;
                 if (px >= W || py >= H) continue;
-                double rgb[3], Tf; int last; unsigned flags;
-                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &flags, NULL, out_gauss_amb);
+                double rgb[3], Tf; int last, last_id; unsigned flags;
+                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &last_id, &flags, NULL, out_gauss_amb);
                 size_t p = (size_t)py * W + px;
+                if (out_last_id) out_last_id[p] = last_id;
                 for (int ch = 0; ch < 3; ++ch) out_img[ch * P + p] = rgb[ch];
                 out_T[p] = Tf;
                 out_last[p] = last;
@@ -747,7 +750,7 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                     if (px >= W || py >= H) continue;
                     size_t p = (size_t)py * W + px;
                     double rgb[3], Tf; int last; unsigned flags;
-                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &flags, rec, out_gauss_amb);
+                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, NULL, &flags, rec, out_gauss_amb);
                     if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
                     double dC[3] = {dL_dimg[p], dL_dimg[P + p], dL_dimg[2 * P + p]};
                     /* R = colour accumulated behind the current Gaussian, normalised by the
@@ -880,12 +883,76 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
 }
 
 /* ------------------------------------------------------------------------- */
+/* Reachable-tile rule (this implementation's refinement of the Sec. 6 tile      */
+/* rectangle; the paper has no counterpart).  A pixel at offset d from the mean   */
+/* is blended only if o exp(-|L^T d|^2 / 2) >= alpha_min, i.e. |L^T d|^2 <= tau,  */
+/* tau = 2 ln(o / alpha_min), with L = [[l11, 0], [l21, l22]] the Cholesky factor */
+/* of the conic.  Of the rectangle's tiles, a row keeps the column interval whose */
+/* pixel centres meet the (slightly widened) ellipse.  The decision is taken in   */
+/* IEEE fp32 round-to-nearest arithmetic, written out step by step below, which  */
+/* is the precision the rasterizer decides it in; -ffp-contract=off keeps every  */
+/* product and sum separately rounded.                                            */
+/*   t    = tau (1 + 2^-10) + 2^-10           (no tiles when t <= 0)             */
+/*   ylim = sqrt(t) / l22                      (|dy| bound of the ellipse)         */
+/*   S    = (L L^T)^-1:  S00 = (l21^2 + l22^2) / (l11 l22)^2,                     */
+/*                       S01 = -l21 / ((l11 l22) l22)                             */
+/*   y*   = S01 sqrt(t / S00)                  (dy of the ellipse's rightmost point) */
+/*   X(y, s) = (s sqrt(max(t - (l22 y)^2, 0)) - l21 y) / l11                      */
+/* Row ty: pixel-centre offsets dy in [ya, yb] = [ty th + 0.5 - v, ty th + th - 0.5 - v] */
+/* clipped to [-ylim, ylim]; the rightmost reach over that band is X(clip(y*), +1), */
+/* the leftmost X(clip(-y*), -1) (each branch is concave/convex in y); widened by */
+/* 0.01 px they bound the columns px with px + 0.5 - u inside; the tiles holding  */
+/* those columns, cut to the rectangle, are kept.                                 */
+/* ------------------------------------------------------------------------- */
+static float reach_x32(float t, float l11, float l21, float l22, float y, float s) {
+    float q = l22 * y;
+    float q2 = q * q;
+    float h = t - q2;
+    h = sqrtf(h > 0.0f ? h : 0.0f);
+    float num = s * h - l21 * y;
+    return num / l11;
+}
+
+static float clampf32(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* Columns [*txa, *txb) of tile row ty inside the rectangle columns [x0, x1). */
+static int reach_row32(const float* L, float tau, float u, float v, int ty, int tw, int th, int x0, int x1,
+                       int* txa, int* txb) {
+    const float w = 0.0009765625f;
+    float t = tau * (1.0f + w) + w;
+    if (!(t > 0.0f)) return 0;
+    float l11 = L[0], l21 = L[1], l22 = L[2];
+    float ylim = sqrtf(t) / l22;
+    float a = l11 * l22;
+    float s00 = (l21 * l21 + l22 * l22) / (a * a);
+    float s01 = (-l21) / (a * l22);
+    float ystar = s01 * sqrtf(t / s00);
+    float ya = ((float)(ty * th) + 0.5f) - v;
+    float yb = ((float)(ty * th + th) - 0.5f) - v;
+    if (ya < -ylim) ya = -ylim;
+    if (yb > ylim) yb = ylim;
+    if (ya > yb) return 0;
+    float xb = reach_x32(t, l11, l21, l22, clampf32(ystar, ya, yb), 1.0f) + 0.01f;
+    float xa = reach_x32(t, l11, l21, l22, clampf32(-ystar, ya, yb), -1.0f) - 0.01f;
+    float fa = ceilf((u + xa) - 0.5f), fb = floorf((u + xb) - 0.5f);
+    const float lim = 1048576.0f;
+    int pa = (int)clampf32(fa, -lim, lim), pb = (int)clampf32(fb, -lim, lim);
+    if (pb < pa) return 0;
+    int lo = floor_div(pa, tw), hi = floor_div(pb, tw) + 1;
+    *txa = lo > x0 ? lo : x0;
+    *txb = hi < x1 ? hi : x1;
+    return *txa < *txb;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Exported: binning definition (App. C) on given fp32 screen-space values.     */
-/* Emits one key per (Gaussian, overlapped tile) in Gaussian order then row-major */
-/* tile order, key = (tile id << 32) | fp32 bits of depth, stable-sorts by key    */
-/* (ties keep emission order), and finds each tile's [start, end).               */
-/* radius <= 0 marks a culled Gaussian.  Returns the number of instances, or      */
-/* -1 if it exceeds capacity (nothing written past capacity).                     */
+/* Emits one key per (Gaussian, tile) in Gaussian order then row-major tile      */
+/* order, key = (tile id << 32) | fp32 bits of depth, stable-sorts by key (ties   */
+/* keep emission order), and finds each tile's [start, end).  The tiles are the   */
+/* 3-sigma rectangle's (Sec. 6); when chol and tau are given, only those the     */
+/* reachable-tile rule above keeps.  radius <= 0 marks a culled Gaussian.         */
+/* Returns the number of instances, or -1 if it exceeds capacity (nothing is     */
+/* written past capacity).                                                       */
 /* ------------------------------------------------------------------------- */
 typedef struct { uint64_t key; int64_t seq; uint32_t val; } inst_t;
 
@@ -896,35 +963,46 @@ static int cmp_inst(const void* a, const void* b) {
     return (x->seq > y->seq) - (x->seq < y->seq);
 }
 
-long orc_bin(long n, const float* uv, const float* depth, const int32_t* radius, int width, int height,
-             int tile_w, int tile_h, long capacity, uint64_t* keys, uint32_t* vals, uint32_t* ranges) {
+/* Tiles of Gaussian i in row ty: [*a, *b); 0 if none. */
+static int bin_row(long i, int ty, const float* uv, const int32_t* radius, const float* chol, const float* tau,
+                   int TX, int TY, int tile_w, int tile_h, int* a, int* b) {
+    if (radius[i] <= 0) return 0;
+    int fu = (int)floorf(uv[2 * i]), fv = (int)floorf(uv[2 * i + 1]), r = radius[i];
+    int x0 = clampi(floor_div(fu - r, tile_w), 0, TX), x1 = clampi(floor_div(fu + r, tile_w) + 1, 0, TX);
+    int y0 = clampi(floor_div(fv - r, tile_h), 0, TY), y1 = clampi(floor_div(fv + r, tile_h) + 1, 0, TY);
+    if (ty < y0 || ty >= y1 || x0 >= x1) return 0;
+    if (!chol) { *a = x0; *b = x1; return 1; }
+    return reach_row32(&chol[3 * i], tau[i], uv[2 * i], uv[2 * i + 1], ty, tile_w, tile_h, x0, x1, a, b);
+}
+
+long orc_bin(long n, const float* uv, const float* depth, const int32_t* radius, const float* chol, const float* tau,
+             int width, int height, int tile_w, int tile_h, long capacity, uint64_t* keys, uint32_t* vals,
+             uint32_t* ranges) {
     int TX = (width + tile_w - 1) / tile_w, TY = (height + tile_h - 1) / tile_h;
     long K = 0;
-    for (long i = 0; i < n; ++i) {
-        if (radius[i] <= 0) continue;
-        int fu = (int)floorf(uv[2 * i]), fv = (int)floorf(uv[2 * i + 1]), r = radius[i];
-        int x0 = clampi(floor_div(fu - r, tile_w), 0, TX), x1 = clampi(floor_div(fu + r, tile_w) + 1, 0, TX);
-        int y0 = clampi(floor_div(fv - r, tile_h), 0, TY), y1 = clampi(floor_div(fv + r, tile_h) + 1, 0, TY);
-        if (x0 < x1 && y0 < y1) K += (long)(x1 - x0) * (y1 - y0);
-    }
+    for (long i = 0; i < n; ++i)
+        for (int ty = 0; ty < TY; ++ty) {
+            int a, b;
+            if (bin_row(i, ty, uv, radius, chol, tau, TX, TY, tile_w, tile_h, &a, &b)) K += b - a;
+        }
     for (long t = 0; t < (long)TX * TY; ++t) { ranges[2 * t] = 0; ranges[2 * t + 1] = 0; }
-    if (K > capacity) return -1;
+    if (K > capacity) return -K;
+    if (!keys) return K;
     inst_t* inst = (inst_t*)malloc(sizeof(inst_t) * (size_t)(K ? K : 1));
     long k = 0;
     for (long i = 0; i < n; ++i) {
-        if (radius[i] <= 0) continue;
-        int fu = (int)floorf(uv[2 * i]), fv = (int)floorf(uv[2 * i + 1]), r = radius[i];
-        int x0 = clampi(floor_div(fu - r, tile_w), 0, TX), x1 = clampi(floor_div(fu + r, tile_w) + 1, 0, TX);
-        int y0 = clampi(floor_div(fv - r, tile_h), 0, TY), y1 = clampi(floor_div(fv + r, tile_h) + 1, 0, TY);
         uint32_t dbits;
         memcpy(&dbits, &depth[i], 4);
-        for (int ty = y0; ty < y1; ++ty)
-            for (int tx = x0; tx < x1; ++tx) {
+        for (int ty = 0; ty < TY; ++ty) {
+            int a, b;
+            if (!bin_row(i, ty, uv, radius, chol, tau, TX, TY, tile_w, tile_h, &a, &b)) continue;
+            for (int tx = a; tx < b; ++tx) {
                 inst[k].key = ((uint64_t)(uint32_t)(ty * TX + tx) << 32) | dbits;
                 inst[k].seq = k;
                 inst[k].val = (uint32_t)i;
                 ++k;
             }
+        }
     }
     qsort(inst, (size_t)K, sizeof(inst_t), cmp_inst);
     for (long j = 0; j < K; ++j) {

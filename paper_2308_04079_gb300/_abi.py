@@ -23,6 +23,8 @@ GS_ERR_NUMERIC = 5
 
 GS_SORT_TWO_PHASE = 0
 GS_SORT_KEY64 = 1
+GS_TILES_REACH = 0
+GS_TILES_RECT = 1
 
 FLAG_CAPACITY = 1
 FLAG_TIMEOUT = 2
@@ -36,7 +38,7 @@ class gs_camera(ctypes.Structure):
 class gs_raster_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("batch_depth", c_int), ("sort_mode", c_int),
                 ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float), ("dilation", c_float),
-                ("guard", c_float), ("extent", c_float)]
+                ("guard", c_float), ("extent", c_float), ("tile_rule", c_int)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -56,7 +58,7 @@ class gs_frame(ctypes.Structure):
 
 class gs_layout(ctypes.Structure):
     _fields_ = [("xy", c_uint64), ("depth", c_uint64), ("conic_opacity", c_uint64), ("rgb", c_uint64),
-                ("radius", c_uint64), ("vals_sorted", c_uint64), ("keys_sorted", c_uint64), ("ranges", c_uint64),
+                ("radius", c_uint64), ("tau", c_uint64), ("vals_sorted", c_uint64), ("keys_sorted", c_uint64), ("ranges", c_uint64),
                 ("grad2d", c_uint64), ("status", c_uint64), ("total_bytes", c_uint64), ("tiles_x", c_int),
                 ("tiles_y", c_int), ("key_passes", c_int), ("depth_passes", c_int)]
 

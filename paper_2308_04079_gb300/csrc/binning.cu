@@ -233,27 +233,49 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(SortPassArgs<KeyT>
 }
 
 // ---------------------------------------------------------------------------------------
-// Scan of tiles per Gaussian (in `order`) with chained look-back.  Per Gaussian it stores the
-// exclusive instance offset and the tile rectangle, and adds the rectangle's four corners to a
-// 2D difference grid over the tiles (+1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and (x0, y1));
-// its 2D prefix sum is the number of instances of every tile, from which k_tile_ranges derives
-// the tile ranges and the digit histograms of the tile-id sort passes.  In KEY64 mode the depth
-// digits of the four low passes are constant per Gaussian: their histograms are weighted by the
-// Gaussian's tile count here.
+// DuplicateWithKeys, first half.  Per Gaussian (in `order`): the 3-sigma tile rectangle, and in
+// each of its rows the interval of tiles the splat can reach (reach_row).  A chained scan with
+// look-back gives each Gaussian its first segment (non-empty row) and first instance; the
+// Gaussian then writes one record per segment (output offset, first tile id, length, Gaussian
+// id) and adds +1 / -1 at the ends of every interval to a per-row difference grid whose prefix
+// sums are the instances of every tile (k_tile_ranges).  In KEY64 mode the depth digits of the
+// four low key passes are constant per Gaussian: their histograms are weighted by its tile count.
 // ---------------------------------------------------------------------------------------
+// Look-back words carry (segments, instances) as two 31-bit fields, each saturated at 2^30
+// (above any capacity), so sums over many chunks cannot carry from one field into the other.
+constexpr unsigned long long kPairSat = 1ull << 30;
+constexpr unsigned long long kField = 0x7FFFFFFFull;
+constexpr int kLocalShift = 40;   // block-local packing: segments << 40 | instances (no overflow
+                                  // for 1024 Gaussians of at most 2^24 tiles and 2^13 rows each)
+
+__device__ __forceinline__ unsigned long long pair_word(unsigned long long segs, unsigned long long tiles) {
+    return (min(segs, kPairSat) << 31) | min(tiles, kPairSat);
+}
+
+__device__ __forceinline__ bool tile_row(const Reach& e, int rect_only, float4 m, int ty, const CamK& c, int x0,
+                                         int x1, int& txa, int& txb) {
+    if (rect_only) {
+        txa = x0;
+        txb = x1;
+        return true;
+    }
+    return reach_row(e, m.x, m.y, ty, c.tile_w, c.tile_h, x0, x1, txa, txb);
+}
+
 template <bool KEY64>
 __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
     constexpr int PER = kDupChunk / kDupThreads;
     __shared__ uint32_t s_hist[KEY64 ? 4 : 1][256];
-    __shared__ uint32_t s_scan[33];
+    __shared__ unsigned long long s_scan[33];
     __shared__ uint32_t s_chunk;
-    __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_base_s, s_base_t;
     const int tid = threadIdx.x;
     uint32_t count = (uint32_t)a.n;
     if (a.count_dev) count = min(count, *a.count_dev);
     const uint32_t chunks = (count + kDupChunk - 1) / kDupChunk;
     const CamK& c = a.cam;
     const int gw = c.tiles_x + 1;
+    const unsigned long long cap = a.capacity;
 
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(a.chunk_counter, 1u);
@@ -262,11 +284,10 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
         __syncthreads();
         const uint32_t chunk = s_chunk;
         if (chunk >= chunks) break;
-        uint32_t tiles[PER];
         uint32_t gids[PER];
         int rad[PER];
-        float4 mean[PER];
-        uint32_t run = 0;
+        float4 mean[PER], L[PER];
+        float tau[PER];
         // gather first (independent loads in flight together), then compute
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -280,40 +301,45 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
             const uint32_t j = chunk * kDupChunk + tid * PER + k;
             rad[k] = j < count ? a.radius[gids[k]] : 0;
             mean[k] = a.xy[gids[k]];
+            L[k] = a.conic[gids[k]];
+            tau[k] = a.tau[gids[k]];
         }
+        uint32_t nseg[PER], ntile[PER];
+        int rx0[PER], rx1[PER], ry0[PER], ry1[PER];
+        uint32_t run_s = 0, run_t = 0;
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const uint32_t j = chunk * kDupChunk + tid * PER + k;
-            tiles[k] = 0;
-            uint2 rect = make_uint2(0u, 0u);
-            if (j < count) {
-                const uint32_t gid = gids[k];
-                const int r = rad[k];
-                int x0, x1, y0, y1;
-                if (r > 0 && tile_rect(mean[k], r, c, x0, x1, y0, y1)) {
-                    tiles[k] = (uint32_t)((x1 - x0) * (y1 - y0));
-                    rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)(x1 - x0) | ((uint32_t)(y1 - y0) << 16));
-                    atomicAdd(&a.diff[y0 * gw + x0], 1);
-                    atomicAdd(&a.diff[y0 * gw + x1], -1);
-                    atomicAdd(&a.diff[y1 * gw + x0], -1);
-                    atomicAdd(&a.diff[y1 * gw + x1], 1);
-                    if (KEY64) {
-                        const uint32_t db = __float_as_uint(a.depth[gid]);
-#pragma unroll
-                        for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], tiles[k]);
+            nseg[k] = 0;
+            ntile[k] = 0;
+            rx0[k] = rx1[k] = ry0[k] = ry1[k] = 0;
+            if (rad[k] > 0 && tile_rect(mean[k], rad[k], c, rx0[k], rx1[k], ry0[k], ry1[k])) {
+                const Reach e = reach_setup(L[k], tau[k]);
+                for (int ty = ry0[k]; ty < ry1[k]; ++ty) {
+                    int txa, txb;
+                    if (tile_row(e, a.rect_only, mean[k], ty, c, rx0[k], rx1[k], txa, txb)) {
+                        ++nseg[k];
+                        ntile[k] += (uint32_t)(txb - txa);
                     }
                 }
-                a.rect[j] = rect;
+                if (KEY64 && ntile[k]) {
+                    const uint32_t db = __float_as_uint(a.depth[gids[k]]);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], ntile[k]);
+                }
             }
-            run += tiles[k];
+            run_s += nseg[k];
+            run_t += ntile[k];
         }
-        uint32_t block_total;
-        const uint32_t texcl = block_exclusive_scan<uint32_t>(run, s_scan, &block_total);
+        unsigned long long local_total;
+        const unsigned long long local_excl = block_exclusive_scan<unsigned long long>(
+            ((unsigned long long)run_s << kLocalShift) | run_t, s_scan, &local_total);
+        const unsigned long long blk_s = local_total >> kLocalShift;
+        const unsigned long long blk_t = local_total & ((1ull << kLocalShift) - 1);
         // Decoupled look-back by warp 0, 32 predecessors per round of loads.
         if (tid < 32) {
             unsigned long long* my = a.lookback + chunk;
-            unsigned long long excl = 0;
-            if (tid == 0) st_relaxed64(my, (chunk == 0 ? kScanInc : kScanAgg) | block_total);
+            unsigned long long ex_s = 0, ex_t = 0;
+            if (tid == 0) st_relaxed64(my, (chunk == 0 ? kScanInc : kScanAgg) | pair_word(blk_s, blk_t));
             if (chunk > 0) {
                 int j = (int)chunk - 1;
                 uint32_t spins = 0;
@@ -333,31 +359,55 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
                         backoff(spins);
                         continue;
                     }
-                    unsigned long long part = (tid <= first_inc) ? (v & kScanValue) : 0ull;
+                    const bool use = tid <= first_inc;
+                    unsigned long long ps = use ? ((v >> 31) & kField) : 0ull;
+                    unsigned long long pt = use ? (v & kField) : 0ull;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                    excl += part;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        ps += __shfl_xor_sync(0xffffffffu, ps, o);
+                        pt += __shfl_xor_sync(0xffffffffu, pt, o);
+                    }
+                    ex_s = min(ex_s + ps, kPairSat);
+                    ex_t = min(ex_t + pt, kPairSat);
                     if (first_inc < 32) break;
                     j -= 32;
                 }
-                if (tid == 0) st_relaxed64(my, kScanInc | ((excl + block_total) & kScanValue));
+                if (tid == 0) st_relaxed64(my, kScanInc | pair_word(ex_s + blk_s, ex_t + blk_t));
             }
             if (tid == 0) {
-                s_base = excl;
+                s_base_s = ex_s;
+                s_base_t = ex_t;
                 if (chunk == chunks - 1) {
-                    const unsigned long long total = excl + block_total;
-                    a.status->num_instances = (uint32_t)min(total, 0xFFFFFFFFull);
-                    if (total > a.capacity) atomicOr(&a.status->flags, kFlagCapacity);
+                    const unsigned long long segs = min(ex_s + blk_s, kPairSat);
+                    const unsigned long long tiles = min(ex_t + blk_t, kPairSat);
+                    a.status->num_instances = (uint32_t)tiles;
+                    *a.num_segments = (uint32_t)segs;
+                    if (tiles > cap) atomicOr(&a.status->flags, kFlagCapacity);
+                    else a.seg_off[segs] = (uint32_t)tiles;   // end of the last segment
                 }
             }
         }
         __syncthreads();
-        unsigned long long off = s_base + texcl;
+        unsigned long long seg = s_base_s + (local_excl >> kLocalShift);
+        unsigned long long off = s_base_t + (local_excl & ((1ull << kLocalShift) - 1));
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const uint32_t j = chunk * kDupChunk + tid * PER + k;
-            if (j < count) a.start[j] = (uint32_t)min(off, 0xFFFFFFFFull);
-            off += tiles[k];
+            if (nseg[k]) {
+                const Reach e = reach_setup(L[k], tau[k]);
+                for (int ty = ry0[k]; ty < ry1[k]; ++ty) {
+                    int txa, txb;
+                    if (!tile_row(e, a.rect_only, mean[k], ty, c, rx0[k], rx1[k], txa, txb)) continue;
+                    atomicAdd(&a.diff[ty * gw + txa], 1);
+                    atomicAdd(&a.diff[ty * gw + txb], -1);
+                    if (seg < cap) {
+                        a.seg_off[seg] = (uint32_t)min(off, cap);
+                        a.seg_tile[seg] = (uint32_t)(ty * c.tiles_x + txa);
+                        a.seg_gid[seg] = gids[k];
+                    }
+                    ++seg;
+                    off += (uint32_t)(txb - txa);
+                }
+            }
         }
         if (KEY64) {
             __syncthreads();
@@ -371,10 +421,11 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// IdentifyTileRanges from instance counts (one block): 2D prefix sum of the difference grid
-// gives the instances of every tile; their exclusive scan in tile-id order gives [start, end)
-// (clamped to the capacity), exactly the ranges of the sorted instance array.  Also adds the
-// digit histograms of the tile-id radix passes (tile ids are the key bits from key_shift on).
+// IdentifyTileRanges from instance counts (one block): row-wise prefix sums of the difference
+// grid give the instances of every tile; their exclusive scan in tile-id order gives
+// [start, end) (clamped to the capacity; [0, 0) for empty tiles), exactly the ranges of the
+// sorted instance array.  Also adds the digit histograms of the tile-id radix passes (tile ids
+// are the key bits from key_shift on).
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
     __shared__ uint32_t s_hist[kMaxKeyPasses][256];
@@ -382,15 +433,9 @@ __global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int TX = a.tiles_x, TY = a.tiles_y, gw = TX + 1;
     for (int k = tid; k < kMaxKeyPasses * 256; k += nt) (&s_hist[0][0])[k] = 0;
-    // row-wise then column-wise inclusive prefix sums, in place
-    for (int y = tid; y <= TY; y += nt) {
+    for (int y = tid; y < TY; y += nt) {
         int run = 0;
         for (int x = 0; x <= TX; ++x) { run += a.diff[y * gw + x]; a.diff[y * gw + x] = run; }
-    }
-    __syncthreads();
-    for (int x = tid; x <= TX; x += nt) {
-        int run = 0;
-        for (int y = 0; y <= TY; ++y) { run += a.diff[y * gw + x]; a.diff[y * gw + x] = run; }
     }
     __syncthreads();
     const uint32_t T = (uint32_t)(TX * TY);
@@ -425,112 +470,52 @@ __global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// DuplicateWithKeys, load-balanced over output slots: a block writes 2048 consecutive instances.
-// Each thread finds the Gaussian of its first slot by binary search over the exclusive offsets
-// and walks forward; the tile of slot `local` inside a w x h rectangle is (local % w, local / w)
-// (quotient from a float reciprocal, corrected by one step).  Keys and values are staged in
-// shared memory and written out coalesced.
+// DuplicateWithKeys, second half: a warp takes 32 consecutive segment records, whose outputs
+// form one contiguous run; every lane finds the segment of each output position it writes by a
+// 5-step search over the lanes' segment ends, so keys and values are written coalesced.
+// Nothing is written after a capacity overflow or a timed-out scan.
 // ---------------------------------------------------------------------------------------
 template <bool KEY64>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
     using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
-    constexpr int PER = kEmitSlots / kEmitThreads;
-    constexpr int WIN = kEmitSlots + 1;         // offsets of the Gaussians that can own the block's slots
-    __shared__ KeyT s_key[kEmitSlots];
-    __shared__ uint32_t s_val[kEmitSlots];
-    __shared__ uint32_t s_start[WIN];
-    __shared__ uint32_t s_j0;
-    const int tid = threadIdx.x;
-    const unsigned long long K = min((unsigned long long)a.status->num_instances, a.capacity);
-    uint32_t count = (uint32_t)a.n;
-    if (a.count_dev) count = min(count, *a.count_dev);
-    const int TX = a.tiles_x;
+    if (a.status->flags & (kFlagCapacity | kFlagTimeout)) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t K = a.status->num_instances;
+    const uint32_t S = *a.num_segments;
     KeyT* keys_out = reinterpret_cast<KeyT*>(a.keys_out);
-    for (unsigned long long k0 = (unsigned long long)blockIdx.x * kEmitSlots; k0 < K;
-         k0 += (unsigned long long)gridDim.x * kEmitSlots) {
-        if (tid == 0) {
-            // last j with start[j] <= k0 (one global binary search per block)
-            uint32_t lo = 0, hi = count - 1;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (a.start[mid] <= k0) lo = mid;
-                else hi = mid - 1;
-            }
-            s_j0 = lo;
-        }
-        __syncthreads();
-        const uint32_t j0 = s_j0;
-        // Window of offsets start[j0 .. j0 + WIN - 1]; entries past the end act as +infinity.
-        for (int w = tid; w < WIN; w += kEmitThreads)
-            s_start[w] = (j0 + w < count) ? a.start[j0 + w] : 0xFFFFFFFFu;
-        __syncthreads();
-        const unsigned long long first = k0 + (unsigned long long)tid * PER;
-        if (first < K) {
-            // last w with s_start[w] <= first, within the window (a Gaussian owning a slot has at
-            // least one tile, so the owners of the block's 2048 slots start inside the window
-            // unless Gaussians without tiles sit in between)
-            int lo = 0, hi = WIN - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((unsigned long long)s_start[mid] <= first) lo = mid;
-                else hi = mid - 1;
-            }
-            uint32_t j = j0 + (uint32_t)lo;
-            if (lo == WIN - 1) {   // window exhausted: continue the search in global memory
-                uint32_t glo = j, ghi = count - 1;
-                while (glo < ghi) {
-                    const uint32_t mid = (glo + ghi + 1) >> 1;
-                    if (a.start[mid] <= first) glo = mid;
-                    else ghi = mid - 1;
-                }
-                j = glo;
-            }
-            uint32_t st = a.start[j];
-            uint32_t nxt = (j + 1 < count) ? a.start[j + 1] : 0xFFFFFFFFu;
-            uint2 rect = a.rect[j];
-            uint32_t gid = a.order ? a.order[j] : j;
-            if (gid >= (uint32_t)a.n) gid = 0;
-            float inv_w = 1.0f / (float)(rect.y & 0xFFFFu);
-            uint32_t dbits = KEY64 ? __float_as_uint(a.depth[gid]) : 0u;
-#pragma unroll 4
-            for (int i = 0; i < PER; ++i) {
-                const unsigned long long kk = first + i;
-                if (kk >= K) break;
-                while ((unsigned long long)nxt <= kk) {   // advance to the Gaussian owning slot kk
-                    ++j;
-                    st = nxt;
-                    nxt = (j + 1 < count) ? a.start[j + 1] : 0xFFFFFFFFu;
-                    rect = a.rect[j];
-                    gid = a.order ? a.order[j] : j;
-                    if (gid >= (uint32_t)a.n) gid = 0;
-                    inv_w = 1.0f / (float)(rect.y & 0xFFFFu);
-                    if (KEY64) dbits = __float_as_uint(a.depth[gid]);
-                }
-                const int w = (int)(rect.y & 0xFFFFu);
-                const int local = (int)(kk - st);
-                int qy = (int)(((float)local + 0.5f) * inv_w);
-                int rx = local - qy * w;
-                if (rx < 0) { --qy; rx += w; }
-                if (rx >= w) { ++qy; rx -= w; }
-                const uint32_t tile =
-                    (uint32_t)(((int)(rect.x >> 16) + qy) * TX + (int)(rect.x & 0xFFFFu) + rx);
-                const int slot = tid * PER + i;
-                if (KEY64) s_key[slot] = (KeyT)(((unsigned long long)tile << 32) | dbits);
-                else s_key[slot] = (KeyT)tile;
-                s_val[slot] = gid;
-            }
-        }
-        __syncthreads();
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; s0 < S; s0 += warps * 32u) {
+        const uint32_t sidx = s0 + (uint32_t)lane;
+        const bool valid = sidx < S;
+        const uint32_t beg = valid ? a.seg_off[sidx] : K;
+        const uint32_t end = valid ? a.seg_off[sidx + 1] : 0xFFFFFFFFu;   // seg_off[S] = K
+        const uint32_t tile0 = valid ? a.seg_tile[sidx] : 0u;
+        uint32_t gid = valid ? a.seg_gid[sidx] : 0u;
+        if (gid >= (uint32_t)a.n) gid = 0;
+        uint32_t dbits = 0;
+        if (KEY64 && valid) dbits = __float_as_uint(a.depth[gid]);
+        const uint32_t out0 = __shfl_sync(0xffffffffu, beg, 0);
+        const uint32_t last_lane = min(31u, S - 1u - s0);
+        const uint32_t out1 = min(__shfl_sync(0xffffffffu, end, last_lane), K);
+        for (uint32_t base = out0; base < out1; base += 32u) {   // warp-uniform trip count
+            const uint32_t out = base + (uint32_t)lane;
+            // segment of position out: the first lane whose segment ends after it
+            int lo = 0;
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int slot = i * kEmitThreads + tid;
-            const unsigned long long kk = k0 + slot;
-            if (kk < K) {
-                keys_out[kk] = s_key[slot];
-                a.vals_out[kk] = s_val[slot];
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, end, lo + step - 1);
+                if (e <= out) lo += step;
+            }
+            const uint32_t sb = __shfl_sync(0xffffffffu, beg, lo);
+            const uint32_t tile = __shfl_sync(0xffffffffu, tile0, lo) + (out - sb);
+            const uint32_t g = __shfl_sync(0xffffffffu, gid, lo);
+            const uint32_t db = __shfl_sync(0xffffffffu, dbits, lo);
+            if (out < out1) {
+                if (KEY64) keys_out[out] = (KeyT)(((unsigned long long)tile << 32) | db);
+                else keys_out[out] = (KeyT)tile;
+                a.vals_out[out] = g;
             }
         }
-        __syncthreads();
     }
 }
 

@@ -22,12 +22,12 @@ int bits_for(uint32_t v) {
 }
 
 struct Layout {
-    size_t control, xy, depth, conic, rgb, radius;
+    size_t control, xy, depth, conic, rgb, radius, tau;
     size_t gkey[2], gval[2];
     size_t scan_lb, sort_lb[2];
     size_t ikey[2], ival[2];
     size_t ranges, grad2d, total;
-    size_t start, rect, diff, diff_count;
+    size_t diff, diff_count;
     size_t sort_lb_rows, scan_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes;
 };
@@ -39,6 +39,7 @@ bool valid_cfg(const gs_raster_config* c) {
     if (!shape_ok) return false;
     if (c->batch_depth < 1 || c->batch_depth > c->tile_w * c->tile_h) return false;
     if (c->sort_mode != GS_SORT_TWO_PHASE && c->sort_mode != GS_SORT_KEY64) return false;
+    if (c->tile_rule != GS_TILES_REACH && c->tile_rule != GS_TILES_RECT) return false;
     if (!(c->alpha_min > 0.f && c->alpha_min < c->alpha_max && c->alpha_max < 1.f)) return false;
     if (!(c->T_min > 0.f && c->T_min < 1.f) || !(c->dilation >= 0.f) || !(c->guard > 0.f) || !(c->extent > 0.f))
         return false;
@@ -70,9 +71,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->conic = take(nn * sizeof(float4));
     L->rgb = take(nn * sizeof(float4));
     L->radius = take(nn * sizeof(int));
+    L->tau = take(nn * sizeof(float));
     for (int k = 0; k < 2; ++k) { L->gkey[k] = take(nn * 4); L->gval[k] = take(nn * 4); }
-    L->start = take(nn * sizeof(uint32_t));
-    L->rect = take(nn * sizeof(uint2));
     L->diff_count = (size_t)(L->tiles_x + 1) * (L->tiles_y + 1);
     L->diff = take(L->diff_count * sizeof(int));
     L->scan_lb_rows = (nn + kDupChunk - 1) / kDupChunk;
@@ -80,7 +80,9 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     const size_t rows_n = (nn + kSortTile - 1) / kSortTile, rows_c = (cc + kSortTileMin - 1) / kSortTileMin;
     L->sort_lb_rows = rows_n > rows_c ? rows_n : rows_c;
     for (int k = 0; k < 2; ++k) L->sort_lb[k] = take(L->sort_lb_rows * 256 * sizeof(uint32_t));
-    for (int k = 0; k < 2; ++k) { L->ikey[k] = take(cc * 8); L->ival[k] = take(cc * 4); }
+    // ikey[1] / ival[1] also hold the segment records between the scan and the emit kernel:
+    // first tiles and offsets (capacity + 1 entries) in ikey[1], Gaussian ids in ival[1].
+    for (int k = 0; k < 2; ++k) { L->ikey[k] = take(cc * 8 + 16); L->ival[k] = take(cc * 4); }
     L->ranges = take((size_t)L->tiles * 2 * sizeof(uint32_t));
     L->grad2d = take(nn * 12 * sizeof(float));
     L->total = off;
@@ -187,6 +189,7 @@ void gs_default_config(gs_raster_config* cfg) {
     cfg->dilation = 0.3f;
     cfg->guard = 1.3f;
     cfg->extent = 3.0f;
+    cfg->tile_rule = GS_TILES_REACH;
 }
 
 size_t gs_workspace_size(int n, int width, int height, uint64_t capacity, const gs_raster_config* cfg) {
@@ -204,6 +207,7 @@ gs_status gs_workspace_layout(int n, int width, int height, uint64_t capacity, c
     out->conic_opacity = L.conic;
     out->rgb = L.rgb;
     out->radius = L.radius;
+    out->tau = L.tau;
     out->vals_sorted = vals_sorted_off(L);
     out->keys_sorted = keys_sorted_off(L);
     out->ranges = L.ranges;
@@ -235,6 +239,7 @@ gs_status gs_preprocess(const gs_frame* f, const gs_gaussians* g, cudaStream_t s
     a.conic_opacity = at<float4>(ws, L.conic);
     a.rgb = at<float4>(ws, L.rgb);
     a.radius = at<int>(ws, L.radius);
+    a.tau = at<float>(ws, L.tau);
     a.status = &ctl->status;
     return ok(launch_preprocess(a, s));
 }
@@ -258,11 +263,16 @@ gs_status gs_bin_sort(const gs_frame* f, cudaStream_t s) {
     ScanArgs d;
     d.n = f->n;
     d.xy = at<float4>(ws, L.xy);
+    d.conic = at<float4>(ws, L.conic);
+    d.tau = at<float>(ws, L.tau);
     d.radius = at<int>(ws, L.radius);
     d.depth = at<float>(ws, L.depth);
     d.cam = cam;
-    d.start = at<uint32_t>(ws, L.start);
-    d.rect = at<uint2>(ws, L.rect);
+    d.seg_tile = at<uint32_t>(ws, L.ikey[1]);
+    d.seg_off = d.seg_tile + (f->capacity > 0 ? f->capacity : 1);
+    d.seg_gid = at<uint32_t>(ws, L.ival[1]);
+    d.num_segments = &ctl->counters[30];
+    d.rect_only = f->cfg.tile_rule == GS_TILES_RECT;
     d.diff = at<int>(ws, L.diff);
     d.capacity = f->capacity;
     d.hist = &ctl->hist_keys[0][0];
@@ -314,13 +324,12 @@ gs_status gs_bin_sort(const gs_frame* f, cudaStream_t s) {
     tr.capacity = f->capacity;
     if (launch_tile_ranges(tr, s) != cudaSuccess) return GS_ERR_CUDA;
     EmitArgs e;
-    e.order = d.order;
-    e.count_dev = d.count_dev;
     e.n = f->n;
-    e.start = d.start;
-    e.rect = d.rect;
+    e.seg_off = d.seg_off;
+    e.seg_tile = d.seg_tile;
+    e.seg_gid = d.seg_gid;
+    e.num_segments = d.num_segments;
     e.depth = d.depth;
-    e.tiles_x = L.tiles_x;
     e.keys_out = at<void>(ws, L.ikey[0]);
     e.vals_out = at<uint32_t>(ws, L.ival[0]);
     e.capacity = f->capacity;

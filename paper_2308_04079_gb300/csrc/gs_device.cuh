@@ -140,6 +140,71 @@ __device__ __forceinline__ bool tile_rect(float4 m, int r, const CamK& c, int& x
     return x0 < x1 && y0 < y1;
 }
 
+// ---- tiles a splat can reach ---------------------------------------------------------------
+// A pixel at offset d from the mean is blended only if o exp(-d^T Q d / 2) >= alpha_min, i.e.
+// d^T Q d <= tau = 2 ln(o / alpha_min) (Q = Sigma'^-1 = L L^T).  Inside the 3-sigma tile rectangle
+// only tiles holding such a pixel are instantiated; every other tile would skip the splat at
+// every pixel, so the image and the gradients are those of the full rectangle.  Per tile row,
+// the pixel centres of the row form a band of offsets y in [ya, yb]; the ellipse d^T Q d <= tau
+// restricted to the band spans x in [xa, xb], where the right end x(y) = (sqrt(tau - (l22 y)^2) -
+// l21 y) / l11 is concave in y and is largest at the band-clamped y of the ellipse's rightmost
+// point (symmetrically for the left end).  tau is widened by 2^-10 (relative and absolute) and
+// the interval by 0.01 px so that rounding never drops a tile the per-pixel test keeps.  Only
+// correctly rounded operations are used, in a fixed order, so the rule is reproducible
+// bit for bit.
+struct Reach {
+    float tm, ylim, ystar, l11, l21, l22;
+    bool any;
+};
+
+__device__ __forceinline__ Reach reach_setup(float4 L, float tau) {
+    Reach e;
+    e.l11 = L.x;
+    e.l21 = L.y;
+    e.l22 = L.z;
+    e.tm = __fadd_rn(__fmul_rn(tau, 1.0f + 0.0009765625f), 0.0009765625f);
+    e.any = e.tm > 0.f;
+    if (!e.any) return e;
+    const float sq = __fsqrt_rn(e.tm);
+    e.ylim = __fdiv_rn(sq, e.l22);
+    const float a = __fmul_rn(e.l11, e.l22);
+    const float qi00 = __fdiv_rn(__fadd_rn(__fmul_rn(e.l21, e.l21), __fmul_rn(e.l22, e.l22)), __fmul_rn(a, a));
+    const float qi01 = __fdiv_rn(-e.l21, __fmul_rn(a, e.l22));
+    e.ystar = __fmul_rn(qi01, __fsqrt_rn(__fdiv_rn(e.tm, qi00)));
+    return e;
+}
+
+__device__ __forceinline__ float reach_x(const Reach& e, float y, float sgn) {
+    const float q = __fmul_rn(e.l22, y);
+    const float h = __fsqrt_rn(fmaxf(__fsub_rn(e.tm, __fmul_rn(q, q)), 0.0f));
+    return __fdiv_rn(__fsub_rn(__fmul_rn(sgn, h), __fmul_rn(e.l21, y)), e.l11);
+}
+
+// Tiles [txa, txb) of tile row ty (inside the rectangle columns [x0, x1)) that the splat with
+// screen mean (u, v) can reach; false when none.
+__device__ __forceinline__ bool reach_row(const Reach& e, float u, float v, int ty, int tw, int th, int x0, int x1,
+                                          int& txa, int& txb) {
+    if (!e.any) return false;
+    float ya = __fsub_rn(__fadd_rn((float)(ty * th), 0.5f), v);
+    float yb = __fsub_rn(__fsub_rn((float)(ty * th + th), 0.5f), v);
+    ya = fmaxf(ya, -e.ylim);
+    yb = fminf(yb, e.ylim);
+    if (ya > yb) return false;
+    const float yr = fminf(fmaxf(e.ystar, ya), yb);
+    const float yl = fminf(fmaxf(-e.ystar, ya), yb);
+    const float xb = __fadd_rn(reach_x(e, yr, 1.0f), 0.01f);
+    const float xa = __fsub_rn(reach_x(e, yl, -1.0f), 0.01f);
+    // pixel columns px with px + 0.5 - u in [xa, xb]
+    const float fa = ceilf(__fsub_rn(__fadd_rn(u, xa), 0.5f));
+    const float fb = floorf(__fsub_rn(__fadd_rn(u, xb), 0.5f));
+    const float lim = 1048576.0f;
+    const int pa = (int)fminf(fmaxf(fa, -lim), lim), pb = (int)fminf(fmaxf(fb, -lim), lim);
+    if (pb < pa) return false;
+    txa = max(x0, floor_div(pa, tw));
+    txb = min(x1, floor_div(pb, tw) + 1);
+    return txa < txb;
+}
+
 // alpha = min(alpha_max, o * G), G = exp(power).  Returns o * G (unclamped) in oG.
 __device__ __forceinline__ float splat_alpha(float power, float o, float alpha_max, float& G, float& oG) {
     G = __expf(power);

@@ -26,9 +26,8 @@ constexpr int kDepthPasses = 4;
 // Scan of tiles per Gaussian: 256 threads, 4 Gaussians per thread.
 constexpr int kDupThreads = 256;
 constexpr int kDupChunk = 1024;
-// Instance emission: 256 threads write 2048 consecutive instances.
+// Instance emission: 256 threads, one warp per 32 segment records.
 constexpr int kEmitThreads = 256;
-constexpr int kEmitSlots = 2048;
 
 // Render: one block per tile, 4 threads per tile row, each owning tile_w / 4 pixels.
 
@@ -36,7 +35,8 @@ constexpr int kEmitSlots = 2048;
 struct Control {
     gs_device_status status;
     uint32_t counters[32];                      // chunk-claim counters: [0] scan, [1..4] depth, [8..15] keys;
-                                                // [31] visible Gaussians counted by the binning stage
+                                                // [30] segment records, [31] visible Gaussians
+                                                // counted by the binning stage
     uint32_t hist_depth[kDepthPasses][256];     // digit histograms, depth sort
     uint32_t hist_keys[kMaxKeyPasses][256];     // digit histograms, instance sort
 };
@@ -56,6 +56,7 @@ struct PreprocessArgs {
     float4* conic_opacity;
     float4* rgb;
     int* radius;
+    float* tau;               // alpha-threshold level 2 ln(o / alpha_min) (reach_setup)
     gs_device_status* status;
 };
 
@@ -113,12 +114,17 @@ struct ScanArgs {
     const uint32_t* count_dev; // number of entries of `order` to use, or null (n)
     int n;
     const float4* xy;
+    const float4* conic;       // (l11, l21, l22, o)
+    const float* tau;          // alpha-threshold level per Gaussian
+    int rect_only;             // 1: every tile of the 3-sigma rectangle (GS_TILES_RECT)
     const int* radius;
     const float* depth;
     CamK cam;
-    uint32_t* start;           // [n] exclusive instance offset per (sorted) Gaussian
-    uint2* rect;               // [n] (x0 | y0 << 16, w | h << 16) per (sorted) Gaussian
-    int* diff;                 // [(tiles_y + 1) * (tiles_x + 1)] 2D difference grid, zeroed
+    uint32_t* seg_off;         // [capacity + 1] first instance of every segment; [S] = K
+    uint32_t* seg_tile;        // [capacity] first tile id of every segment
+    uint32_t* seg_gid;         // [capacity] Gaussian of every segment
+    uint32_t* num_segments;
+    int* diff;                 // [tiles_y * (tiles_x + 1)] per-row difference grid, zeroed
     unsigned long long capacity;
     uint32_t* hist;            // [4][256] depth-digit histograms (KEY64 only)
     unsigned long long* lookback;  // [chunks], zeroed
@@ -127,7 +133,7 @@ struct ScanArgs {
 };
 
 struct TileRangesArgs {
-    int* diff;                 // difference grid, turned into per-tile counts in place
+    int* diff;                 // per-row difference grid, turned into per-tile counts in place
     int tiles_x, tiles_y;
     uint32_t* ranges;
     uint32_t* hist;            // [tile_passes][256] histograms of the tile-id passes
@@ -137,13 +143,12 @@ struct TileRangesArgs {
 };
 
 struct EmitArgs {
-    const uint32_t* order;
-    const uint32_t* count_dev;
     int n;
-    const uint32_t* start;
-    const uint2* rect;
+    const uint32_t* seg_off;
+    const uint32_t* seg_tile;
+    const uint32_t* seg_gid;
+    const uint32_t* num_segments;
     const float* depth;
-    int tiles_x;
     void* keys_out;
     uint32_t* vals_out;
     unsigned long long capacity;

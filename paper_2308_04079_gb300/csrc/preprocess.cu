@@ -190,6 +190,9 @@ __global__ void __launch_bounds__(256) k_preprocess_t(PreprocessArgs a) {
         a.conic_opacity[i] = co;
         a.rgb[i] = rgb;
         a.radius[i] = radius;
+        // alpha >= alpha_min  <=>  d^T Q d <= 2 ln(o / alpha_min): the level the binning
+        // stage intersects with each tile row (reach_setup).
+        a.tau[i] = visible ? 2.0f * (logf(o) - logf(a.cfg.alpha_min)) : 0.0f;
     }
     const uint32_t vis = __ballot_sync(0xffffffffu, visible);
     if ((threadIdx.x & 31) == 0 && vis) atomicAdd(&a.status->num_visible, (uint32_t)__popc(vis));

@@ -47,13 +47,32 @@ struct Staged {
     float4 b;   // (l11', l21', l22', 1/o)
 };
 
-__device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s) {
+__device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s,
+                                            float2& lim) {
     const float ox = tile_offset(x0, m.x, m.z);
     const float oy = tile_offset(y0, m.y, m.w);
     const float lo = __log2f(L.w);
-    s.a = make_float4(ox, oy, __fsub_rn(lo, log2_amin), lo);
+    const float thr = __fsub_rn(lo, log2_amin);
+    s.a = make_float4(ox, oy, thr, lo);
     s.b = make_float4(__fmul_rn(L.x, kScaleLog2), __fmul_rn(L.y, kScaleLog2), __fmul_rn(L.z, kScaleLog2),
                       __frcp_rn(L.w));
+    // Half-widths of the bounding box of the ellipse s = d^T Q' d <= thr (Q' = L' L'^T):
+    // sqrt(thr (Q'^-1)_00) and sqrt(thr (Q'^-1)_11), widened by a small margin so that the
+    // box test below never drops a pixel that the per-pixel test would keep.
+    if (thr > 0.f) {
+        const float l11 = s.b.x, l21 = s.b.y, l22 = s.b.z;
+        const float xl = sqrtf(thr * (l21 * l21 + l22 * l22)) / (l11 * l22);
+        const float yl = sqrtf(thr) / l22;
+        lim = make_float2(xl * 1.001f + 0.01f, yl * 1.001f + 0.01f);
+    } else {
+        lim = make_float2(-1e30f, -1e30f);   // never reaches alpha >= alpha_min
+    }
+}
+
+// True when no pixel of the warp's 8 tile rows can be within the splat's box: the warp skips
+// the splat (the test is uniform across the warp).
+__device__ __forceinline__ bool warp_misses(const Staged& s, float2 lim, float wy0, float wx1) {
+    return (s.a.x > lim.x) | (s.a.x + wx1 < -lim.x) | (wy0 + s.a.y > lim.y) | (wy0 + 7.0f + s.a.y < -lim.y);
 }
 
 // Per (thread row, splat): p at the thread's first pixel, its step to the next owned pixel, q, q^2.
@@ -78,6 +97,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
+    float2* s_lim = reinterpret_cast<float2*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
     const CamK& c = a.cam;
     const int tile = blockIdx.x;
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
@@ -86,6 +106,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
     const int x0 = tx * c.tile_w, y0 = ty * c.tile_h;
     const int py = y0 + ly;
     const float lyf = (float)ly, c0f = (float)c0;
+    const float wy0 = (float)((threadIdx.x >> 5) * 8), wx1 = (float)(c.tile_w - 1);
     const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
     const float amax = a.cfg.alpha_max, tmin = a.cfg.T_min;
     const float log2_amin = __log2f(a.cfg.alpha_min);
@@ -109,14 +130,17 @@ __global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
             uint32_t g = a.vals[b + k];
             if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
             Staged st;
-            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
+            float2 lim;
+            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st, lim);
             s_sp[k] = st;
             s_rgb[k] = a.rgb[g];
+            s_lim[k] = lim;
         }
         __syncthreads();
         if (ndone < PX) {
             for (int k = 0; k < nb; ++k) {
                 const Staged st = s_sp[k];
+                if (warp_misses(st, s_lim[k], wy0, wx1)) continue;
                 float p0, dp, q, qq;
                 splat_row(st, lyf, c0f, p0, dp, q, qq);
                 if (qq > st.a.z) continue;                         // s >= q^2: the whole row skips
@@ -165,7 +189,9 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
-    uint32_t* s_idx = reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
+    float2* s_lim = reinterpret_cast<float2*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
+    uint32_t* s_idx =
+        reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * a.batch);
     __shared__ uint32_t s_max;
     const CamK& c = a.cam;
     const int tile = blockIdx.x;
@@ -176,6 +202,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
     const int py = y0 + ly;
     const float lyf = (float)ly, c0f = (float)c0;
     const uint32_t start = a.ranges[2 * tile], len = a.ranges[2 * tile + 1] - start;
+    const float wy0 = (float)((threadIdx.x >> 5) * 8), wx1 = (float)(c.tile_w - 1);
     const float amax = a.cfg.alpha_max;
     const float log2_amin = __log2f(a.cfg.alpha_min);
     const size_t P = (size_t)c.W * c.H;
@@ -216,9 +243,11 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
             uint32_t g = a.vals[start + (uint32_t)(bend - 1 - k)];
             if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
             Staged st;
-            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
+            float2 lim;
+            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st, lim);
             s_sp[k] = st;
             s_rgb[k] = a.rgb[g];
+            s_lim[k] = lim;
             s_idx[k] = g;
         }
         __syncthreads();
@@ -229,6 +258,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
             for (int v = 0; v < 9; ++v) g[v] = 0.f;
             bool contrib = false;
             const Staged st = s_sp[k];
+            if (warp_misses(st, s_lim[k], wy0, wx1)) continue;
             float p0, dp, q, qq;
             splat_row(st, lyf, c0f, p0, dp, q, qq);
             if (pos < tmax && qq <= st.a.z) {                      // s >= q^2: else the whole row skips
@@ -294,8 +324,10 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
     }
 }
 
-size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4)) * (size_t)batch; }
-size_t bwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(uint32_t)) * (size_t)batch; }
+size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * (size_t)batch; }
+size_t bwd_smem(int batch) {
+    return (sizeof(Staged) + sizeof(float4) + sizeof(float2) + sizeof(uint32_t)) * (size_t)batch;
+}
 
 }  // namespace
 

@@ -19,16 +19,18 @@ import torch
 
 from . import _abi as abi
 
+_TILE_RULES = {"reach": abi.GS_TILES_REACH, "rect": abi.GS_TILES_RECT}
 _SORT_MODES = {"two_phase": abi.GS_SORT_TWO_PHASE, "key64": abi.GS_SORT_KEY64}
 
 
-def make_config(tile=(16, 16), batch_depth: int | None = None, sort_mode: str = "two_phase", **overrides
-                ) -> abi.gs_raster_config:
+def make_config(tile=(16, 16), batch_depth: int | None = None, sort_mode: str = "two_phase",
+                tile_rule: str = "reach", **overrides) -> abi.gs_raster_config:
     """Rasterizer constants (paper defaults) with optional overrides."""
     cfg = abi.gs_default_config()
     cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
     cfg.batch_depth = int(batch_depth) if batch_depth else cfg.tile_w * cfg.tile_h
     cfg.sort_mode = _SORT_MODES[sort_mode]
+    cfg.tile_rule = _TILE_RULES[tile_rule]
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg

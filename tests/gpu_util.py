@@ -27,8 +27,31 @@ def gpu_forward(g_np, cam, bg, cfg=None, capacity=None):
     img, T, last = fr.outputs()
     fr.render_forward(bg, img, T, last)
     torch.cuda.synchronize()
+    last_np = last.cpu().numpy()
     return dict(img=img.cpu().numpy().astype(np.float64), T=T.cpu().numpy().astype(np.float64),
-                last=last.cpu().numpy(), frame=fr, g=gt, img_t=img, T_t=T, last_t=last)
+                last=last_np, last_id=last_contributor_ids(fr, last_np), frame=fr, g=gt, img_t=img, T_t=T,
+                last_t=last)
+
+
+def last_contributor_ids(fr, last):
+    """Gaussian index of every pixel's last contributor (-1 = none): the GPU's `last` is a
+    1-based position in its tile's instance list, the oracle's list may hold other (never
+    blended) splats, so the two are compared by Gaussian index."""
+    import torch
+    _, st = fr.status()
+    K = min(int(st.num_instances), fr.capacity)
+    ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).view(-1, 2).cpu().numpy().astype(np.int64)
+    vals = fr.view("vals_sorted", torch.int32, max(K, 1)).cpu().numpy().astype(np.int64)
+    H, W = last.shape
+    tw, th = fr.cfg.tile_w, fr.cfg.tile_h
+    TX = (W + tw - 1) // tw
+    py, px = np.mgrid[0:H, 0:W]
+    t = (py // th) * TX + px // tw
+    pos = ranges[t, 0] + last.astype(np.int64) - 1
+    out = np.full(last.shape, -1, np.int64)
+    hit = last > 0
+    out[hit] = vals[pos[hit]]
+    return out
 
 
 def gpu_backward(run, bg, dimg_np):
@@ -79,7 +102,7 @@ def compare_images(gpu, orc, max_amb_frac=0.01, atol=IMG_ATOL, check_last=True):
     assert stats["max_T_err"] <= atol, stats
     if check_last:
         sure = (orc["pix_amb"] & 5) == 0            # no decision near any threshold
-        mism = (gpu["last"] != orc["last"]) & sure
+        mism = (gpu["last_id"] != orc["last_id"]) & sure
         stats["last_mismatch"] = int(mism.sum())
         assert stats["last_mismatch"] == 0, stats
     return stats

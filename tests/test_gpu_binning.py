@@ -1,44 +1,50 @@
 """gs_bin_sort vs the oracle's binning definition (App. C, Algorithm 2), bit for bit:
 instance count, sorted Gaussian indices, 64-bit keys (or tile ids) and tile ranges, for both
-sort schedules, several tile shapes, depth ties, culled and off-screen splats, huge splats,
-empty input, and instance counts spanning many sort tiles and scan chunks.  The
-screen-space inputs come from the seeded generator, written straight into the workspace."""
+sort schedules, both tile rules (reachable tiles, the paper's 3-sigma rectangle), several
+tile shapes, depth ties, culled, faint and off-screen splats, huge splats, empty input, and
+instance counts spanning many sort tiles and scan chunks.  The screen-space inputs come from
+the seeded generator, written straight into the workspace."""
 import numpy as np
 import pytest
 
 import oracle
 import synthetic as S
+from screen_util import random_splats
 
 pytestmark = pytest.mark.gpu
 
 
 def _screen(seed, n, W, H, rmax, culled=0.1, ties=0.1, huge=0):
-    rng = np.random.default_rng(seed)
-    uv = np.stack([rng.uniform(-40, W + 40, n), rng.uniform(-40, H + 40, n)], 1).astype(np.float32)
-    depth = rng.uniform(0.2, 30, n).astype(np.float32)
-    if n:
-        depth[rng.random(n) < ties] = depth[0]
-        nxt = np.nextafter(depth[0], np.float32(1e9))
-        depth[rng.random(n) < ties / 2] = nxt
-    radius = rng.integers(1, rmax + 1, n).astype(np.int32)
-    radius[rng.random(n) < culled] = 0
-    if huge and n:
-        radius[rng.choice(n, huge, replace=False)] = 5000
-    return uv, depth, radius
+    return random_splats(seed, n, W, H, rmax, culled=culled, ties=ties, huge=huge)
 
 
-def _bin_gpu(uv, depth, radius, W, H, tile, mode, capacity):
+def _oracle_bin(sp, W, H, tile, rule, capacity=None):
+    kw = dict(chol=sp["chol"], tau=sp["tau"]) if rule == "reach" else {}
+    return oracle.bin_instances(sp["uv"], sp["depth"], sp["radius"], W, H, tile[0], tile[1], capacity=capacity, **kw)
+
+
+def _oracle_count(sp, W, H, tile=(16, 16), rule="reach"):
+    kw = dict(chol=sp["chol"], tau=sp["tau"]) if rule == "reach" else {}
+    return oracle.instance_count(sp["uv"], sp["radius"], W, H, tile[0], tile[1], **kw)
+
+
+def _bin_gpu(sp, W, H, tile, mode, capacity, rule="reach"):
     import torch
     from paper_2308_04079_gb300 import Frame, make_config
-    n = uv.shape[0]
+    n = sp["uv"].shape[0]
     cam = S.look_at_camera([0, 0, -4], [0, 0, 0], W, H, 60.0)
-    fr = Frame(n, cam, make_config(tile=tile, sort_mode=mode), capacity=capacity)
+    fr = Frame(n, cam, make_config(tile=tile, sort_mode=mode, tile_rule=rule), capacity=capacity)
     if n:
         xy4 = np.zeros((n, 4), np.float32)
-        xy4[:, :2] = uv                                   # double-float mean with a zero low part
+        xy4[:, :2] = sp["uv"]                             # double-float mean with a zero low part
+        co = np.zeros((n, 4), np.float32)
+        co[:, :3] = sp["chol"]
+        co[:, 3] = sp["opacity"]
         fr.view("xy", torch.float32, 4 * n).copy_(torch.from_numpy(xy4.reshape(-1)))
-        fr.view("depth", torch.float32, n).copy_(torch.from_numpy(depth))
-        fr.view("radius", torch.int32, n).copy_(torch.from_numpy(radius))
+        fr.view("conic_opacity", torch.float32, 4 * n).copy_(torch.from_numpy(co.reshape(-1)))
+        fr.view("tau", torch.float32, n).copy_(torch.from_numpy(sp["tau"]))
+        fr.view("depth", torch.float32, n).copy_(torch.from_numpy(sp["depth"]))
+        fr.view("radius", torch.int32, n).copy_(torch.from_numpy(sp["radius"]))
     fr.bin_sort()
     code, st = fr.status()
     return fr, code, st
@@ -54,15 +60,16 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("rule", ["reach", "rect"])
 @pytest.mark.parametrize("mode", ["two_phase", "key64"])
 @pytest.mark.parametrize("seed,n,W,H,tile,rmax,huge", CASES)
-def test_bin_sort_bit_exact(mode, seed, n, W, H, tile, rmax, huge):
+def test_bin_sort_bit_exact(mode, rule, seed, n, W, H, tile, rmax, huge):
     import torch
     from paper_2308_04079_gb300 import _abi
-    uv, depth, radius = _screen(seed, n, W, H, rmax, huge=huge)
-    keys_o, vals_o, ranges_o = oracle.bin_instances(uv, depth, radius, W, H, tile[0], tile[1])
+    sp = _screen(seed, n, W, H, rmax, huge=huge)
+    keys_o, vals_o, ranges_o = _oracle_bin(sp, W, H, tile, rule)
     K = len(vals_o)
-    fr, code, st = _bin_gpu(uv, depth, radius, W, H, tile, mode, capacity=K + 777)
+    fr, code, st = _bin_gpu(sp, W, H, tile, mode, capacity=K + 777, rule=rule)
     assert code == _abi.GS_OK
     assert st.num_instances == K
     vals = fr.view("vals_sorted", torch.int32, K).cpu().numpy().view(np.uint32)
@@ -81,35 +88,40 @@ def test_bin_sort_bit_exact(mode, seed, n, W, H, tile, rmax, huge):
 def test_bin_sort_empty_and_all_culled(mode):
     import torch
     from paper_2308_04079_gb300 import _abi
-    z = np.zeros((0, 2), np.float32)
-    fr, code, st = _bin_gpu(z, np.zeros(0, np.float32), np.zeros(0, np.int32), 64, 48, (16, 16), mode, 10)
+    fr, code, st = _bin_gpu(_screen(7, 0, 64, 48, 10), 64, 48, (16, 16), mode, 10)
     assert code == _abi.GS_OK and st.num_instances == 0
     assert np.all(fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy() == 0)
-    uv, depth, radius = _screen(7, 500, 64, 48, 10)
-    radius[:] = 0
-    fr, code, st = _bin_gpu(uv, depth, radius, 64, 48, (16, 16), mode, 10)
+    sp = _screen(7, 500, 64, 48, 10)
+    sp["radius"][:] = 0
+    fr, code, st = _bin_gpu(sp, 64, 48, (16, 16), mode, 10)
     assert code == _abi.GS_OK and st.num_instances == 0
+    # visible but fainter than alpha_min everywhere: no reachable tile
+    sp = _screen(7, 500, 64, 48, 10, culled=0.0)
+    sp["tau"][:] = -0.5
+    fr, code, st = _bin_gpu(sp, 64, 48, (16, 16), mode, 10)
+    assert code == _abi.GS_OK and st.num_instances == 0
+    assert np.all(fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy() == 0)
 
 
 @pytest.mark.parametrize("mode", ["two_phase", "key64"])
 def test_bin_sort_capacity_overflow_is_reported(mode):
     from paper_2308_04079_gb300 import _abi
-    uv, depth, radius = _screen(8, 20000, 640, 480, 30)
-    K = oracle.instance_count(uv, radius, 640, 480)
-    fr, code, st = _bin_gpu(uv, depth, radius, 640, 480, (16, 16), mode, K // 3)
+    sp = _screen(8, 20000, 640, 480, 30)
+    K = _oracle_count(sp, 640, 480)
+    fr, code, st = _bin_gpu(sp, 640, 480, (16, 16), mode, K // 3)
     assert code == _abi.GS_ERR_CAPACITY
     assert st.num_instances == K
     # the workspace stays usable: a large enough frame bins the same input exactly
-    fr2, code2, st2 = _bin_gpu(uv, depth, radius, 640, 480, (16, 16), mode, K)
+    fr2, code2, st2 = _bin_gpu(sp, 640, 480, (16, 16), mode, K)
     assert code2 == _abi.GS_OK and st2.num_instances == K
 
 
 def test_bin_sort_deterministic_and_modes_agree():
     import torch
-    uv, depth, radius = _screen(9, 40000, 1280, 720, 35, huge=2)
-    K = oracle.instance_count(uv, radius, 1280, 720)
+    sp = _screen(9, 40000, 1280, 720, 35, huge=2)
+    K = _oracle_count(sp, 1280, 720)
     outs = []
     for mode in ("two_phase", "two_phase", "key64"):
-        fr, code, st = _bin_gpu(uv, depth, radius, 1280, 720, (16, 16), mode, K)
+        fr, code, st = _bin_gpu(sp, 1280, 720, (16, 16), mode, K)
         outs.append(fr.view("vals_sorted", torch.int32, K).cpu().numpy().copy())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])

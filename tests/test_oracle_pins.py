@@ -487,3 +487,88 @@ def test_backward_matches_finite_differences_config2_crop():
             params.append((name, (i, int(rng.integers(0, 4 if name == "quats" else 3)))))
     checked, skipped, worst = _fd_check(g, cam, dimg, bg, params)
     assert checked >= 0.85 * len(params), (checked, skipped)
+
+
+# --------------------------------------------------------------------------------------
+# Reachable-tile rule (a refinement of the Sec. 6 rectangle): pinned against FP64 brute
+# force over pixel centres, not against its own fp32 steps.
+# --------------------------------------------------------------------------------------
+from screen_util import ALPHA_MIN, random_splats  # noqa: E402
+
+
+def _rect_tiles(uv, r, W, H, tw, th):
+    TX, TY = -(-W // tw), -(-H // th)
+    fu, fv = int(np.floor(uv[0])), int(np.floor(uv[1]))
+    x0 = min(max((fu - r) // tw, 0), TX); x1 = min(max((fu + r) // tw + 1, 0), TX)
+    y0 = min(max((fv - r) // th, 0), TY); y1 = min(max((fv + r) // th + 1, 0), TY)
+    return x0, x1, y0, y1
+
+
+@pytest.mark.parametrize("seed,W,H,tw,th,rmax", [(11, 160, 96, 16, 16, 60), (12, 120, 72, 8, 8, 30),
+                                                  (13, 144, 80, 16, 8, 90)])
+def test_reach_rule_keeps_every_tile_where_alpha_reaches_threshold(seed, W, H, tw, th, rmax):
+    """Every pixel centre of the rectangle where the FP64 splat has o G >= alpha_min (1 - 1e-5)
+    lies in a kept tile; every kept tile is within 0.5 px (rows) and 0.011 px (columns) of the
+    widened ellipse; kept tiles are a subset of the rectangle, and the rule drops tiles."""
+    sp = random_splats(seed, 250, W, H, rmax, culled=0.0)
+    keys, vals, _ = oracle.bin_instances(sp["uv"], sp["depth"], sp["radius"], W, H, tw, th,
+                                         chol=sp["chol"], tau=sp["tau"])
+    TX = -(-W // tw)
+    kept = {}
+    for k, i in zip((keys >> np.uint64(32)).astype(np.int64), vals):
+        kept.setdefault(int(i), set()).add(int(k))
+    total_rect = 0
+    for i in range(len(sp["radius"])):
+        x0, x1, y0, y1 = _rect_tiles(sp["uv"][i].astype(np.float64), int(sp["radius"][i]), W, H, tw, th)
+        rect = {ty * TX + tx for ty in range(y0, y1) for tx in range(x0, x1)}
+        total_rect += len(rect)
+        mine = kept.get(i, set())
+        assert mine <= rect
+        if not rect:
+            continue
+        A, B, C = sp["conic"][i]
+        u, v = sp["uv"][i].astype(np.float64)
+        px = np.arange(x0 * tw, x1 * tw) + 0.5
+        py = np.arange(y0 * th, y1 * th) + 0.5
+        dx, dy = np.meshgrid(px - u, py - v)
+        q = A * dx * dx + 2 * B * dx * dy + C * dy * dy
+        alpha = sp["opacity"][i] * np.exp(-0.5 * q)
+        hit = alpha >= ALPHA_MIN * (1 - 1e-5)
+        ty_idx, tx_idx = np.nonzero(hit)
+        need = {(y0 + r // th) * TX + (x0 + c // tw) for r, c in zip(ty_idx, tx_idx)}
+        assert need <= mine, (i, sorted(need - mine))
+        # tightness: some pixel column of the tile, moved by <= 0.011 px, meets the ellipse
+        # q <= t at a y within the tile's band of pixel-centre rows
+        t = float(sp["tau"][i]) * (1 + 2.0 ** -10) + 2.0 ** -10
+        for tile in mine:
+            tx, ty = tile % TX, tile // TX
+            cx = np.arange(tx * tw, tx * tw + tw) + 0.5 - u
+            cx = np.sign(cx) * np.maximum(np.abs(cx) - 0.011, 0.0)
+            ya, yb = ty * th + 0.5 - v, ty * th + th - 0.5 - v
+            ys = np.clip(-B * cx / C, ya, yb)
+            qmin = (A * cx * cx + 2 * B * cx * ys + C * ys * ys).min()
+            assert qmin <= t * (1 + 1e-5) + 1e-5, (i, tile, qmin, t)
+    K = len(vals)
+    assert K < 0.8 * total_rect, (K, total_rect)
+
+
+def test_reach_rule_binning_is_the_rectangle_binning_filtered():
+    """Same keys order as the rectangle binning with the dropped pairs removed (one stable sort
+    of the emitted keys, ranges consistent)."""
+    W, H, tw, th = 200, 120, 16, 16
+    sp = random_splats(21, 400, W, H, 45, huge=2)
+    k_r, v_r, r_r = oracle.bin_instances(sp["uv"], sp["depth"], sp["radius"], W, H, tw, th)
+    k_e, v_e, r_e = oracle.bin_instances(sp["uv"], sp["depth"], sp["radius"], W, H, tw, th,
+                                         chol=sp["chol"], tau=sp["tau"])
+    pairs_e = list(zip(k_e.tolist(), v_e.tolist()))
+    keep = set(pairs_e)
+    filtered = [p for p in zip(k_r.tolist(), v_r.tolist()) if p in keep]
+    assert filtered == pairs_e
+    for t in range(r_e.shape[0]):
+        a, b = r_e[t]
+        assert np.all((k_e[a:b] >> np.uint64(32)) == t)
+        assert (b - a) == int(np.sum((k_e >> np.uint64(32)) == t))
+    # splats fainter than alpha_min reach no tile
+    faint = sp["opacity"] < ALPHA_MIN
+    assert faint.any() and not np.isin(np.nonzero(faint)[0], v_e).any()
+    assert oracle.instance_count(sp["uv"], sp["radius"], W, H, tw, th, chol=sp["chol"], tau=sp["tau"]) == len(v_e)
