@@ -897,20 +897,20 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
 /*   S    = (L L^T)^-1:  S00 = (l21^2 + l22^2) / (l11 l22)^2,                     */
 /*                       S01 = -l21 / ((l11 l22) l22)                             */
 /*   y*   = S01 sqrt(t / S00)                  (dy of the ellipse's rightmost point) */
-/*   X(y, s) = (s sqrt(max(t - (l22 y)^2, 0)) - l21 y) / l11                      */
+/*   X(y, s) = (s sqrt(max(t - (l22 y)^2, 0)) - l21 y) * (1 / l11)                */
 /* Row ty: pixel-centre offsets dy in [ya, yb] = [ty th + 0.5 - v, ty th + th - 0.5 - v] */
 /* clipped to [-ylim, ylim]; the rightmost reach over that band is X(clip(y*), +1), */
 /* the leftmost X(clip(-y*), -1) (each branch is concave/convex in y); widened by */
 /* 0.01 px they bound the columns px with px + 0.5 - u inside; the tiles holding  */
 /* those columns, cut to the rectangle, are kept.                                 */
 /* ------------------------------------------------------------------------- */
-static float reach_x32(float t, float l11, float l21, float l22, float y, float s) {
+static float reach_x32(float t, float inv11, float l21, float l22, float y, float s) {
     float q = l22 * y;
     float q2 = q * q;
     float h = t - q2;
     h = sqrtf(h > 0.0f ? h : 0.0f);
     float num = s * h - l21 * y;
-    return num / l11;
+    return num * inv11;
 }
 
 static float clampf32(float x, float lo, float hi) { return x < lo ? lo : (x > hi ? hi : x); }
@@ -922,6 +922,7 @@ static int reach_row32(const float* L, float tau, float u, float v, int ty, int 
     float t = tau * (1.0f + w) + w;
     if (!(t > 0.0f)) return 0;
     float l11 = L[0], l21 = L[1], l22 = L[2];
+    float inv11 = 1.0f / l11;
     float ylim = sqrtf(t) / l22;
     float a = l11 * l22;
     float s00 = (l21 * l21 + l22 * l22) / (a * a);
@@ -932,8 +933,8 @@ static int reach_row32(const float* L, float tau, float u, float v, int ty, int 
     if (ya < -ylim) ya = -ylim;
     if (yb > ylim) yb = ylim;
     if (ya > yb) return 0;
-    float xb = reach_x32(t, l11, l21, l22, clampf32(ystar, ya, yb), 1.0f) + 0.01f;
-    float xa = reach_x32(t, l11, l21, l22, clampf32(-ystar, ya, yb), -1.0f) - 0.01f;
+    float xb = reach_x32(t, inv11, l21, l22, clampf32(ystar, ya, yb), 1.0f) + 0.01f;
+    float xa = reach_x32(t, inv11, l21, l22, clampf32(-ystar, ya, yb), -1.0f) - 0.01f;
     float fa = ceilf((u + xa) - 0.5f), fb = floorf((u + xb) - 0.5f);
     const float lim = 1048576.0f;
     int pa = (int)clampf32(fa, -lim, lim), pb = (int)clampf32(fb, -lim, lim);

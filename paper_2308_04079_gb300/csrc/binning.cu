@@ -38,7 +38,6 @@ constexpr int kLbWindow = 8;                // predecessors read per look-back r
 constexpr unsigned long long kScanAgg = 1ull << 62;
 constexpr unsigned long long kScanInc = 2ull << 62;
 constexpr unsigned long long kScanFlags = 3ull << 62;
-constexpr unsigned long long kScanValue = (1ull << 62) - 1;
 
 template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
@@ -252,14 +251,46 @@ __device__ __forceinline__ unsigned long long pair_word(unsigned long long segs,
     return (min(segs, kPairSat) << 31) | min(tiles, kPairSat);
 }
 
-__device__ __forceinline__ bool tile_row(const Reach& e, int rect_only, float4 m, int ty, const CamK& c, int x0,
-                                         int x1, int& txa, int& txb) {
+__device__ __forceinline__ bool tile_row(const Reach& e, int rect_only, float u, float v, int ty, int tw_log2, int th,
+                                         int x0, int x1, int& txa, int& txb) {
     if (rect_only) {
         txa = x0;
         txb = x1;
         return true;
     }
-    return reach_row(e, m.x, m.y, ty, c.tile_w, c.tile_h, x0, x1, txa, txb);
+    return reach_row(e, u, v, ty, tw_log2, th, x0, x1, txa, txb);
+}
+
+// Rows of one splat are handled by a group of kRowLanes lanes (lane r of the group takes rows
+// r, r + kRowLanes, ...), so that a warp's lanes stay busy whatever the mix of splat heights.
+// A round gives each of the warp's 32 / kRowLanes groups the splat of one owner lane.
+constexpr int kRowLanes = 8;
+constexpr int kGroups = 32 / kRowLanes;
+
+// Per-splat state a group needs, broadcast from the owner lane.
+struct RowJob {
+    Reach e;
+    float u, v;
+    int x0, x1, y0, rows;
+};
+
+__device__ __forceinline__ RowJob row_job(const Reach& e, float u, float v, uint32_t rx, uint32_t ry, int src) {
+    RowJob j;
+    j.e.tm = __shfl_sync(0xffffffffu, e.tm, src);
+    j.e.ylim = __shfl_sync(0xffffffffu, e.ylim, src);
+    j.e.ystar = __shfl_sync(0xffffffffu, e.ystar, src);
+    j.e.inv11 = __shfl_sync(0xffffffffu, e.inv11, src);
+    j.e.l21 = __shfl_sync(0xffffffffu, e.l21, src);
+    j.e.l22 = __shfl_sync(0xffffffffu, e.l22, src);
+    j.e.any = j.e.tm > 0.f;
+    j.u = __shfl_sync(0xffffffffu, u, src);
+    j.v = __shfl_sync(0xffffffffu, v, src);
+    const uint32_t x = __shfl_sync(0xffffffffu, rx, src), y = __shfl_sync(0xffffffffu, ry, src);
+    j.x0 = (int)(x & 0xFFFFu);
+    j.x1 = (int)(x >> 16);
+    j.y0 = (int)(y & 0xFFFFu);
+    j.rows = (int)(y >> 16) - j.y0;
+    return j;
 }
 
 template <bool KEY64>
@@ -269,12 +300,14 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
     __shared__ unsigned long long s_scan[33];
     __shared__ uint32_t s_chunk;
     __shared__ unsigned long long s_base_s, s_base_t;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, sub = lane % kRowLanes, grp = lane / kRowLanes;
     uint32_t count = (uint32_t)a.n;
     if (a.count_dev) count = min(count, *a.count_dev);
     const uint32_t chunks = (count + kDupChunk - 1) / kDupChunk;
     const CamK& c = a.cam;
     const int gw = c.tiles_x + 1;
+    const int tw_log2 = c.tile_w == 16 ? 4 : 3;
+    const int th = c.tile_h;
     const unsigned long long cap = a.capacity;
 
     for (;;) {
@@ -284,55 +317,86 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
         __syncthreads();
         const uint32_t chunk = s_chunk;
         if (chunk >= chunks) break;
+        // Gaussian j = chunk * 1024 + k * 256 + tid: consecutive lanes take consecutive entries
         uint32_t gids[PER];
         int rad[PER];
         float4 mean[PER], L[PER];
         float tau[PER];
-        // gather first (independent loads in flight together), then compute
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const uint32_t j = chunk * kDupChunk + tid * PER + k;
+            const uint32_t j = chunk * kDupChunk + k * kDupThreads + tid;
             uint32_t gid = j < count ? (a.order ? a.order[j] : j) : 0u;
             if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
             gids[k] = gid;
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const uint32_t j = chunk * kDupChunk + tid * PER + k;
+            const uint32_t j = chunk * kDupChunk + k * kDupThreads + tid;
             rad[k] = j < count ? a.radius[gids[k]] : 0;
             mean[k] = a.xy[gids[k]];
             L[k] = a.conic[gids[k]];
             tau[k] = a.tau[gids[k]];
         }
-        uint32_t nseg[PER], ntile[PER];
-        int rx0[PER], rx1[PER], ry0[PER], ry1[PER];
-        uint32_t run_s = 0, run_t = 0;
+        uint32_t rx[PER], ry[PER];   // rectangle columns / rows packed lo | hi << 16 (rows 0: none)
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
+            int x0, x1, y0, y1;
+            const bool vis = rad[k] > 0 && tile_rect(mean[k], rad[k], c, x0, x1, y0, y1);
+            rx[k] = vis ? ((uint32_t)x0 | ((uint32_t)x1 << 16)) : 0u;
+            ry[k] = vis ? ((uint32_t)y0 | ((uint32_t)y1 << 16)) : 0u;
+        }
+        // ---- count the segments and tiles of every splat ----
+        uint32_t nseg[PER], ntile[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const Reach e = reach_setup(L[k], tau[k]);
             nseg[k] = 0;
             ntile[k] = 0;
-            rx0[k] = rx1[k] = ry0[k] = ry1[k] = 0;
-            if (rad[k] > 0 && tile_rect(mean[k], rad[k], c, rx0[k], rx1[k], ry0[k], ry1[k])) {
-                const Reach e = reach_setup(L[k], tau[k]);
-                for (int ty = ry0[k]; ty < ry1[k]; ++ty) {
+            for (int r = 0; r < 32 / kGroups; ++r) {
+                const RowJob jb = row_job(e, mean[k].x, mean[k].y, rx[k], ry[k], r * kGroups + grp);
+                uint32_t s = 0, t = 0;
+                for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
                     int txa, txb;
-                    if (tile_row(e, a.rect_only, mean[k], ty, c, rx0[k], rx1[k], txa, txb)) {
-                        ++nseg[k];
-                        ntile[k] += (uint32_t)(txb - txa);
+                    if (base + sub < jb.rows &&
+                        tile_row(jb.e, a.rect_only, jb.u, jb.v, jb.y0 + base + sub, tw_log2, th, jb.x0, jb.x1, txa, txb)) {
+                        s += 1;
+                        t += (uint32_t)(txb - txa);
                     }
                 }
-                if (KEY64 && ntile[k]) {
-                    const uint32_t db = __float_as_uint(a.depth[gids[k]]);
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], ntile[k]);
+                for (int o = 1; o < kRowLanes; o <<= 1) {
+                    s += __shfl_xor_sync(0xffffffffu, s, o);
+                    t += __shfl_xor_sync(0xffffffffu, t, o);
+                }
+                // owner lane r * kGroups + g takes the totals of group g
+                const int from = (lane % kGroups) * kRowLanes;
+                const uint32_t ts = __shfl_sync(0xffffffffu, s, from), tt = __shfl_sync(0xffffffffu, t, from);
+                if (lane / kGroups == r) {
+                    nseg[k] = ts;
+                    ntile[k] = tt;
                 }
             }
-            run_s += nseg[k];
-            run_t += ntile[k];
         }
-        unsigned long long local_total;
-        const unsigned long long local_excl = block_exclusive_scan<unsigned long long>(
-            ((unsigned long long)run_s << kLocalShift) | run_t, s_scan, &local_total);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (KEY64 && ntile[k]) {
+                const uint32_t db = __float_as_uint(a.depth[gids[k]]);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], ntile[k]);
+            }
+        }
+        // ---- chunk offsets: block scan (k-major order) + decoupled look-back ----
+        // Thread order inside the chunk is (k, tid); scan each k-slice and chain the slices.
+        unsigned long long excl_k[PER];
+        unsigned long long local_total = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            unsigned long long tot;
+            const unsigned long long ex = block_exclusive_scan<unsigned long long>(
+                ((unsigned long long)nseg[k] << kLocalShift) | ntile[k], s_scan, &tot);
+            excl_k[k] = local_total + ex;
+            local_total += tot;
+        }
         const unsigned long long blk_s = local_total >> kLocalShift;
         const unsigned long long blk_t = local_total & ((1ull << kLocalShift) - 1);
         // Decoupled look-back by warp 0, 32 predecessors per round of loads.
@@ -388,24 +452,49 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
             }
         }
         __syncthreads();
-        unsigned long long seg = s_base_s + (local_excl >> kLocalShift);
-        unsigned long long off = s_base_t + (local_excl & ((1ull << kLocalShift) - 1));
+        // ---- write segment records and per-row tile counts ----
+        const uint32_t cap32 = (uint32_t)cap;
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            if (nseg[k]) {
-                const Reach e = reach_setup(L[k], tau[k]);
-                for (int ty = ry0[k]; ty < ry1[k]; ++ty) {
-                    int txa, txb;
-                    if (!tile_row(e, a.rect_only, mean[k], ty, c, rx0[k], rx1[k], txa, txb)) continue;
-                    atomicAdd(&a.diff[ty * gw + txa], 1);
-                    atomicAdd(&a.diff[ty * gw + txb], -1);
-                    if (seg < cap) {
-                        a.seg_off[seg] = (uint32_t)min(off, cap);
-                        a.seg_tile[seg] = (uint32_t)(ty * c.tiles_x + txa);
-                        a.seg_gid[seg] = gids[k];
+            const Reach e = reach_setup(L[k], tau[k]);
+            // first segment / instance of this lane's splat, clamped (nothing is written past cap)
+            const uint32_t seg0 = (uint32_t)min(s_base_s + (excl_k[k] >> kLocalShift), cap);
+            const uint32_t off0 = (uint32_t)min(s_base_t + (excl_k[k] & ((1ull << kLocalShift) - 1)), cap);
+            for (int r = 0; r < 32 / kGroups; ++r) {
+                const int src = r * kGroups + grp;
+                const RowJob jb = row_job(e, mean[k].x, mean[k].y, rx[k], ry[k], src);
+                const uint32_t gs0 = __shfl_sync(0xffffffffu, seg0, src);
+                const uint32_t go0 = __shfl_sync(0xffffffffu, off0, src);
+                const uint32_t gid = __shfl_sync(0xffffffffu, gids[k], src);
+                uint32_t cs = 0, ct = 0;   // segments / tiles of the rows before this pass
+                for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
+                    const int ty = jb.y0 + base + sub;
+                    int txa = 0, txb = 0;
+                    const bool ok = base + sub < jb.rows &&
+                                    tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2, th, jb.x0, jb.x1, txa, txb);
+                    const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
+                    uint32_t is = ok ? 1u : 0u, it = len;   // inclusive scans over the group's lanes
+#pragma unroll
+                    for (int d = 1; d < kRowLanes; d <<= 1) {
+                        const uint32_t ns = __shfl_up_sync(0xffffffffu, is, d, kRowLanes);
+                        const uint32_t nt = __shfl_up_sync(0xffffffffu, it, d, kRowLanes);
+                        if (sub >= d) {
+                            is += ns;
+                            it += nt;
+                        }
                     }
-                    ++seg;
-                    off += (uint32_t)(txb - txa);
+                    if (ok) {
+                        atomicAdd(&a.diff[ty * gw + txa], 1);
+                        atomicAdd(&a.diff[ty * gw + txb], -1);
+                        const uint32_t seg = gs0 + cs + is - 1u;
+                        if (seg < cap32) {
+                            a.seg_off[seg] = min(go0 + ct + it - len, cap32);
+                            a.seg_tile[seg] = (uint32_t)(ty * c.tiles_x + txa);
+                            a.seg_gid[seg] = gid;
+                        }
+                    }
+                    cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
+                    ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
                 }
             }
         }

@@ -153,21 +153,20 @@ __device__ __forceinline__ bool tile_rect(float4 m, int r, const CamK& c, int& x
 // correctly rounded operations are used, in a fixed order, so the rule is reproducible
 // bit for bit.
 struct Reach {
-    float tm, ylim, ystar, l11, l21, l22;
+    float tm, ylim, ystar, inv11, l21, l22;
     bool any;
 };
 
 __device__ __forceinline__ Reach reach_setup(float4 L, float tau) {
     Reach e;
-    e.l11 = L.x;
     e.l21 = L.y;
     e.l22 = L.z;
     e.tm = __fadd_rn(__fmul_rn(tau, 1.0f + 0.0009765625f), 0.0009765625f);
     e.any = e.tm > 0.f;
-    if (!e.any) return e;
+    e.inv11 = __fdiv_rn(1.0f, L.x);
     const float sq = __fsqrt_rn(e.tm);
     e.ylim = __fdiv_rn(sq, e.l22);
-    const float a = __fmul_rn(e.l11, e.l22);
+    const float a = __fmul_rn(L.x, e.l22);
     const float qi00 = __fdiv_rn(__fadd_rn(__fmul_rn(e.l21, e.l21), __fmul_rn(e.l22, e.l22)), __fmul_rn(a, a));
     const float qi01 = __fdiv_rn(-e.l21, __fmul_rn(a, e.l22));
     e.ystar = __fmul_rn(qi01, __fsqrt_rn(__fdiv_rn(e.tm, qi00)));
@@ -177,13 +176,13 @@ __device__ __forceinline__ Reach reach_setup(float4 L, float tau) {
 __device__ __forceinline__ float reach_x(const Reach& e, float y, float sgn) {
     const float q = __fmul_rn(e.l22, y);
     const float h = __fsqrt_rn(fmaxf(__fsub_rn(e.tm, __fmul_rn(q, q)), 0.0f));
-    return __fdiv_rn(__fsub_rn(__fmul_rn(sgn, h), __fmul_rn(e.l21, y)), e.l11);
+    return __fmul_rn(__fsub_rn(__fmul_rn(sgn, h), __fmul_rn(e.l21, y)), e.inv11);
 }
 
 // Tiles [txa, txb) of tile row ty (inside the rectangle columns [x0, x1)) that the splat with
-// screen mean (u, v) can reach; false when none.
-__device__ __forceinline__ bool reach_row(const Reach& e, float u, float v, int ty, int tw, int th, int x0, int x1,
-                                          int& txa, int& txb) {
+// screen mean (u, v) can reach; false when none.  Tile widths are powers of two (tw_log2).
+__device__ __forceinline__ bool reach_row(const Reach& e, float u, float v, int ty, int tw_log2, int th, int x0,
+                                          int x1, int& txa, int& txb) {
     if (!e.any) return false;
     float ya = __fsub_rn(__fadd_rn((float)(ty * th), 0.5f), v);
     float yb = __fsub_rn(__fsub_rn((float)(ty * th + th), 0.5f), v);
@@ -200,8 +199,8 @@ __device__ __forceinline__ bool reach_row(const Reach& e, float u, float v, int 
     const float lim = 1048576.0f;
     const int pa = (int)fminf(fmaxf(fa, -lim), lim), pb = (int)fminf(fmaxf(fb, -lim), lim);
     if (pb < pa) return false;
-    txa = max(x0, floor_div(pa, tw));
-    txb = min(x1, floor_div(pb, tw) + 1);
+    txa = max(x0, pa >> tw_log2);          // arithmetic shift: floor division
+    txb = min(x1, (pb >> tw_log2) + 1);
     return txa < txb;
 }
 
