@@ -58,9 +58,12 @@ __global__ void __launch_bounds__(256) k_depth_hist(DepthHistArgs a) {
     __shared__ uint32_t s_hist[4][256];
     for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) (&s_hist[0][0])[k] = 0;
     __syncthreads();
+    __shared__ uint32_t s_vis;
+    if (threadIdx.x == 0) s_vis = 0;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const int stride = gridDim.x * blockDim.x;
+    uint32_t vis_count = 0;   // per warp (lane 0); one global atomic per block at the end
     for (int base = blockIdx.x * blockDim.x; base < a.n; base += stride) {
         const int i = base + threadIdx.x;
         const bool valid = i < a.n;
@@ -72,10 +75,12 @@ __global__ void __launch_bounds__(256) k_depth_hist(DepthHistArgs a) {
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (valid && (peers & lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
         }
-        const uint32_t vis = __ballot_sync(0xffffffffu, valid && key != 0xFFFFFFFFu);
-        if (lane == 0 && vis) atomicAdd(a.num_visible, (uint32_t)__popc(vis));
+        vis_count += (uint32_t)__popc(__ballot_sync(0xffffffffu, valid && key != 0xFFFFFFFFu));
     }
     __syncthreads();
+    if (lane == 0 && vis_count) atomicAdd(&s_vis, vis_count);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_vis) atomicAdd(a.num_visible, s_vis);
     for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) {
         const uint32_t v = (&s_hist[0][0])[k];
         if (v) atomicAdd(&a.hist[k], v);
