@@ -227,6 +227,31 @@ gs_status gs_render_backward_tiles(const gs_frame* frame, const float bg[3], con
 gs_status gs_render_backward_gaussians(const gs_frame* frame, const gs_gaussians* g, const gs_gradients* grads,
                                        int accumulate, cudaStream_t stream);
 
+/* Depth ordering without workspace or allocation (no counterpart in the paper; it is the
+ * first phase of the GS_SORT_TWO_PHASE binning schedule offered on its own).
+ * Writes order[0..n): the indices i with radius[i] > 0 sorted by the fp32 bits of depth[i]
+ * (ties by index), followed by the culled indices (radius[i] <= 0) in increasing order; the
+ * same order gs_bin_sort uses internally.  status->num_visible receives the count of visible
+ * Gaussians and status->flags bit 1 a spin-wait timeout (results then invalid); the other
+ * fields are zero.  Asynchronous on `stream`.
+ *   depth   device float[n]   camera-space depth of every Gaussian (positive for visible ones)
+ *   radius  device int32[n]   screen radius, <= 0 = culled
+ *   order   device uint32[n]  output, caller-owned
+ *   status  device gs_device_status, caller-owned, overwritten
+ * All scratch lives in a file-scope device array of the library sized for
+ * n <= GS_STATIC_ORDER_MAX_N (about 4.3 MB per device), so the call allocates nothing: for
+ * callers that cannot allocate where they need the ordering (cudaMalloc / cudaFree may
+ * synchronise the device and stall other streams; a fixed memory budget leaves no room for a
+ * workspace).  The scratch address is looked up once per device on the first call, which may
+ * load the module on that device: make the first call on each device outside stream capture.
+ * The scratch is shared by every call on a device, so calls that overlap in time (two streams
+ * or two host threads) race and must be ordered by the caller.
+ * Errors: GS_ERR_INVALID_ARG for n < 0, n > GS_STATIC_ORDER_MAX_N or a null pointer,
+ * GS_ERR_CUDA. */
+#define GS_STATIC_ORDER_MAX_N 262144
+gs_status gs_depth_order_static(int n, const float* depth, const int* radius, uint32_t* order,
+                                gs_device_status* status, cudaStream_t stream);
+
 /* Copy the workspace status block to the host (synchronises the stream) and return the first
  * device-side error as a status: GS_ERR_TIMEOUT, GS_ERR_CAPACITY, GS_ERR_NUMERIC or GS_OK. */
 gs_status gs_read_status(const gs_frame* frame, gs_device_status* out, cudaStream_t stream);

@@ -23,6 +23,7 @@ GS_ERR_NUMERIC = 5
 
 GS_SORT_TWO_PHASE = 0
 GS_SORT_KEY64 = 1
+GS_STATIC_ORDER_MAX_N = 262144
 GS_TILES_REACH = 0
 GS_TILES_RECT = 1
 
@@ -86,6 +87,7 @@ SIGNATURES = [
     ("gs_render_backward_gaussians", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians),
                                              ctypes.POINTER(gs_gradients), c_int, c_void_p]),
     ("gs_read_status", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_device_status), c_void_p]),
+    ("gs_depth_order_static", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("gs_status_string", ctypes.c_char_p, [c_int]),
 ]
 
@@ -186,3 +188,9 @@ def gs_read_status(frame: gs_frame, stream: int):
     if code in (GS_ERR_INVALID_ARG, GS_ERR_CUDA):
         raise GSError(code, "gs_read_status")
     return code, st
+
+
+def gs_depth_order_static(n: int, depth: int, radius: int, order: int, status: int, stream: int) -> None:
+    """Depth ordering with the library's static scratch (device pointers in, nothing
+    allocated); see include/gs.h."""
+    _check(load().gs_depth_order_static(n, depth, radius, order, status, stream), "gs_depth_order_static")

@@ -138,3 +138,17 @@ def test_stage_calls_validate_before_touching_the_device(lib):
     bg = (ctypes.c_float * 3)(0, 0, 0)
     assert L.gs_render_forward(ctypes.byref(f), ctypes.byref(bg), None, None, None, None) == _abi.GS_ERR_INVALID_ARG
     assert _abi.status_string(_abi.GS_ERR_CAPACITY) == "instance capacity exceeded"
+
+
+def test_static_depth_order_validates_before_touching_the_device(lib):
+    """The static-scratch depth ordering rejects n beyond its scratch, n < 0 and null pointers
+    synchronously, without a device call."""
+    from paper_2308_04079_gb300 import _abi
+    L = _abi.load()
+    nmax = _abi.GS_STATIC_ORDER_MAX_N
+    assert L.gs_depth_order_static(nmax + 1, 256, 256, 256, 256, None) == _abi.GS_ERR_INVALID_ARG
+    assert L.gs_depth_order_static(-1, 256, 256, 256, 256, None) == _abi.GS_ERR_INVALID_ARG
+    assert L.gs_depth_order_static(10, 256, 256, 256, None, None) == _abi.GS_ERR_INVALID_ARG
+    assert L.gs_depth_order_static(10, None, 256, 256, 256, None) == _abi.GS_ERR_INVALID_ARG
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    assert f"#define GS_STATIC_ORDER_MAX_N {nmax}" in src
