@@ -44,6 +44,15 @@ FLOPS_EVAL = 14
 FLOPS_BLEND_FWD = 9
 FLOPS_BLEND_BWD = 39
 
+CONFIG3_N = 3_000_000
+KERNEL_NAMES = {"preprocess": "k_preprocess_t", "render_forward": "k_render_forward_t",
+                "render_backward_tiles": "k_render_backward_t",
+                "render_backward_gaussians": "k_preprocess_backward_t"}
+# DRAM bytes (read + write) per launch of each single-kernel stage on the 3M-Gaussian 1080p
+# frame, from the ncu capture summarised in the named file under profiles/; None where no
+# capture of the current kernel exists.
+TRAFFIC = {"render_backward_tiles": 106_850_000}   # profiles/k_render_backward_config3.md
+
 
 def env_int(k, d):
     try:
@@ -116,22 +125,38 @@ class ClockSampler:
 # Our arm
 # ------------------------------------------------------------------------------------------
 def launches_per_step(layout) -> int:
-    binning = (1 + layout.depth_passes + 1 + 1 + layout.key_passes + 1) if layout.depth_passes else \
-        (1 + 1 + layout.key_passes + 1)
+    """Kernels one step launches: preprocess; binning = [depth histogram + depth passes] +
+    scan + ranges + emit + sort-prepare + instance passes; forward; backward tiles; backward
+    Gaussians."""
+    binning = 4 + layout.key_passes + ((1 + layout.depth_passes) if layout.depth_passes else 0)
     return 1 + binning + 1 + 2
 
 
-def byte_model(n, n_vis, K, P, tiles, sh_floats, layout):
-    """Algorithmic DRAM bytes per launch of each stage (kernel table)."""
+def byte_model(n, n_vis, K, segs, P, tiles, sh_floats, layout):
+    """Algorithmic DRAM bytes per launch of each stage: what the stage must read and write
+    once, with the measured visible count, instance count K and segment count."""
     b = {}
-    b["preprocess"] = n * (44 + 48) + n_vis * sh_floats * 4
-    depth_sort = (8 * n + layout.depth_passes * 16 * n) if layout.depth_passes else 0
+    # read mu, s, q, o (44 B) for every Gaussian and the SH rows (sh_floats x 4 B) of visible
+    # ones; write mean (16), depth (4), conic+opacity (16), rgb (16), radius (4), tau (4)
+    b["preprocess"] = n * (44 + 60) + n_vis * sh_floats * 4
     key_bytes = 4 if layout.depth_passes else 8
-    b["bin_sort"] = depth_sort + n_vis * 16 + K * (key_bytes + 4) + layout.key_passes * 2 * K * (key_bytes + 4) \
-        + K * key_bytes + tiles * 8
-    b["render_forward"] = K * 4 + n_vis * 40 + P * 20 + tiles * 8
-    b["render_backward_tiles"] = K * 4 + n_vis * (40 + 36) + P * 20 + tiles * 8
-    b["render_backward_gaussians"] = n_vis * (44 + sh_floats * 4 + 36 + 16) + n * (4 + 236 + 8)
+    # depth sort (two-phase): histogram read of depth+radius, then per pass read+write of
+    # (key, value); scan: per visible Gaussian read order, radius, mean, conic, tau (44 B),
+    # write 12 B per segment record; emit: read the records, write K (key, value); instance
+    # sort passes: read+write K (key, value); ranges: 8 B per tile
+    depth_sort = (8 * n + layout.depth_passes * 16 * n) if layout.depth_passes else 0
+    b["bin_sort"] = depth_sort + n_vis * 44 + segs * 12 * 2 + K * (key_bytes + 4) \
+        + layout.key_passes * 2 * K * (key_bytes + 4) + tiles * 8
+    # per instance one value read and one gathered splat (mean 16 + conic 16 + rgb 16 = 48 B;
+    # the gather of a splat is counted once per instance, i.e. L2 reuse across tiles ignored);
+    # per pixel write rgb, T, last (20 B)
+    b["render_forward"] = K * (4 + 48) + P * 20 + tiles * 8
+    # per instance value + splat gather; per pixel read dL/dC, T, last (20 B); per visible
+    # Gaussian 48 B of accumulators written (atomics) once
+    b["render_backward_tiles"] = K * (4 + 48) + P * 20 + tiles * 8 + n_vis * 48
+    # per Gaussian read parameters (44 B) and, for visible ones, SH rows, accumulators (48 B)
+    # and screen-space state (36 B); write every gradient (236 B) and the mean2d gradient (8 B)
+    b["render_backward_gaussians"] = n * (44 + 236 + 8) + n_vis * (sh_floats * 4 + 48 + 36)
     return b
 
 
@@ -145,7 +170,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     if gbuild.needs_build():
         gbuild.build()
-    g, cam, bg, dimg = S.config3(k=1 + rank)
+    g, cam, bg, dimg = S.config3(n=args.gaussians, k=1 + rank)
     bg = tuple(float(x) for x in bg)
     gt = GaussianTensors.from_numpy(g, device=dev).prepared()
     d_dimg = torch.from_numpy(dimg).to(dev)
@@ -185,6 +210,8 @@ def run_ours(args, rank, world, local_rank):
         raise RuntimeError(f"warm-up step failed: {_abi.status_string(code)}")
     n_vis, K = int(st.num_visible), int(st.num_instances)
     sum_last = float(last.to(torch.float64).sum().item())
+    blended = int(st.blended_pairs)
+    segs = int(st.num_segments)
 
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -223,29 +250,38 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak, peak_kind = load_peaks()
     P = cam.width * cam.height
     sh_floats = 48
-    bytes_ = byte_model(gt.n, n_vis, K, P, fr.tiles, sh_floats, fr.layout)
+    bytes_ = byte_model(gt.n, n_vis, K, segs, P, fr.tiles, sh_floats, fr.layout)
     kernels = {}
     for s in stages:
         kernels[s] = {"ms": round(stage_ms[s], 4), "alg_bytes": int(bytes_[s]),
                       "gbs": round(bytes_[s] / (stage_ms[s] * 1e-3) / 1e9, 1)}
-    evals = sum_last
-    flops_fwd = evals * FLOPS_EVAL
-    flops_bwd = evals * (FLOPS_EVAL + FLOPS_BLEND_BWD)
+    # Render kernels: the backward walks exactly sum(last) (pixel, splat) pairs and blends
+    # `blended` of them; the forward evaluates at least those pairs and blends the same ones.
+    flops_fwd = sum_last * FLOPS_EVAL + blended * FLOPS_BLEND_FWD
+    flops_bwd = sum_last * FLOPS_EVAL + blended * FLOPS_BLEND_BWD
     kernels["render_forward"]["alg_tflops"] = round(flops_fwd / (stage_ms["render_forward"] * 1e-3) / 1e12, 2)
     kernels["render_backward_tiles"]["alg_tflops"] = round(
         flops_bwd / (stage_ms["render_backward_tiles"] * 1e-3) / 1e12, 2)
-    dom = max(stages, key=lambda s: stage_ms[s])
+    # The roofline is reported for the dominant single kernel; gs_bin_sort is a sequence of
+    # ten launches and is reported per stage only.
+    single = ["preprocess", "render_forward", "render_backward_tiles", "render_backward_gaussians"]
+    dom = max(single, key=lambda s: stage_ms[s])
+    traffic = TRAFFIC.get(dom) if args.gaussians == CONFIG3_N else None
     if dom in ("render_forward", "render_backward_tiles"):
         fl = flops_fwd if dom == "render_forward" else flops_bwd
         ach = fl / (stage_ms[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach, 3), "peak": round(ALU_PEAK_TFLOPS, 1),
-                "unit": "TFLOP/s", "frac": round(ach / ALU_PEAK_TFLOPS, 4), "traffic": None,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "units": f"{int(evals)} evaluated (pixel, Gaussian) pairs"}
+        roof = {"kernel": KERNEL_NAMES[dom], "bound": "alu", "achieved": round(ach, 3),
+                "peak": round(ALU_PEAK_TFLOPS, 1), "unit": "TFLOP/s", "frac": round(ach / ALU_PEAK_TFLOPS, 4),
+                "traffic": traffic, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "units": f"{int(sum_last)} walked (pixel, splat) pairs x {FLOPS_EVAL} + {blended} blended pairs x "
+                         f"{FLOPS_BLEND_FWD if dom == 'render_forward' else FLOPS_BLEND_BWD} flops",
+                "alg_bytes": int(bytes_[dom]),
+                "hbm_frac": round(bytes_[dom] / (stage_ms[dom] * 1e-3) / 1e9 / hbm_peak, 4)}
     else:
         ach = bytes_[dom] / (stage_ms[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"}
+        roof = {"kernel": KERNEL_NAMES[dom], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": traffic,
+                "peak_kind": f"{peak_kind} hbm_gbs"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -255,9 +291,11 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "gaussians": gt.n, "width": cam.width, "height": cam.height,
+        "config": {"workload": WORKLOAD if gt.n == CONFIG3_N else f"{WORKLOAD} (subsampled to {gt.n} Gaussians)",
+                   "gaussians": gt.n, "width": cam.width, "height": cam.height,
                    "sh_degree": 3, "tile": f"{cfg.tile_w}x{cfg.tile_h}", "sort_mode": args.sort_mode,
-                   "visible": n_vis, "instances": K, "sum_last": int(sum_last),
+                   "visible": n_vis, "instances": K, "segments": segs, "sum_last": int(sum_last),
+                   "blended_pairs": blended,
                    "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
@@ -344,11 +382,18 @@ def oracle_frame_estimate(g, cam, bg, dimg, n_tiles, seed=0):
 
 def cpu_baseline(g, cam, bg, dimg, n_tiles):
     import oracle
+    total = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    n_tiles = min(n_tiles, total)
     frame_s, t_s, t_pre = oracle_frame_estimate(g, cam, bg, dimg, n_tiles)
+    if n_tiles == total:
+        sample = (f"FP64 oracle: one whole frame, preprocess of all {g.n} Gaussians + forward and backward of "
+                  f"all {total} 16x16 tiles ({t_s:.1f} s)")
+    else:
+        sample = (f"FP64 oracle: preprocess of all {g.n} Gaussians + forward+backward of {n_tiles} random "
+                  f"16x16 tiles of the frame ({t_s:.1f} s), extrapolated to {total} tiles (preprocess "
+                  f"{t_pre:.1f} s counted twice, as forward and backward each run it)")
     return {"value": round(1.0 / frame_s, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle: preprocess of all {g.n} Gaussians + forward+backward of {n_tiles} random "
-                      f"16x16 tiles of the 1080p frame ({t_s:.1f} s), extrapolated to 8160 tiles "
-                      f"(preprocess {t_pre:.1f} s counted twice, as forward and backward each run it)"}
+            "sample": sample}
 
 
 def run_reference(args, rank, world):
@@ -394,8 +439,11 @@ def main():
     ap.add_argument("--sort-mode", choices=["two_phase", "key64"], default="two_phase")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-tiles", type=int, default=128)
+    ap.add_argument("--cpu-tiles", type=int, default=8160,
+                    help="16x16 tiles of the frame the CPU baseline renders (8160 = the whole frame)")
     ap.add_argument("--ref-tiles", type=int, default=32)
+    ap.add_argument("--gaussians", type=int, default=CONFIG3_N,
+                    help="Gaussians of the config-3 scene (smaller counts for profiling captures)")
     args = ap.parse_args()
     rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     if args.impl == "reference":

@@ -155,7 +155,10 @@ typedef struct gs_device_status {
     uint32_t num_instances;   /* (Gaussian, tile) pairs (may exceed capacity, see flags)       */
     uint32_t num_visible;     /* Gaussians that survived culling                               */
     uint32_t num_nonfinite;   /* Gaussians culled because an input was NaN or Inf              */
-    uint32_t reserved[4];
+    uint64_t blended_pairs;   /* (pixel, splat) pairs the last gs_render_backward(_tiles) call
+                                 back-propagated through (alpha >= alpha_min, before the stop) */
+    uint32_t num_segments;    /* tile-row runs of instances written by gs_bin_sort            */
+    uint32_t reserved;
 } gs_device_status;
 
 /* Fill cfg with the paper's constants: 16x16 tiles, batch 128, alpha in [1/255, 0.99],

@@ -66,7 +66,8 @@ class gs_layout(ctypes.Structure):
 
 class gs_device_status(ctypes.Structure):
     _fields_ = [("flags", c_uint32), ("num_instances", c_uint32), ("num_visible", c_uint32),
-                ("num_nonfinite", c_uint32), ("reserved", c_uint32 * 4)]
+                ("num_nonfinite", c_uint32), ("blended_pairs", ctypes.c_uint64),
+                ("num_segments", c_uint32), ("reserved", c_uint32)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/gs.h

@@ -572,6 +572,7 @@ __global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
 template <bool KEY64>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
     using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.status->num_segments = *a.num_segments;
     if (a.status->flags & (kFlagCapacity | kFlagTimeout)) return;
     const int lane = threadIdx.x & 31;
     const uint32_t K = a.status->num_instances;

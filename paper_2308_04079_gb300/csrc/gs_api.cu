@@ -369,6 +369,8 @@ gs_status gs_render_backward_tiles(const gs_frame* f, const float bg[3], const f
     void* ws = f->ws;
     float* grad2d = at<float>(ws, L.grad2d);
     if (cudaMemsetAsync(grad2d, 0, (size_t)f->n * 12 * sizeof(float), s) != cudaSuccess) return GS_ERR_CUDA;
+    gs_device_status* st = &at<Control>(ws, L.control)->status;
+    if (cudaMemsetAsync(&st->blended_pairs, 0, sizeof(st->blended_pairs), s) != cudaSuccess) return GS_ERR_CUDA;
     RenderBwdArgs a;
     a.n = f->n;
     a.cam = cam_k(f, L);
@@ -384,6 +386,7 @@ gs_status gs_render_backward_tiles(const gs_frame* f, const float bg[3], const f
     a.T_final = T;
     a.last = last;
     a.grad2d = grad2d;
+    a.blended = reinterpret_cast<unsigned long long*>(&st->blended_pairs);
     return ok(launch_render_backward(a, L.tiles, s));
 }
 

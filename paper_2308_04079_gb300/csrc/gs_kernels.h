@@ -152,7 +152,7 @@ struct EmitArgs {
     void* keys_out;
     uint32_t* vals_out;
     unsigned long long capacity;
-    const gs_device_status* status;
+    gs_device_status* status;  // num_segments is reported here
 };
 
 struct SortPrepareArgs {
@@ -193,6 +193,7 @@ struct RenderBwdArgs {
     const float* T_final;
     const uint32_t* last;
     float* grad2d;             // [n, 12] accumulators, zeroed
+    unsigned long long* blended;   // count of back-propagated (pixel, splat) pairs, zeroed
 };
 
 // Host-side launchers (defined next to their kernels).  Each returns the launch status.

@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
     if ((threadIdx.x & 31) == 0) atomicMax(&s_max, wmax);
     __syncthreads();
     const uint32_t count = min(s_max, len);   // last positions never exceed the tile's list
+    uint32_t nblend = 0;
 
     for (int bend = (int)count; bend > 0; bend -= a.batch) {
         const int nb = min(a.batch, bend);
@@ -268,6 +269,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
                     const float s = splat_s(p0, dp, qq, j, p);
                     if (pos >= mylast[j] || s > st.a.z) continue;
                     contrib = true;
+                    ++nblend;
                     const float oG = exp2f(__fsub_rn(st.a.w, s));
                     const float alpha = fminf(amax, oG);
                     const float one_m = __fsub_rn(1.0f, alpha);
@@ -322,6 +324,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
             }
         }
     }
+    const uint32_t wblend = __reduce_add_sync(0xffffffffu, nblend);
+    if ((threadIdx.x & 31) == 0 && wblend) atomicAdd(a.blended, (unsigned long long)wblend);
 }
 
 size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * (size_t)batch; }
