@@ -230,6 +230,32 @@ gs_status gs_render_backward_tiles(const gs_frame* frame, const float bg[3], con
 gs_status gs_render_backward_gaussians(const gs_frame* frame, const gs_gaussians* g, const gs_gradients* grads,
                                        int accumulate, cudaStream_t stream);
 
+/* ---- Batches: several frames in one launch per stage --------------------------------------
+ * A batch is an array of `views` frames (1 <= views <= GS_MAX_BATCH), each with its own
+ * camera, image size, capacity and workspace, all with the same tile shape, batch depth, sort
+ * mode and tile rule.  Each stage runs as one launch per kernel for the whole batch (the work
+ * of all frames is split over one grid), so views of uneven size share the GPU instead of
+ * running one after another.  Every frame's results are those of the single-frame call.
+ *   gaussians[v]  the Gaussians frame v renders; views of one scene give equal descriptions.
+ *   bg            host float[views][3].
+ *   out_rgb, out_T, out_last, dL_drgb, T, last: host arrays of `views` device pointers, each
+ *                 laid out as in the single-frame call for that frame's image size.
+ *   grads[v]      gradient outputs of frame v.  Frames whose gaussians[] and grads[] are equal
+ *                 form a group: the group's gradients are the sum over its frames, written once
+ *                 (accumulate = 0) or added (accumulate = 1).  Frames of different groups must
+ *                 not share any gradient buffer.
+ * Errors: GS_ERR_INVALID_ARG (bad frame, mismatched configuration, views out of range,
+ * overlapping gradient outputs), GS_ERR_CUDA.  Device conditions are in each frame's status. */
+#define GS_MAX_BATCH 32
+gs_status gs_batch_preprocess(const gs_frame* frames, const gs_gaussians* gaussians, int views, cudaStream_t stream);
+gs_status gs_batch_bin_sort(const gs_frame* frames, int views, cudaStream_t stream);
+gs_status gs_batch_render_forward(const gs_frame* frames, int views, const float* bg, float* const* out_rgb,
+                                  float* const* out_T, uint32_t* const* out_last, cudaStream_t stream);
+gs_status gs_batch_render_backward(const gs_frame* frames, const gs_gaussians* gaussians, int views,
+                                   const float* bg, const float* const* dL_drgb, const float* const* T,
+                                   const uint32_t* const* last, const gs_gradients* grads, int accumulate,
+                                   cudaStream_t stream);
+
 /* Depth ordering without workspace or allocation (no counterpart in the paper; it is the
  * first phase of the GS_SORT_TWO_PHASE binning schedule offered on its own).
  * Writes order[0..n): the indices i with radius[i] > 0 sorted by the fp32 bits of depth[i]

@@ -8,6 +8,6 @@ the ctypes binding with the same names; :mod:`.rasterizer` adds workspace manage
 ``torch.autograd.Function``.  Importing this package does not load the library; the first
 call does, and fails loudly if it has not been built.
 """
-from .rasterizer import Frame, GaussianTensors, RasterizeFunction, make_config, rasterize, render
+from .rasterizer import Frame, FrameBatch, GaussianTensors, RasterizeFunction, make_config, rasterize, render
 
-__all__ = ["Frame", "GaussianTensors", "RasterizeFunction", "make_config", "rasterize", "render"]
+__all__ = ["Frame", "FrameBatch", "GaussianTensors", "RasterizeFunction", "make_config", "rasterize", "render"]

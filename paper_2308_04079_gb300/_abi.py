@@ -24,6 +24,7 @@ GS_ERR_NUMERIC = 5
 GS_SORT_TWO_PHASE = 0
 GS_SORT_KEY64 = 1
 GS_STATIC_ORDER_MAX_N = 262144
+GS_MAX_BATCH = 32
 GS_TILES_REACH = 0
 GS_TILES_RECT = 1
 
@@ -88,6 +89,14 @@ SIGNATURES = [
     ("gs_render_backward_gaussians", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians),
                                              ctypes.POINTER(gs_gradients), c_int, c_void_p]),
     ("gs_read_status", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_device_status), c_void_p]),
+    ("gs_batch_preprocess", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians), c_int, c_void_p]),
+    ("gs_batch_bin_sort", c_int, [ctypes.POINTER(gs_frame), c_int, c_void_p]),
+    ("gs_batch_render_forward", c_int, [ctypes.POINTER(gs_frame), c_int, ctypes.POINTER(c_float),
+                                        ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                        c_void_p]),
+    ("gs_batch_render_backward", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians), c_int,
+                                         ctypes.POINTER(c_float), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                         ctypes.POINTER(c_void_p), ctypes.POINTER(gs_gradients), c_int, c_void_p]),
     ("gs_depth_order_static", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("gs_status_string", ctypes.c_char_p, [c_int]),
 ]
@@ -195,3 +204,41 @@ def gs_depth_order_static(n: int, depth: int, radius: int, order: int, status: i
     """Depth ordering with the library's static scratch (device pointers in, nothing
     allocated); see include/gs.h."""
     _check(load().gs_depth_order_static(n, depth, radius, order, status, stream), "gs_depth_order_static")
+
+
+def _ptrs(values):
+    arr = (c_void_p * len(values))(*[int(v) for v in values])
+    return ctypes.cast(arr, ctypes.POINTER(c_void_p)), arr
+
+
+def gs_batch_preprocess(frames, gaussians, stream: int) -> None:
+    fr = (gs_frame * len(frames))(*frames)
+    gg = (gs_gaussians * len(gaussians))(*gaussians)
+    _check(load().gs_batch_preprocess(fr, gg, len(frames), stream), "gs_batch_preprocess")
+
+
+def gs_batch_bin_sort(frames, stream: int) -> None:
+    fr = (gs_frame * len(frames))(*frames)
+    _check(load().gs_batch_bin_sort(fr, len(frames), stream), "gs_batch_bin_sort")
+
+
+def gs_batch_render_forward(frames, bg, out_rgb, out_T, out_last, stream: int) -> None:
+    """bg: per-view (r, g, b); out_*: per-view device pointers."""
+    fr = (gs_frame * len(frames))(*frames)
+    b = (c_float * (3 * len(frames)))(*[float(x) for rgb in bg for x in rgb])
+    p_rgb, k1 = _ptrs(out_rgb)
+    p_T, k2 = _ptrs(out_T)
+    p_last, k3 = _ptrs(out_last)
+    _check(load().gs_batch_render_forward(fr, len(frames), b, p_rgb, p_T, p_last, stream), "gs_batch_render_forward")
+
+
+def gs_batch_render_backward(frames, gaussians, bg, dL_drgb, T, last, grads, accumulate: bool, stream: int) -> None:
+    fr = (gs_frame * len(frames))(*frames)
+    gg = (gs_gaussians * len(gaussians))(*gaussians)
+    gr = (gs_gradients * len(grads))(*grads)
+    b = (c_float * (3 * len(frames)))(*[float(x) for rgb in bg for x in rgb])
+    p_d, k1 = _ptrs(dL_drgb)
+    p_T, k2 = _ptrs(T)
+    p_last, k3 = _ptrs(last)
+    _check(load().gs_batch_render_backward(fr, gg, len(frames), b, p_d, p_T, p_last, gr, int(bool(accumulate)),
+                                           stream), "gs_batch_render_backward")

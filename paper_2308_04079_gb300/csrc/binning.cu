@@ -20,6 +20,7 @@
 // back over predecessor chunks (bounded spin), stages the keys in shared memory in local sorted
 // order and writes them out coalesced.  Digit histograms of every pass are computed up front
 // (fused into the kernel that produces the keys).
+#include <algorithm>
 #include <type_traits>
 
 #include "gs_device.cuh"
@@ -54,7 +55,12 @@ __device__ __forceinline__ void backoff(uint32_t spins) {
 // Depth-key histograms (TWO_PHASE): key = fp32 bits of depth, culled -> 0xFFFFFFFF.
 // Also zeroes the look-back rows the first depth pass uses.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_depth_hist(DepthHistArgs a) {
+template <int MAXF>
+__global__ void __launch_bounds__(256) k_depth_hist(const __grid_constant__ Multi<DepthHistArgs, MAXF> m) {
+    // frame f owns blocks [base[f], base[f + 1])
+    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);
+    const DepthHistArgs& a = m.a[f];
+    const int lblock = (int)(blockIdx.x - m.base[f]), nblocks = (int)(m.base[f + 1] - m.base[f]);
     __shared__ uint32_t s_hist[4][256];
     for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) (&s_hist[0][0])[k] = 0;
     __syncthreads();
@@ -62,9 +68,9 @@ __global__ void __launch_bounds__(256) k_depth_hist(DepthHistArgs a) {
     if (threadIdx.x == 0) s_vis = 0;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    const int stride = gridDim.x * blockDim.x;
+    const int stride = nblocks * blockDim.x;
     uint32_t vis_count = 0;   // per warp (lane 0); one global atomic per block at the end
-    for (int base = blockIdx.x * blockDim.x; base < a.n; base += stride) {
+    for (int base = lblock * blockDim.x; base < a.n; base += stride) {
         const int i = base + threadIdx.x;
         const bool valid = i < a.n;
         uint32_t key = 0xFFFFFFFFu;
@@ -86,15 +92,15 @@ __global__ void __launch_bounds__(256) k_depth_hist(DepthHistArgs a) {
         if (v) atomicAdd(&a.hist[k], v);
     }
     const int rows = (a.n + kSortTile - 1) / kSortTile;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (long long)rows * 256; k += stride)
+    for (long long k = (long long)lblock * blockDim.x + threadIdx.x; k < (long long)rows * 256; k += stride)
         a.lookback_first[k] = 0;
 }
 
 // ---------------------------------------------------------------------------------------
 // One LSD digit pass (8 bits at `shift`), stable.
 // ---------------------------------------------------------------------------------------
-template <typename KeyT>
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(SortPassArgs<KeyT> a) {
+template <typename KeyT, int MAXF>
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_constant__ Multi<SortPassArgs<KeyT>, MAXF> m) {
     constexpr int ITEMS = SortTile<KeyT>::items;
     constexpr int TILE = SortTile<KeyT>::keys;
     constexpr int WARPS = kSortThreads / 32;
@@ -106,22 +112,45 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(SortPassArgs<KeyT>
     __shared__ uint32_t s_digit_off[256];
     __shared__ uint32_t s_scan[33];
     __shared__ uint32_t s_chunk;
+    __shared__ uint32_t s_base[MAXF + 1];   // chunks of frames [0, f) (device-side counts)
+    __shared__ int s_frame;                 // frame whose digit offsets s_digit_off holds
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = lanemask_lt();
-    uint32_t count = a.count_host;
-    if (a.count_dev) count = min(count, *a.count_dev);
-    const uint32_t chunks = (count + TILE - 1) / TILE;
-    {
-        uint32_t tot;
-        s_digit_off[tid] = block_exclusive_scan<uint32_t>(a.hist[tid], s_scan, &tot);
+    if (tid < 32) {
+        uint32_t c = 0;
+        if (tid < m.frames) {
+            const SortPassArgs<KeyT>& af = m.a[tid];
+            uint32_t cnt = af.count_host;
+            if (af.count_dev) cnt = min(cnt, *af.count_dev);
+            c = (cnt + TILE - 1) / TILE;
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(c);
+        if (tid < m.frames) s_base[tid + 1] = inc;
+        if (tid == 0) {
+            s_base[0] = 0;
+            s_frame = -1;
+        }
     }
+    __syncthreads();
+    const uint32_t total = s_base[m.frames];
     for (;;) {
-        if (tid == 0) s_chunk = atomicAdd(a.chunk_counter, 1u);
+        if (tid == 0) s_chunk = atomicAdd(m.a[0].chunk_counter, 1u);
         for (int k = tid; k < WARPS * 256; k += kSortThreads) (&s_hist[0][0])[k] = 0;
         __syncthreads();
-        const uint32_t chunk = s_chunk;
-        if (chunk >= chunks) break;
+        const uint32_t g = s_chunk;
+        if (g >= total) break;
+        int f = 0;
+        while (f + 1 < m.frames && s_base[f + 1] <= g) ++f;
+        const SortPassArgs<KeyT>& a = m.a[f];
+        const uint32_t chunk = g - s_base[f];
+        uint32_t count = a.count_host;
+        if (a.count_dev) count = min(count, *a.count_dev);
+        if (f != s_frame) {   // block-uniform: global digit offsets of this frame's pass
+            uint32_t tot;
+            s_digit_off[tid] = block_exclusive_scan<uint32_t>(a.hist[tid], s_scan, &tot);
+            if (tid == 0) s_frame = f;
+        }
         if (a.lookback_next) a.lookback_next[(size_t)chunk * 256 + tid] = 0;
         const uint32_t wbase = chunk * TILE + warp * 32 * ITEMS;
 
@@ -298,30 +327,49 @@ __device__ __forceinline__ RowJob row_job(const Reach& e, float u, float v, uint
     return j;
 }
 
-template <bool KEY64>
-__global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
+template <bool KEY64, int MAXF>
+__global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
     constexpr int PER = kDupChunk / kDupThreads;
     __shared__ uint32_t s_hist[KEY64 ? 4 : 1][256];
     __shared__ unsigned long long s_scan[33];
     __shared__ uint32_t s_chunk;
     __shared__ unsigned long long s_base_s, s_base_t;
+    __shared__ uint32_t s_fbase[MAXF + 1];   // chunks of frames [0, f)
     const int tid = threadIdx.x, lane = tid & 31, sub = lane % kRowLanes, grp = lane / kRowLanes;
-    uint32_t count = (uint32_t)a.n;
-    if (a.count_dev) count = min(count, *a.count_dev);
-    const uint32_t chunks = (count + kDupChunk - 1) / kDupChunk;
-    const CamK& c = a.cam;
-    const int gw = c.tiles_x + 1;
-    const int tw_log2 = c.tile_w == 16 ? 4 : 3;
-    const int th = c.tile_h;
-    const unsigned long long cap = a.capacity;
+    if (tid < 32) {
+        uint32_t ch = 0;
+        if (tid < m.frames) {
+            const ScanArgs& af = m.a[tid];
+            uint32_t cnt = (uint32_t)af.n;
+            if (af.count_dev) cnt = min(cnt, *af.count_dev);
+            ch = (cnt + kDupChunk - 1) / kDupChunk;
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(ch);
+        if (tid < m.frames) s_fbase[tid + 1] = inc;
+        if (tid == 0) s_fbase[0] = 0;
+    }
+    __syncthreads();
+    const uint32_t total = s_fbase[m.frames];
 
     for (;;) {
-        if (tid == 0) s_chunk = atomicAdd(a.chunk_counter, 1u);
+        if (tid == 0) s_chunk = atomicAdd(m.a[0].chunk_counter, 1u);
         if (KEY64)
             for (int k = tid; k < 4 * 256; k += kDupThreads) (&s_hist[0][0])[k] = 0;
         __syncthreads();
-        const uint32_t chunk = s_chunk;
-        if (chunk >= chunks) break;
+        const uint32_t g = s_chunk;
+        if (g >= total) break;
+        int f = 0;
+        while (f + 1 < m.frames && s_fbase[f + 1] <= g) ++f;
+        const ScanArgs& a = m.a[f];
+        const uint32_t chunk = g - s_fbase[f];
+        const uint32_t chunks = s_fbase[f + 1] - s_fbase[f];
+        uint32_t count = (uint32_t)a.n;
+        if (a.count_dev) count = min(count, *a.count_dev);
+        const CamK& c = a.cam;
+        const int gw = c.tiles_x + 1;
+        const int tw_log2 = c.tile_w == 16 ? 4 : 3;
+        const int th = c.tile_h;
+        const unsigned long long cap = a.capacity;
         // Gaussian j = chunk * 1024 + k * 256 + tid: consecutive lanes take consecutive entries
         uint32_t gids[PER];
         int rad[PER];
@@ -521,7 +569,9 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(ScanArgs a) {
 // sorted instance array.  Also adds the digit histograms of the tile-id radix passes (tile ids
 // are the key bits from key_shift on).
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
+template <int MAXF>
+__global__ void __launch_bounds__(1024) k_tile_ranges(const __grid_constant__ Multi<TileRangesArgs, MAXF> m) {
+    const TileRangesArgs& a = m.a[blockIdx.x];   // one block per frame
     __shared__ uint32_t s_hist[kMaxKeyPasses][256];
     __shared__ uint32_t s_scan[33];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -569,17 +619,35 @@ __global__ void __launch_bounds__(1024) k_tile_ranges(TileRangesArgs a) {
 // 5-step search over the lanes' segment ends, so keys and values are written coalesced.
 // Nothing is written after a capacity overflow or a timed-out scan.
 // ---------------------------------------------------------------------------------------
-template <bool KEY64>
-__global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
+template <bool KEY64, int MAXF>
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ Multi<EmitArgs, MAXF> m) {
     using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.status->num_segments = *a.num_segments;
-    if (a.status->flags & (kFlagCapacity | kFlagTimeout)) return;
-    const int lane = threadIdx.x & 31;
-    const uint32_t K = a.status->num_instances;
-    const uint32_t S = *a.num_segments;
-    KeyT* keys_out = reinterpret_cast<KeyT*>(a.keys_out);
+    __shared__ uint32_t s_ubase[MAXF + 1];   // 32-segment units of frames [0, f)
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        uint32_t units = 0;
+        if (tid < m.frames) {
+            const EmitArgs& af = m.a[tid];
+            const uint32_t S = *af.num_segments;
+            if (blockIdx.x == 0) af.status->num_segments = S;
+            // nothing is emitted for a frame after a capacity overflow or a timed-out scan
+            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout))) units = (S + 31u) / 32u;
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
+        if (tid < m.frames) s_ubase[tid + 1] = inc;
+        if (tid == 0) s_ubase[0] = 0;
+    }
+    __syncthreads();
+    const uint32_t total = s_ubase[m.frames];
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; s0 < S; s0 += warps * 32u) {
+    for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += warps) {
+        int f = 0;
+        while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        const EmitArgs& a = m.a[f];
+        const uint32_t K = a.status->num_instances;
+        const uint32_t S = *a.num_segments;
+        KeyT* keys_out = reinterpret_cast<KeyT*>(a.keys_out);
+        const uint32_t s0 = (u - s_ubase[f]) * 32u;
         const uint32_t sidx = s0 + (uint32_t)lane;
         const bool valid = sidx < S;
         const uint32_t beg = valid ? a.seg_off[sidx] : K;
@@ -616,61 +684,109 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitArgs a) {
 
 // Zero the look-back rows of the first instance-sort pass (row count depends on the
 // device-side instance count).
-__global__ void k_sort_prepare(SortPrepareArgs a) {
-    const uint32_t count = min((unsigned long long)a.status->num_instances, a.capacity);
-    const uint32_t rows = (count + a.tile_keys - 1) / a.tile_keys;
-    const size_t total = (size_t)rows * 256;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
-        a.lookback[k] = 0;
+template <int MAXF>
+__global__ void k_sort_prepare(const __grid_constant__ Multi<SortPrepareArgs, MAXF> m) {
+    for (int f = 0; f < m.frames; ++f) {
+        const SortPrepareArgs& a = m.a[f];
+        const uint32_t count = min((unsigned long long)a.status->num_instances, a.capacity);
+        const uint32_t rows = (count + a.tile_keys - 1) / a.tile_keys;
+        const size_t total = (size_t)rows * 256;
+        for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
+            a.lookback[k] = 0;
+    }
 }
 
-cudaError_t launch_depth_hist(const DepthHistArgs& a, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    int grid = (a.n + 255) / 256;
-    const int cap = persistent_grid((const void*)k_depth_hist, 256);
-    if (grid > cap) grid = cap;
-    k_depth_hist<<<grid, 256, 0, s>>>(a);
+template <int MAXF>
+cudaError_t launch_depth_hist(Multi<DepthHistArgs, MAXF>& m, cudaStream_t s) {
+    // blocks per frame: 8 keys per thread, at most a persistent grid each
+    const int cap = persistent_grid((const void*)k_depth_hist<MAXF>, 256);
+    m.base[0] = 0;
+    for (int f = 0; f < m.frames; ++f) {
+        const int b = std::min(std::max((m.a[f].n + 2047) / 2048, 1), cap);
+        m.base[f + 1] = m.base[f] + (uint32_t)(m.a[f].n > 0 ? b : 0);
+    }
+    if (m.base[m.frames] == 0) return cudaSuccess;
+    k_depth_hist<MAXF><<<m.base[m.frames], 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 
-template <typename KeyT>
-static cudaError_t launch_onesweep_t(const SortPassArgs<KeyT>& a, int max_chunks, cudaStream_t s) {
-    int grid = persistent_grid((const void*)k_onesweep<KeyT>, kSortThreads);
+template <typename KeyT, int MAXF>
+cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_chunks, cudaStream_t s) {
+    int grid = persistent_grid((const void*)k_onesweep<KeyT, MAXF>, kSortThreads);
     if (max_chunks > 0 && grid > max_chunks) grid = max_chunks;
-    k_onesweep<KeyT><<<grid, kSortThreads, 0, s>>>(a);
+    k_onesweep<KeyT, MAXF><<<grid, kSortThreads, 0, s>>>(m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_onesweep(const SortPassArgs<uint32_t>& a, int max_chunks, cudaStream_t s) {
-    return launch_onesweep_t(a, max_chunks, s);
-}
-
-cudaError_t launch_onesweep(const SortPassArgs<unsigned long long>& a, int max_chunks, cudaStream_t s) {
-    return launch_onesweep_t(a, max_chunks, s);
-}
-
-cudaError_t launch_scan_tiles(const ScanArgs& a, bool key64, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    if (key64) k_scan_tiles<true><<<persistent_grid((const void*)k_scan_tiles<true>, kDupThreads), kDupThreads, 0, s>>>(a);
-    else k_scan_tiles<false><<<persistent_grid((const void*)k_scan_tiles<false>, kDupThreads), kDupThreads, 0, s>>>(a);
+template <int MAXF>
+cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s) {
+    if (key64)
+        k_scan_tiles<true, MAXF><<<persistent_grid((const void*)k_scan_tiles<true, MAXF>, kDupThreads), kDupThreads, 0,
+                                   s>>>(m);
+    else
+        k_scan_tiles<false, MAXF><<<persistent_grid((const void*)k_scan_tiles<false, MAXF>, kDupThreads), kDupThreads,
+                                    0, s>>>(m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_ranges(const TileRangesArgs& a, cudaStream_t s) {
-    k_tile_ranges<<<1, 1024, 0, s>>>(a);
+template <int MAXF>
+cudaError_t launch_tile_ranges(const Multi<TileRangesArgs, MAXF>& m, cudaStream_t s) {
+    k_tile_ranges<MAXF><<<m.frames, 1024, 0, s>>>(m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const EmitArgs& a, bool key64, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
-    if (key64) k_emit<true><<<persistent_grid((const void*)k_emit<true>, kEmitThreads), kEmitThreads, 0, s>>>(a);
-    else k_emit<false><<<persistent_grid((const void*)k_emit<false>, kEmitThreads), kEmitThreads, 0, s>>>(a);
+template <int MAXF>
+cudaError_t launch_emit(const Multi<EmitArgs, MAXF>& m, bool key64, cudaStream_t s) {
+    if (key64)
+        k_emit<true, MAXF><<<persistent_grid((const void*)k_emit<true, MAXF>, kEmitThreads), kEmitThreads, 0, s>>>(m);
+    else
+        k_emit<false, MAXF><<<persistent_grid((const void*)k_emit<false, MAXF>, kEmitThreads), kEmitThreads, 0, s>>>(m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort_prepare(const SortPrepareArgs& a, cudaStream_t s) {
-    k_sort_prepare<<<persistent_grid((const void*)k_sort_prepare, 256), 256, 0, s>>>(a);
+template <int MAXF>
+cudaError_t launch_sort_prepare(const Multi<SortPrepareArgs, MAXF>& m, cudaStream_t s) {
+    k_sort_prepare<MAXF><<<persistent_grid((const void*)k_sort_prepare<MAXF>, 256), 256, 0, s>>>(m);
     return cudaGetLastError();
 }
+
+// Zeroes every frame's regions of a batch (one launch instead of one memset per region).
+__global__ void __launch_bounds__(256) k_clear(const __grid_constant__ Multi<ClearArgs, kMaxFrames> m) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int f = 0; f < m.frames; ++f) {
+        for (int r = 0; r < kClearRegions; ++r) {
+            uint32_t* p = m.a[f].ptr[r];
+            const unsigned long long w = m.a[f].words[r];
+            if (!p || !w) continue;
+            if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+                uint4* p4 = reinterpret_cast<uint4*>(p);
+                const unsigned long long w4 = w / 4;
+                for (unsigned long long k = t0; k < w4; k += stride) p4[k] = make_uint4(0u, 0u, 0u, 0u);
+                for (unsigned long long k = 4 * w4 + t0; k < w; k += stride) p[k] = 0u;
+            } else {
+                for (unsigned long long k = t0; k < w; k += stride) p[k] = 0u;
+            }
+        }
+    }
+}
+
+cudaError_t launch_clear(const Multi<ClearArgs, kMaxFrames>& m, cudaStream_t s) {
+    k_clear<<<persistent_grid((const void*)k_clear, 256), 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+#define GS_INSTANTIATE_BINNING(F)                                                                           \
+    template cudaError_t launch_depth_hist<F>(Multi<DepthHistArgs, F>&, cudaStream_t);                        \
+    template cudaError_t launch_onesweep<uint32_t, F>(const Multi<SortPassArgs<uint32_t>, F>&, int, cudaStream_t); \
+    template cudaError_t launch_onesweep<unsigned long long, F>(const Multi<SortPassArgs<unsigned long long>, F>&, \
+                                                                int, cudaStream_t);                           \
+    template cudaError_t launch_scan_tiles<F>(const Multi<ScanArgs, F>&, bool, cudaStream_t);                  \
+    template cudaError_t launch_tile_ranges<F>(const Multi<TileRangesArgs, F>&, cudaStream_t);                 \
+    template cudaError_t launch_emit<F>(const Multi<EmitArgs, F>&, bool, cudaStream_t);                        \
+    template cudaError_t launch_sort_prepare<F>(const Multi<SortPrepareArgs, F>&, cudaStream_t);
+
+GS_INSTANTIATE_BINNING(1)
+GS_INSTANTIATE_BINNING(kMaxFrames)
 
 }  // namespace gs

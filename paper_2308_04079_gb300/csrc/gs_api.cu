@@ -1,5 +1,6 @@
 // gs_api.cu -- host side of the C ABI declared in include/gs.h: argument validation, the
 // workspace layout, and the launch sequence of each stage of Algorithm 2.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -146,31 +147,429 @@ gs_status ok(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 size_t keys_sorted_off(const Layout& L) { return L.ikey[L.key_passes % 2]; }
 size_t vals_sorted_off(const Layout& L) { return L.ival[L.key_passes % 2]; }
 
-template <typename KeyT>
-gs_status run_key_sort(const gs_frame* f, const Layout& L, Control* ctl, cudaStream_t s) {
-    void* ws = f->ws;
-    gs_device_status* st = &ctl->status;
-    SortPrepareArgs pa{at<uint32_t>(ws, L.sort_lb[0]), SortTile<KeyT>::keys, st, (unsigned long long)f->capacity};
-    if (launch_sort_prepare(pa, s) != cudaSuccess) return GS_ERR_CUDA;
-    for (int p = 0; p < L.key_passes; ++p) {
-        SortPassArgs<KeyT> a;
-        a.keys_in = at<KeyT>(ws, L.ikey[p % 2]);
-        a.vals_in = at<uint32_t>(ws, L.ival[p % 2]);
-        a.depth_src = nullptr;
-        a.radius_src = nullptr;
-        a.keys_out = at<KeyT>(ws, L.ikey[(p + 1) % 2]);
-        a.vals_out = at<uint32_t>(ws, L.ival[(p + 1) % 2]);
-        a.count_dev = &st->num_instances;
-        a.count_host = (uint32_t)f->capacity;
-        a.shift = 8 * p;
-        a.hist = ctl->hist_keys[p];
-        a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
-        a.lookback_next = (p + 1 < L.key_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
-        a.chunk_counter = &ctl->counters[8 + p];
-        a.status = st;
-        if (launch_onesweep(a, 0, s) != cudaSuccess) return GS_ERR_CUDA;
+// ---- stage implementations over a set of frames (a batch; a single frame is a batch of 1) ----
+
+// Frames of one call, validated, with their layouts.
+template <int MAXF>
+struct FrameSet {
+    int count = 0;
+    const gs_frame* f[MAXF];
+    Layout L[MAXF];
+};
+
+bool same_shape(const gs_raster_config& a, const gs_raster_config& b) {
+    return a.tile_w == b.tile_w && a.tile_h == b.tile_h && a.batch_depth == b.batch_depth &&
+           a.sort_mode == b.sort_mode && a.tile_rule == b.tile_rule;
+}
+
+template <int MAXF>
+bool collect(const gs_frame* frames, int views, FrameSet<MAXF>* fs) {
+    if (!frames || views < 1 || views > MAXF) return false;
+    fs->count = views;
+    for (int v = 0; v < views; ++v) {
+        fs->f[v] = &frames[v];
+        if (!valid_frame(&frames[v], &fs->L[v])) return false;
+        if (!same_shape(frames[v].cfg, frames[0].cfg)) return false;
+    }
+    return true;
+}
+
+template <int MAXF>
+Control* control_of(const FrameSet<MAXF>& fs, int v) {
+    return at<Control>(fs.f[v]->ws, fs.L[v].control);
+}
+
+// SH rows can be read and written as float4 when every row starts 16-byte aligned (the same
+// rule the kernels' launchers apply to the first frame of a launch).
+bool sh_vec(const float* sh, int sh_stride, const float* gsh = nullptr) {
+    const bool base = reinterpret_cast<uintptr_t>(sh) % 16 == 0 &&
+                      (gsh == nullptr || reinterpret_cast<uintptr_t>(gsh) % 16 == 0);
+    return base && (3 * sh_stride) % 4 == 0;
+}
+
+// Zeroes, per frame, the regions [ptr, ptr + words): cudaMemsetAsync for one frame, one kernel
+// for a batch.
+template <int MAXF>
+gs_status clear_regions(const FrameSet<MAXF>& fs, const ClearArgs* regions, cudaStream_t s) {
+    if (MAXF == 1 || fs.count == 1) {
+        for (int v = 0; v < fs.count; ++v)
+            for (int r = 0; r < kClearRegions; ++r)
+                if (regions[v].ptr[r] && regions[v].words[r] &&
+                    cudaMemsetAsync(regions[v].ptr[r], 0, regions[v].words[r] * 4, s) != cudaSuccess)
+                    return GS_ERR_CUDA;
+        return GS_OK;
+    }
+    Multi<ClearArgs, kMaxFrames> m;
+    m.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v) m.a[v] = regions[v];
+    return ok(launch_clear(m, s));
+}
+
+template <int MAXF>
+gs_status preprocess_impl(const FrameSet<MAXF>& fs, const gs_gaussians* g, cudaStream_t s) {
+    ClearArgs clr[MAXF];
+    for (int v = 0; v < fs.count; ++v) {
+        clr[v] = ClearArgs{};
+        clr[v].ptr[0] = reinterpret_cast<uint32_t*>(&control_of(fs, v)->status);
+        clr[v].words[0] = sizeof(gs_device_status) / 4;
+    }
+    gs_status st = clear_regions(fs, clr, s);
+    if (st != GS_OK) return st;
+    // one launch per (SH degree, SH row alignment) class of frames
+    bool done[MAXF] = {};
+    for (int v0 = 0; v0 < fs.count; ++v0) {
+        if (done[v0]) continue;
+        Multi<PreprocessArgs, MAXF> m;
+        m.frames = 0;
+        for (int v = v0; v < fs.count; ++v) {
+            if (done[v] || g[v].sh_degree != g[v0].sh_degree ||
+                sh_vec(g[v].sh, g[v].sh_stride) != sh_vec(g[v0].sh, g[v0].sh_stride))
+                continue;
+            done[v] = true;
+            const gs_frame* f = fs.f[v];
+            const Layout& L = fs.L[v];
+            void* ws = f->ws;
+            PreprocessArgs& a = m.a[m.frames++];
+            a.n = f->n;
+            a.means = g[v].means; a.scales = g[v].scales; a.quats = g[v].quats; a.opacities = g[v].opacities;
+            a.sh = g[v].sh;
+            a.sh_degree = g[v].sh_degree; a.sh_stride = g[v].sh_stride;
+            a.cam = cam_k(f, L);
+            a.cfg = cfg_k(f->cfg);
+            a.xy = at<float4>(ws, L.xy);
+            a.depth = at<float>(ws, L.depth);
+            a.conic_opacity = at<float4>(ws, L.conic);
+            a.rgb = at<float4>(ws, L.rgb);
+            a.radius = at<int>(ws, L.radius);
+            a.tau = at<float>(ws, L.tau);
+            a.status = &control_of(fs, v)->status;
+        }
+        if (launch_preprocess(m, s) != cudaSuccess) return GS_ERR_CUDA;
     }
     return GS_OK;
+}
+
+template <typename KeyT, int MAXF>
+gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
+    Multi<SortPrepareArgs, MAXF> pm;
+    pm.frames = fs.count;
+    int max_passes = 0;
+    for (int v = 0; v < fs.count; ++v) {
+        Control* ctl = control_of(fs, v);
+        pm.a[v] = SortPrepareArgs{at<uint32_t>(fs.f[v]->ws, fs.L[v].sort_lb[0]), SortTile<KeyT>::keys, &ctl->status,
+                                  (unsigned long long)fs.f[v]->capacity};
+        max_passes = std::max(max_passes, fs.L[v].key_passes);
+    }
+    if (launch_sort_prepare(pm, s) != cudaSuccess) return GS_ERR_CUDA;
+    Control* ctl0 = control_of(fs, 0);
+    for (int p = 0; p < max_passes; ++p) {
+        Multi<SortPassArgs<KeyT>, MAXF> m;
+        m.frames = fs.count;
+        for (int v = 0; v < fs.count; ++v) {
+            const Layout& L = fs.L[v];
+            void* ws = fs.f[v]->ws;
+            Control* ctl = control_of(fs, v);
+            SortPassArgs<KeyT>& a = m.a[v];
+            const bool live = p < L.key_passes;   // frames with fewer tile bits sort fewer passes
+            a.keys_in = at<KeyT>(ws, L.ikey[p % 2]);
+            a.vals_in = at<uint32_t>(ws, L.ival[p % 2]);
+            a.depth_src = nullptr;
+            a.radius_src = nullptr;
+            a.keys_out = at<KeyT>(ws, L.ikey[(p + 1) % 2]);
+            a.vals_out = at<uint32_t>(ws, L.ival[(p + 1) % 2]);
+            a.count_dev = &ctl->status.num_instances;
+            a.count_host = live ? (uint32_t)fs.f[v]->capacity : 0u;
+            a.shift = 8 * p;
+            a.hist = ctl->hist_keys[p < kMaxKeyPasses ? p : 0];
+            a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
+            a.lookback_next = (p + 1 < L.key_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
+            a.chunk_counter = &ctl0->counters[8 + p];
+            a.status = &ctl->status;
+        }
+        if (launch_onesweep(m, 0, s) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+template <int MAXF>
+gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
+    const bool key64 = fs.f[0]->cfg.sort_mode == GS_SORT_KEY64;
+    ClearArgs clr[MAXF];
+    for (int v = 0; v < fs.count; ++v) {
+        const Layout& L = fs.L[v];
+        void* ws = fs.f[v]->ws;
+        Control* ctl = control_of(fs, v);
+        clr[v] = ClearArgs{};
+        // flags + num_instances, every counter and histogram, the difference grid, the scan look-back
+        clr[v].ptr[0] = reinterpret_cast<uint32_t*>(&ctl->status);
+        clr[v].words[0] = 2;
+        clr[v].ptr[1] = &ctl->counters[0];
+        clr[v].words[1] = (sizeof(Control) - offsetof(Control, counters)) / 4;
+        clr[v].ptr[2] = at<uint32_t>(ws, L.diff);
+        clr[v].words[2] = L.diff_count;
+        clr[v].ptr[3] = at<uint32_t>(ws, L.scan_lb);
+        clr[v].words[3] = L.scan_lb_rows * 2;
+    }
+    gs_status st = clear_regions(fs, clr, s);
+    if (st != GS_OK) return st;
+    Control* ctl0 = control_of(fs, 0);
+
+    Multi<ScanArgs, MAXF> d;
+    d.frames = fs.count;
+    if (!key64) {
+        // Phase 1: stable sort of every frame's Gaussians by fp32 depth bits (culled ones last).
+        Multi<DepthHistArgs, MAXF> h;
+        h.frames = fs.count;
+        int chunks = 0;
+        for (int v = 0; v < fs.count; ++v) {
+            const Layout& L = fs.L[v];
+            void* ws = fs.f[v]->ws;
+            Control* ctl = control_of(fs, v);
+            h.a[v] = DepthHistArgs{fs.f[v]->n, at<float>(ws, L.depth), at<int>(ws, L.radius), &ctl->hist_depth[0][0],
+                                   at<uint32_t>(ws, L.sort_lb[0]), &ctl->counters[31]};
+            chunks += (fs.f[v]->n + kSortTile - 1) / kSortTile;
+        }
+        if (launch_depth_hist(h, s) != cudaSuccess) return GS_ERR_CUDA;
+        for (int p = 0; p < kDepthPasses; ++p) {
+            Multi<SortPassArgs<uint32_t>, MAXF> m;
+            m.frames = fs.count;
+            for (int v = 0; v < fs.count; ++v) {
+                const Layout& L = fs.L[v];
+                void* ws = fs.f[v]->ws;
+                Control* ctl = control_of(fs, v);
+                SortPassArgs<uint32_t>& a = m.a[v];
+                a.keys_in = p == 0 ? nullptr : at<uint32_t>(ws, L.gkey[(p + 1) % 2]);
+                a.vals_in = p == 0 ? nullptr : at<uint32_t>(ws, L.gval[(p + 1) % 2]);
+                a.depth_src = at<float>(ws, L.depth);
+                a.radius_src = at<int>(ws, L.radius);
+                a.keys_out = at<uint32_t>(ws, L.gkey[p % 2]);
+                a.vals_out = at<uint32_t>(ws, L.gval[p % 2]);
+                a.count_dev = nullptr;
+                a.count_host = (uint32_t)fs.f[v]->n;
+                a.shift = 8 * p;
+                a.hist = ctl->hist_depth[p];
+                a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
+                a.lookback_next = (p + 1 < kDepthPasses) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
+                a.chunk_counter = &ctl0->counters[1 + p];
+                a.status = &ctl->status;
+            }
+            if (chunks > 0 && launch_onesweep(m, chunks, s) != cudaSuccess) return GS_ERR_CUDA;
+        }
+    }
+    for (int v = 0; v < fs.count; ++v) {
+        const gs_frame* f = fs.f[v];
+        const Layout& L = fs.L[v];
+        void* ws = f->ws;
+        Control* ctl = control_of(fs, v);
+        ScanArgs& a = d.a[v];
+        a.n = f->n;
+        a.order = key64 ? nullptr : at<uint32_t>(ws, L.gval[(kDepthPasses - 1) % 2]);
+        a.count_dev = key64 ? nullptr : &ctl->counters[31];
+        a.xy = at<float4>(ws, L.xy);
+        a.conic = at<float4>(ws, L.conic);
+        a.tau = at<float>(ws, L.tau);
+        a.rect_only = f->cfg.tile_rule == GS_TILES_RECT;
+        a.radius = at<int>(ws, L.radius);
+        a.depth = at<float>(ws, L.depth);
+        a.cam = cam_k(f, L);
+        a.seg_tile = at<uint32_t>(ws, L.ikey[1]);
+        a.seg_off = a.seg_tile + (f->capacity > 0 ? f->capacity : 1);
+        a.seg_gid = at<uint32_t>(ws, L.ival[1]);
+        a.num_segments = &ctl->counters[30];
+        a.diff = at<int>(ws, L.diff);
+        a.capacity = f->capacity;
+        a.hist = &ctl->hist_keys[0][0];
+        a.lookback = at<unsigned long long>(ws, L.scan_lb);
+        a.chunk_counter = &ctl0->counters[0];
+        a.status = &ctl->status;
+    }
+    if (launch_scan_tiles(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    Multi<TileRangesArgs, MAXF> tr;
+    tr.frames = fs.count;
+    Multi<EmitArgs, MAXF> e;
+    e.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v) {
+        const gs_frame* f = fs.f[v];
+        const Layout& L = fs.L[v];
+        void* ws = f->ws;
+        Control* ctl = control_of(fs, v);
+        TileRangesArgs& t = tr.a[v];
+        t.diff = at<int>(ws, L.diff);
+        t.tiles_x = L.tiles_x;
+        t.tiles_y = L.tiles_y;
+        t.ranges = at<uint32_t>(ws, L.ranges);
+        t.tile_passes = key64 ? L.key_passes - 4 : L.key_passes;
+        t.key_shift = key64 ? 32 : 0;
+        t.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
+        t.capacity = f->capacity;
+        EmitArgs& a = e.a[v];
+        a.n = f->n;
+        a.seg_off = d.a[v].seg_off;
+        a.seg_tile = d.a[v].seg_tile;
+        a.seg_gid = d.a[v].seg_gid;
+        a.num_segments = d.a[v].num_segments;
+        a.depth = d.a[v].depth;
+        a.keys_out = at<void>(ws, L.ikey[0]);
+        a.vals_out = at<uint32_t>(ws, L.ival[0]);
+        a.capacity = f->capacity;
+        a.status = &ctl->status;
+    }
+    if (launch_tile_ranges(tr, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (key64) return key_sort<unsigned long long>(fs, s);
+    return key_sort<uint32_t>(fs, s);
+}
+
+template <int MAXF>
+gs_status render_forward_impl(const FrameSet<MAXF>& fs, const float* bg, float* const* out_rgb,
+                              float* const* out_T, uint32_t* const* out_last, cudaStream_t s) {
+    Multi<RenderFwdArgs, MAXF> m;
+    m.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v) {
+        const gs_frame* f = fs.f[v];
+        const Layout& L = fs.L[v];
+        void* ws = f->ws;
+        RenderFwdArgs& a = m.a[v];
+        a.n = f->n;
+        a.cam = cam_k(f, L);
+        a.cfg = cfg_k(f->cfg);
+        for (int k = 0; k < 3; ++k) a.bg[k] = bg[3 * v + k];
+        a.batch = f->cfg.batch_depth;
+        a.ranges = at<uint32_t>(ws, L.ranges);
+        a.vals = at<uint32_t>(ws, vals_sorted_off(L));
+        a.xy = at<float4>(ws, L.xy);
+        a.conic_opacity = at<float4>(ws, L.conic);
+        a.rgb = at<float4>(ws, L.rgb);
+        a.out_rgb = out_rgb[v];
+        a.out_T = out_T[v];
+        a.out_last = out_last[v];
+    }
+    return ok(launch_render_forward(m, s));
+}
+
+template <int MAXF>
+gs_status render_backward_tiles_impl(const FrameSet<MAXF>& fs, const float* bg, const float* const* dL_drgb,
+                                     const float* const* T, const uint32_t* const* last, cudaStream_t s) {
+    ClearArgs clr[MAXF];
+    Multi<RenderBwdArgs, MAXF> m;
+    m.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v) {
+        const gs_frame* f = fs.f[v];
+        const Layout& L = fs.L[v];
+        void* ws = f->ws;
+        gs_device_status* st = &control_of(fs, v)->status;
+        clr[v] = ClearArgs{};
+        clr[v].ptr[0] = at<uint32_t>(ws, L.grad2d);
+        clr[v].words[0] = (unsigned long long)f->n * 12;
+        clr[v].ptr[1] = reinterpret_cast<uint32_t*>(&st->blended_pairs);
+        clr[v].words[1] = 2;
+        RenderBwdArgs& a = m.a[v];
+        a.n = f->n;
+        a.cam = cam_k(f, L);
+        a.cfg = cfg_k(f->cfg);
+        for (int k = 0; k < 3; ++k) a.bg[k] = bg[3 * v + k];
+        a.batch = f->cfg.batch_depth;
+        a.ranges = at<uint32_t>(ws, L.ranges);
+        a.vals = at<uint32_t>(ws, vals_sorted_off(L));
+        a.xy = at<float4>(ws, L.xy);
+        a.conic_opacity = at<float4>(ws, L.conic);
+        a.rgb = at<float4>(ws, L.rgb);
+        a.dL_drgb = dL_drgb[v];
+        a.T_final = T[v];
+        a.last = last[v];
+        a.grad2d = at<float>(ws, L.grad2d);
+        a.blended = reinterpret_cast<unsigned long long*>(&st->blended_pairs);
+    }
+    gs_status st = clear_regions(fs, clr, s);
+    if (st != GS_OK) return st;
+    return ok(launch_render_backward(m, s));
+}
+
+bool same_gaussians(const gs_gaussians& a, const gs_gaussians& b) {
+    return a.means == b.means && a.scales == b.scales && a.quats == b.quats && a.opacities == b.opacities &&
+           a.sh == b.sh && a.n == b.n && a.sh_degree == b.sh_degree && a.sh_stride == b.sh_stride;
+}
+
+bool same_gradients(const gs_gradients& a, const gs_gradients& b) {
+    return a.means == b.means && a.scales == b.scales && a.quats == b.quats && a.opacities == b.opacities &&
+           a.sh == b.sh && a.mean2d == b.mean2d;
+}
+
+bool gradients_overlap(const gs_gradients& a, const gs_gradients& b) {
+    return a.means == b.means || a.scales == b.scales || a.quats == b.quats || a.opacities == b.opacities ||
+           a.sh == b.sh || (a.mean2d && a.mean2d == b.mean2d);
+}
+
+// Groups the frames by the Gaussians they render: a group's gradients are summed into its
+// outputs in one pass.  Frames of different groups must not share a gradient buffer.
+template <int MAXF>
+bool group_frames(int count, const gs_gaussians* g, const gs_gradients* gr, int* group_of, int* first, int* groups) {
+    *groups = 0;
+    for (int v = 0; v < count; ++v) {
+        group_of[v] = -1;
+        for (int k = 0; k < *groups; ++k) {
+            const int u = first[k];
+            if (same_gaussians(g[u], g[v]) && same_gradients(gr[u], gr[v])) { group_of[v] = k; break; }
+            if (gradients_overlap(gr[u], gr[v])) return false;
+        }
+        if (group_of[v] < 0) { first[*groups] = v; group_of[v] = (*groups)++; }
+    }
+    return true;
+}
+
+template <int MAXF>
+gs_status render_backward_gaussians_impl(const FrameSet<MAXF>& fs, const gs_gaussians* g, const gs_gradients* gr,
+                                         int accumulate, cudaStream_t s) {
+    int group_of[MAXF], first[MAXF], groups = 0;
+    if (!group_frames<MAXF>(fs.count, g, gr, group_of, first, &groups)) return GS_ERR_INVALID_ARG;
+    // one launch per (SH degree, SH row alignment) class of groups
+    bool done[MAXF] = {};
+    for (int k0 = 0; k0 < groups; ++k0) {
+        if (done[k0]) continue;
+        const gs_gaussians& g0 = g[first[k0]];
+        const gs_gradients& r0 = gr[first[k0]];
+        const bool vec0 = sh_vec(g0.sh, g0.sh_stride, r0.sh);
+        BwdPlan<MAXF> m;
+        m.groups = 0;
+        int nf = 0;
+        for (int k = k0; k < groups; ++k) {
+            const gs_gaussians& gk = g[first[k]];
+            const gs_gradients& rk = gr[first[k]];
+            if (done[k] || gk.sh_degree != g0.sh_degree || sh_vec(gk.sh, gk.sh_stride, rk.sh) != vec0) continue;
+            done[k] = true;
+            if (gk.n == 0) continue;
+            m.frame_begin[m.groups] = nf;
+            for (int v = 0; v < fs.count; ++v) {
+                if (group_of[v] != k) continue;
+                const gs_frame* f = fs.f[v];
+                const Layout& L = fs.L[v];
+                void* ws = f->ws;
+                PreprocessBwdArgs& b = m.a[nf++];
+                b.n = f->n;
+                b.means = gk.means; b.scales = gk.scales; b.quats = gk.quats; b.opacities = gk.opacities;
+                b.sh = gk.sh;
+                b.sh_degree = gk.sh_degree; b.sh_stride = gk.sh_stride;
+                b.cam = cam_k(f, L);
+                b.cfg = cfg_k(f->cfg);
+                b.grad2d = at<float>(ws, L.grad2d);
+                b.rgb = at<float4>(ws, L.rgb);
+                b.radius = at<int>(ws, L.radius);
+                b.g_means = rk.means; b.g_scales = rk.scales; b.g_quats = rk.quats; b.g_opacities = rk.opacities;
+                b.g_sh = rk.sh; b.g_mean2d = rk.mean2d;
+                b.accumulate = accumulate;
+            }
+            m.frame_begin[++m.groups] = nf;
+        }
+        if (m.groups > 0 && launch_preprocess_backward(m, s) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+bool valid_gradients(const gs_frame* f, const gs_gradients* gr) {
+    if (!gr) return false;
+    if (f->n > 0 && (!gr->means || !gr->scales || !gr->quats || !gr->opacities || !gr->sh)) return false;
+    if (f->n > 0 && reinterpret_cast<uintptr_t>(gr->quats) % 16) return false;
+    return true;
 }
 
 }  // namespace
@@ -222,207 +621,97 @@ gs_status gs_workspace_layout(int n, int width, int height, uint64_t capacity, c
 }
 
 gs_status gs_preprocess(const gs_frame* f, const gs_gaussians* g, cudaStream_t s) {
-    Layout L;
-    if (!valid_frame(f, &L) || !valid_gaussians(f, g)) return GS_ERR_INVALID_ARG;
-    void* ws = f->ws;
-    Control* ctl = at<Control>(ws, L.control);
-    if (cudaMemsetAsync(&ctl->status, 0, sizeof(gs_device_status), s) != cudaSuccess) return GS_ERR_CUDA;
-    if (f->n == 0) return GS_OK;
-    PreprocessArgs a;
-    a.n = f->n;
-    a.means = g->means; a.scales = g->scales; a.quats = g->quats; a.opacities = g->opacities; a.sh = g->sh;
-    a.sh_degree = g->sh_degree; a.sh_stride = g->sh_stride;
-    a.cam = cam_k(f, L);
-    a.cfg = cfg_k(f->cfg);
-    a.xy = at<float4>(ws, L.xy);
-    a.depth = at<float>(ws, L.depth);
-    a.conic_opacity = at<float4>(ws, L.conic);
-    a.rgb = at<float4>(ws, L.rgb);
-    a.radius = at<int>(ws, L.radius);
-    a.tau = at<float>(ws, L.tau);
-    a.status = &ctl->status;
-    return ok(launch_preprocess(a, s));
+    FrameSet<1> fs;
+    if (!collect(f, 1, &fs) || !valid_gaussians(f, g)) return GS_ERR_INVALID_ARG;
+    return preprocess_impl(fs, g, s);
 }
 
 gs_status gs_bin_sort(const gs_frame* f, cudaStream_t s) {
-    Layout L;
-    if (!valid_frame(f, &L)) return GS_ERR_INVALID_ARG;
-    void* ws = f->ws;
-    Control* ctl = at<Control>(ws, L.control);
-    gs_device_status* st = &ctl->status;
-    // flags + num_instances, then every counter and histogram
-    if (cudaMemsetAsync(st, 0, 2 * sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(&ctl->counters[0], 0, sizeof(Control) - offsetof(Control, counters), s) != cudaSuccess)
-        return GS_ERR_CUDA;
-    if (cudaMemsetAsync(at<char>(ws, L.diff), 0, L.diff_count * sizeof(int), s) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(at<char>(ws, L.scan_lb), 0, L.scan_lb_rows * sizeof(unsigned long long), s) != cudaSuccess)
-        return GS_ERR_CUDA;
-    const CamK cam = cam_k(f, L);
-    const bool key64 = f->cfg.sort_mode == GS_SORT_KEY64;
-
-    ScanArgs d;
-    d.n = f->n;
-    d.xy = at<float4>(ws, L.xy);
-    d.conic = at<float4>(ws, L.conic);
-    d.tau = at<float>(ws, L.tau);
-    d.radius = at<int>(ws, L.radius);
-    d.depth = at<float>(ws, L.depth);
-    d.cam = cam;
-    d.seg_tile = at<uint32_t>(ws, L.ikey[1]);
-    d.seg_off = d.seg_tile + (f->capacity > 0 ? f->capacity : 1);
-    d.seg_gid = at<uint32_t>(ws, L.ival[1]);
-    d.num_segments = &ctl->counters[30];
-    d.rect_only = f->cfg.tile_rule == GS_TILES_RECT;
-    d.diff = at<int>(ws, L.diff);
-    d.capacity = f->capacity;
-    d.hist = &ctl->hist_keys[0][0];
-    d.lookback = at<unsigned long long>(ws, L.scan_lb);
-    d.chunk_counter = &ctl->counters[0];
-    d.status = st;
-
-    if (!key64) {
-        // Phase 1: stable sort of all Gaussians by fp32 depth bits (culled ones last).
-        if (f->n > 0) {
-            DepthHistArgs h{f->n, at<float>(ws, L.depth), at<int>(ws, L.radius), &ctl->hist_depth[0][0],
-                            at<uint32_t>(ws, L.sort_lb[0]), &ctl->counters[31]};
-            if (launch_depth_hist(h, s) != cudaSuccess) return GS_ERR_CUDA;
-            const int chunks = (f->n + kSortTile - 1) / kSortTile;
-            for (int p = 0; p < kDepthPasses; ++p) {
-                SortPassArgs<uint32_t> a;
-                a.keys_in = p == 0 ? nullptr : at<uint32_t>(ws, L.gkey[(p + 1) % 2]);
-                a.vals_in = p == 0 ? nullptr : at<uint32_t>(ws, L.gval[(p + 1) % 2]);
-                a.depth_src = at<float>(ws, L.depth);
-                a.radius_src = at<int>(ws, L.radius);
-                a.keys_out = at<uint32_t>(ws, L.gkey[p % 2]);
-                a.vals_out = at<uint32_t>(ws, L.gval[p % 2]);
-                a.count_dev = nullptr;
-                a.count_host = (uint32_t)f->n;
-                a.shift = 8 * p;
-                a.hist = ctl->hist_depth[p];
-                a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
-                a.lookback_next = (p + 1 < kDepthPasses) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
-                a.chunk_counter = &ctl->counters[1 + p];
-                a.status = st;
-                if (launch_onesweep(a, chunks, s) != cudaSuccess) return GS_ERR_CUDA;
-            }
-        }
-        d.order = at<uint32_t>(ws, L.gval[(kDepthPasses - 1) % 2]);
-        d.count_dev = &ctl->counters[31];
-    } else {
-        d.order = nullptr;
-        d.count_dev = nullptr;
-    }
-    if (launch_scan_tiles(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
-    TileRangesArgs tr;
-    tr.diff = at<int>(ws, L.diff);
-    tr.tiles_x = L.tiles_x;
-    tr.tiles_y = L.tiles_y;
-    tr.ranges = at<uint32_t>(ws, L.ranges);
-    tr.tile_passes = key64 ? L.key_passes - 4 : L.key_passes;
-    tr.key_shift = key64 ? 32 : 0;
-    tr.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
-    tr.capacity = f->capacity;
-    if (launch_tile_ranges(tr, s) != cudaSuccess) return GS_ERR_CUDA;
-    EmitArgs e;
-    e.n = f->n;
-    e.seg_off = d.seg_off;
-    e.seg_tile = d.seg_tile;
-    e.seg_gid = d.seg_gid;
-    e.num_segments = d.num_segments;
-    e.depth = d.depth;
-    e.keys_out = at<void>(ws, L.ikey[0]);
-    e.vals_out = at<uint32_t>(ws, L.ival[0]);
-    e.capacity = f->capacity;
-    e.status = st;
-    if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
-    if (key64) return run_key_sort<unsigned long long>(f, L, ctl, s);
-    return run_key_sort<uint32_t>(f, L, ctl, s);
+    FrameSet<1> fs;
+    if (!collect(f, 1, &fs)) return GS_ERR_INVALID_ARG;
+    return bin_sort_impl(fs, s);
 }
 
 gs_status gs_render_forward(const gs_frame* f, const float bg[3], float* out_rgb, float* out_T, uint32_t* out_last,
                             cudaStream_t s) {
-    Layout L;
-    if (!valid_frame(f, &L) || !bg || !out_rgb || !out_T || !out_last) return GS_ERR_INVALID_ARG;
-    void* ws = f->ws;
-    RenderFwdArgs a;
-    a.n = f->n;
-    a.cam = cam_k(f, L);
-    a.cfg = cfg_k(f->cfg);
-    for (int k = 0; k < 3; ++k) a.bg[k] = bg[k];
-    a.batch = f->cfg.batch_depth;
-    a.ranges = at<uint32_t>(ws, L.ranges);
-    a.vals = at<uint32_t>(ws, vals_sorted_off(L));
-    a.xy = at<float4>(ws, L.xy);
-    a.conic_opacity = at<float4>(ws, L.conic);
-    a.rgb = at<float4>(ws, L.rgb);
-    a.out_rgb = out_rgb;
-    a.out_T = out_T;
-    a.out_last = out_last;
-    return ok(launch_render_forward(a, L.tiles, s));
+    FrameSet<1> fs;
+    if (!collect(f, 1, &fs) || !bg || !out_rgb || !out_T || !out_last) return GS_ERR_INVALID_ARG;
+    return render_forward_impl(fs, bg, &out_rgb, &out_T, &out_last, s);
 }
 
 gs_status gs_render_backward_tiles(const gs_frame* f, const float bg[3], const float* dL_drgb, const float* T,
                                    const uint32_t* last, cudaStream_t s) {
-    Layout L;
-    if (!valid_frame(f, &L) || !bg || !dL_drgb || !T || !last) return GS_ERR_INVALID_ARG;
+    FrameSet<1> fs;
+    if (!collect(f, 1, &fs) || !bg || !dL_drgb || !T || !last) return GS_ERR_INVALID_ARG;
     if (f->n == 0) return GS_OK;
-    void* ws = f->ws;
-    float* grad2d = at<float>(ws, L.grad2d);
-    if (cudaMemsetAsync(grad2d, 0, (size_t)f->n * 12 * sizeof(float), s) != cudaSuccess) return GS_ERR_CUDA;
-    gs_device_status* st = &at<Control>(ws, L.control)->status;
-    if (cudaMemsetAsync(&st->blended_pairs, 0, sizeof(st->blended_pairs), s) != cudaSuccess) return GS_ERR_CUDA;
-    RenderBwdArgs a;
-    a.n = f->n;
-    a.cam = cam_k(f, L);
-    a.cfg = cfg_k(f->cfg);
-    for (int k = 0; k < 3; ++k) a.bg[k] = bg[k];
-    a.batch = f->cfg.batch_depth;
-    a.ranges = at<uint32_t>(ws, L.ranges);
-    a.vals = at<uint32_t>(ws, vals_sorted_off(L));
-    a.xy = at<float4>(ws, L.xy);
-    a.conic_opacity = at<float4>(ws, L.conic);
-    a.rgb = at<float4>(ws, L.rgb);
-    a.dL_drgb = dL_drgb;
-    a.T_final = T;
-    a.last = last;
-    a.grad2d = grad2d;
-    a.blended = reinterpret_cast<unsigned long long*>(&st->blended_pairs);
-    return ok(launch_render_backward(a, L.tiles, s));
+    return render_backward_tiles_impl(fs, bg, &dL_drgb, &T, &last, s);
 }
 
 gs_status gs_render_backward_gaussians(const gs_frame* f, const gs_gaussians* g, const gs_gradients* gr,
                                        int accumulate, cudaStream_t s) {
-    Layout L;
-    if (!valid_frame(f, &L) || !valid_gaussians(f, g) || !gr) return GS_ERR_INVALID_ARG;
-    if (f->n > 0 && (!gr->means || !gr->scales || !gr->quats || !gr->opacities || !gr->sh)) return GS_ERR_INVALID_ARG;
-    if (f->n > 0 && reinterpret_cast<uintptr_t>(gr->quats) % 16) return GS_ERR_INVALID_ARG;
+    FrameSet<1> fs;
+    if (!collect(f, 1, &fs) || !valid_gaussians(f, g) || !valid_gradients(f, gr)) return GS_ERR_INVALID_ARG;
     if (f->n == 0) return GS_OK;
-    void* ws = f->ws;
-    PreprocessBwdArgs b;
-    b.n = f->n;
-    b.means = g->means; b.scales = g->scales; b.quats = g->quats; b.opacities = g->opacities; b.sh = g->sh;
-    b.sh_degree = g->sh_degree; b.sh_stride = g->sh_stride;
-    b.cam = cam_k(f, L);
-    b.cfg = cfg_k(f->cfg);
-    b.grad2d = at<float>(ws, L.grad2d);
-    b.rgb = at<float4>(ws, L.rgb);
-    b.radius = at<int>(ws, L.radius);
-    b.g_means = gr->means; b.g_scales = gr->scales; b.g_quats = gr->quats; b.g_opacities = gr->opacities;
-    b.g_sh = gr->sh; b.g_mean2d = gr->mean2d;
-    b.accumulate = accumulate;
-    return ok(launch_preprocess_backward(b, s));
+    return render_backward_gaussians_impl(fs, g, gr, accumulate, s);
 }
 
 gs_status gs_render_backward(const gs_frame* f, const gs_gaussians* g, const float bg[3], const float* dL_drgb,
                              const float* T, const uint32_t* last, const gs_gradients* gr, int accumulate,
                              cudaStream_t s) {
-    Layout L;
-    if (!valid_frame(f, &L) || !valid_gaussians(f, g) || !bg || !dL_drgb || !T || !last || !gr) return GS_ERR_INVALID_ARG;
-    if (f->n > 0 && (!gr->means || !gr->scales || !gr->quats || !gr->opacities || !gr->sh)) return GS_ERR_INVALID_ARG;
-    if (f->n > 0 && reinterpret_cast<uintptr_t>(gr->quats) % 16) return GS_ERR_INVALID_ARG;
-    const gs_status st = gs_render_backward_tiles(f, bg, dL_drgb, T, last, s);
+    FrameSet<1> fs;
+    if (!collect(f, 1, &fs) || !valid_gaussians(f, g) || !bg || !dL_drgb || !T || !last || !valid_gradients(f, gr))
+        return GS_ERR_INVALID_ARG;
+    if (f->n == 0) return GS_OK;
+    const gs_status st = render_backward_tiles_impl(fs, bg, &dL_drgb, &T, &last, s);
     if (st != GS_OK) return st;
-    return gs_render_backward_gaussians(f, g, gr, accumulate, s);
+    return render_backward_gaussians_impl(fs, g, gr, accumulate, s);
+}
+
+// ---- batches ----------------------------------------------------------------------------
+
+gs_status gs_batch_preprocess(const gs_frame* frames, const gs_gaussians* g, int views, cudaStream_t s) {
+    if (views == 1) return gs_preprocess(frames, g, s);
+    FrameSet<kMaxFrames> fs;
+    if (!g || !collect(frames, views, &fs)) return GS_ERR_INVALID_ARG;
+    for (int v = 0; v < views; ++v)
+        if (!valid_gaussians(&frames[v], &g[v])) return GS_ERR_INVALID_ARG;
+    return preprocess_impl(fs, g, s);
+}
+
+gs_status gs_batch_bin_sort(const gs_frame* frames, int views, cudaStream_t s) {
+    if (views == 1) return gs_bin_sort(frames, s);
+    FrameSet<kMaxFrames> fs;
+    if (!collect(frames, views, &fs)) return GS_ERR_INVALID_ARG;
+    return bin_sort_impl(fs, s);
+}
+
+gs_status gs_batch_render_forward(const gs_frame* frames, int views, const float* bg, float* const* out_rgb,
+                                  float* const* out_T, uint32_t* const* out_last, cudaStream_t s) {
+    if (!bg || !out_rgb || !out_T || !out_last) return GS_ERR_INVALID_ARG;
+    if (views == 1) return gs_render_forward(frames, bg, out_rgb[0], out_T[0], out_last[0], s);
+    FrameSet<kMaxFrames> fs;
+    if (!collect(frames, views, &fs)) return GS_ERR_INVALID_ARG;
+    for (int v = 0; v < views; ++v)
+        if (!out_rgb[v] || !out_T[v] || !out_last[v]) return GS_ERR_INVALID_ARG;
+    return render_forward_impl(fs, bg, out_rgb, out_T, out_last, s);
+}
+
+gs_status gs_batch_render_backward(const gs_frame* frames, const gs_gaussians* g, int views, const float* bg,
+                                   const float* const* dL_drgb, const float* const* T, const uint32_t* const* last,
+                                   const gs_gradients* grads, int accumulate, cudaStream_t s) {
+    if (!g || !bg || !dL_drgb || !T || !last || !grads) return GS_ERR_INVALID_ARG;
+    if (views == 1) return gs_render_backward(frames, g, bg, dL_drgb[0], T[0], last[0], grads, accumulate, s);
+    FrameSet<kMaxFrames> fs;
+    if (!collect(frames, views, &fs)) return GS_ERR_INVALID_ARG;
+    for (int v = 0; v < views; ++v)
+        if (!valid_gaussians(&frames[v], &g[v]) || !dL_drgb[v] || !T[v] || !last[v] ||
+            !valid_gradients(&frames[v], &grads[v]))
+            return GS_ERR_INVALID_ARG;
+    int group_of[kMaxFrames], first[kMaxFrames], groups = 0;
+    if (!group_frames<kMaxFrames>(views, g, grads, group_of, first, &groups)) return GS_ERR_INVALID_ARG;
+    const gs_status st = render_backward_tiles_impl(fs, bg, dL_drgb, T, last, s);
+    if (st != GS_OK) return st;
+    return render_backward_gaussians_impl(fs, g, grads, accumulate, s);
 }
 
 gs_status gs_read_status(const gs_frame* f, gs_device_status* out, cudaStream_t s) {

@@ -31,6 +31,29 @@ constexpr int kEmitThreads = 256;
 
 // Render: one block per tile, 4 threads per tile row, each owning tile_w / 4 pixels.
 
+// Batches: one launch per stage serves up to kMaxFrames frames (views of one scene, or of
+// several scenes).  A kernel receives the argument blocks of all its frames by value; frame f
+// owns the work units [base[f], base[f + 1]) (blocks, tiles or Gaussians) when the split is
+// known on the host, otherwise the kernel derives it from device-side counts.  A single frame
+// is a batch of one (MAXF = 1).
+constexpr int kMaxFrames = 32;
+
+template <typename A, int MAXF>
+struct Multi {
+    int frames;
+    uint32_t base[MAXF + 1];
+    A a[MAXF];
+};
+
+// Frame owning work unit g of a host-side split (frames <= 32: a linear walk).
+template <int MAXF>
+__device__ __forceinline__ int find_frame(const uint32_t* base, int frames, uint32_t g) {
+    if (MAXF == 1) return 0;
+    int f = 0;
+    while (f + 1 < frames && base[f + 1] <= g) ++f;
+    return f;
+}
+
 // Control block at the start of the workspace.
 struct Control {
     gs_device_status status;
@@ -80,6 +103,24 @@ struct PreprocessBwdArgs {
     float* g_sh;
     float* g_mean2d;
     int accumulate;
+};
+
+// Per-Gaussian backward of a batch: frames grouped by the Gaussians they render (group g =
+// frames [frame_begin[g], frame_begin[g + 1]), all with the same Gaussians, gradient outputs
+// and accumulate flag); group g owns blocks [block_base[g], block_base[g + 1]).
+template <int MAXF>
+struct BwdPlan {
+    int groups;
+    uint32_t block_base[MAXF + 1];
+    int frame_begin[MAXF + 1];
+    PreprocessBwdArgs a[MAXF];
+};
+
+// Zeroing of up to kClearRegions buffers per frame in one launch (batches).
+constexpr int kClearRegions = 4;
+struct ClearArgs {
+    uint32_t* ptr[kClearRegions];
+    unsigned long long words[kClearRegions];
 };
 
 struct DepthHistArgs {
@@ -199,16 +240,17 @@ struct RenderBwdArgs {
 // Host-side launchers (defined next to their kernels).  Each returns the launch status.
 // Persistent kernels size their grid as SM count x resident blocks per SM.
 int persistent_grid(const void* kernel, int threads);
-cudaError_t launch_preprocess(const PreprocessArgs& a, cudaStream_t s);
-cudaError_t launch_preprocess_backward(const PreprocessBwdArgs& a, cudaStream_t s);
-cudaError_t launch_depth_hist(const DepthHistArgs& a, cudaStream_t s);
-cudaError_t launch_onesweep(const SortPassArgs<uint32_t>& a, int max_chunks, cudaStream_t s);
-cudaError_t launch_onesweep(const SortPassArgs<unsigned long long>& a, int max_chunks, cudaStream_t s);
-cudaError_t launch_scan_tiles(const ScanArgs& a, bool key64, cudaStream_t s);
-cudaError_t launch_tile_ranges(const TileRangesArgs& a, cudaStream_t s);
-cudaError_t launch_emit(const EmitArgs& a, bool key64, cudaStream_t s);
-cudaError_t launch_sort_prepare(const SortPrepareArgs& a, cudaStream_t s);
-cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, cudaStream_t s);
-cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, cudaStream_t s);
+template <int MAXF> cudaError_t launch_preprocess(Multi<PreprocessArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_preprocess_backward(BwdPlan<MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_depth_hist(Multi<DepthHistArgs, MAXF>& m, cudaStream_t s);
+template <typename KeyT, int MAXF>
+cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_chunks, cudaStream_t s);
+template <int MAXF> cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s);
+template <int MAXF> cudaError_t launch_tile_ranges(const Multi<TileRangesArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_emit(const Multi<EmitArgs, MAXF>& m, bool key64, cudaStream_t s);
+template <int MAXF> cudaError_t launch_sort_prepare(const Multi<SortPrepareArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_render_forward(Multi<RenderFwdArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_render_backward(Multi<RenderBwdArgs, MAXF>& m, cudaStream_t s);
+cudaError_t launch_clear(const Multi<ClearArgs, kMaxFrames>& m, cudaStream_t s);
 
 }  // namespace gs

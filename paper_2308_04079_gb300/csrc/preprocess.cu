@@ -123,10 +123,12 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, float (&f)
 
 }  // namespace
 
-template <int DEG, bool VEC>
-__global__ void __launch_bounds__(256) k_preprocess_t(PreprocessArgs a) {
+template <int DEG, bool VEC, int MAXF>
+__global__ void __launch_bounds__(256) k_preprocess_t(const __grid_constant__ Multi<PreprocessArgs, MAXF> m) {
     constexpr int D = (DEG + 1) * (DEG + 1);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns blocks [base[f], base[f+1])
+    const PreprocessArgs& a = m.a[f];
+    const int i = (int)(blockIdx.x - m.base[f]) * blockDim.x + threadIdx.x;
     bool visible = false;
     if (i < a.n) {
         const CamK& c = a.cam;
@@ -198,36 +200,24 @@ __global__ void __launch_bounds__(256) k_preprocess_t(PreprocessArgs a) {
     if ((threadIdx.x & 31) == 0 && vis) atomicAdd(&a.status->num_visible, (uint32_t)__popc(vis));
 }
 
-template <int DEG, bool VEC>
-__global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs a) {
-    constexpr int D = (DEG + 1) * (DEG + 1);
-    constexpr int NF = 4 * ((3 * D + 3) / 4);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    float* gsh = a.g_sh + (size_t)i * a.sh_stride * 3;
-    const int row = a.sh_stride * 3;   // floats per Gaussian in the SH buffers
-    const int radius = a.radius[i];
-    if (radius <= 0) {
-        if (!a.accumulate) {
-            for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = 0.f; a.g_scales[3 * i + k] = 0.f; }
-            reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            a.g_opacities[i] = 0.f;
-            if (VEC) {
-                for (int k = 0; k < row / 4; ++k) reinterpret_cast<float4*>(gsh)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                for (int k = 0; k < row; ++k) gsh[k] = 0.f;
-            }
-            if (a.g_mean2d) { a.g_mean2d[2 * i] = 0.f; a.g_mean2d[2 * i + 1] = 0.f; }
-        }
-        return;
-    }
+// Gradient of one Gaussian from one view, added into the accumulators (the Gaussian's
+// parameters and SH coefficients are loaded once for all views of a batch).
+template <int DEG>
+struct BwdAcc {
+    static constexpr int D = (DEG + 1) * (DEG + 1);
+    static constexpr int NF = 4 * ((3 * D + 3) / 4);
+    float gm[3], gs[3], gq[4], go, du, dv;
+    float gsh[NF];
+};
+
+template <int DEG>
+__device__ __forceinline__ void bwd_view(const PreprocessBwdArgs& a, int i, const float mu[3], const float s[3],
+                                         float4 q, const float* f, BwdAcc<DEG>& acc) {
+    constexpr int D = BwdAcc<DEG>::D;
     const CamK& c = a.cam;
     const float4 g0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i];       // du dv dS00 dS01
     const float4 g1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];   // dS11 do dr dg
     const float g2 = a.grad2d[12 * i + 8];                                    // db(rgb)
-    const float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
-    const float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
-    const float4 q = reinterpret_cast<const float4*>(a.quats)[i];
     Proj p;
     project_mean(mu, c, p);
     project_cov(s, q, c, a.cfg.dilation, p);
@@ -252,9 +242,9 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs
         for (int k = 0; k < 3; ++k)
             dT2[3 * r + k] = dV[3 * r] * p.M[3 * k] + dV[3 * r + 1] * p.M[3 * k + 1] + dV[3 * r + 2] * p.M[3 * k + 2];
     // M = R diag(s).
-    float gs3[3], dR[9];
+    float dR[9];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gs3[k] = dM[k] * p.R[k] + dM[3 + k] * p.R[3 + k] + dM[6 + k] * p.R[6 + k];
+    for (int k = 0; k < 3; ++k) acc.gs[k] += dM[k] * p.R[k] + dM[3 + k] * p.R[3 + k] + dM[6 + k] * p.R[6 + k];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -270,8 +260,10 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs
     dq[3] = 2.f * (-2.f * qk * dR[0] - qr * dR[1] + qi * dR[2] + qr * dR[3] - 2.f * qk * dR[4] + qj * dR[5] +
                    qi * dR[6] + qj * dR[7]);
     const float proj = dq[0] * qr + dq[1] * qi + dq[2] * qj + dq[3] * qk;
-    const float4 gq = make_float4((dq[0] - qr * proj) * p.qinv, (dq[1] - qi * proj) * p.qinv,
-                                  (dq[2] - qj * proj) * p.qinv, (dq[3] - qk * proj) * p.qinv);
+    acc.gq[0] += (dq[0] - qr * proj) * p.qinv;
+    acc.gq[1] += (dq[1] - qi * proj) * p.qinv;
+    acc.gq[2] += (dq[2] - qj * proj) * p.qinv;
+    acc.gq[3] += (dq[3] - qk * proj) * p.qinv;
     // T2 = J W with J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]].
     float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
 #pragma unroll
@@ -288,9 +280,8 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs
     const float dt1 = dv * fy * iz - dJ12 * fy * iz2;
     const float dt2 = -du * fx * p.xz * iz - dv * fy * p.yz * iz - dJ00 * fx * iz2 + dJ02 * 2.f * fx * p.xz * iz2 -
                       dJ11 * fy * iz2 + dJ12 * 2.f * fy * p.yz * iz2;
-    float gm[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) gm[k] = c.R[k] * dt0 + c.R[3 + k] * dt1 + c.R[6 + k] * dt2;
+    for (int k = 0; k < 3; ++k) acc.gm[k] += c.R[k] * dt0 + c.R[3 + k] * dt1 + c.R[6 + k] * dt2;
 
     // Colour: dL/dSH and the view-direction term.
     const float4 rgbm = a.rgb[i];
@@ -305,27 +296,71 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs
     float3 dY[16];
     sh_basis(DEG, ex, ey, ez, Y);
     sh_basis_grad(DEG, ex, ey, ez, dY);
-    float f[NF];
-    load_sh<D, VEC>(a.sh + (size_t)i * row, f);
     float ddx = 0.f, ddy = 0.f, ddz = 0.f;
-    float gout[NF];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const float w = f[3 * k] * dr + f[3 * k + 1] * dg + f[3 * k + 2] * dbl;
         ddx += w * dY[k].x;
         ddy += w * dY[k].y;
         ddz += w * dY[k].z;
-        gout[3 * k] = Y[k] * dr;
-        gout[3 * k + 1] = Y[k] * dg;
-        gout[3 * k + 2] = Y[k] * dbl;
+        acc.gsh[3 * k] += Y[k] * dr;
+        acc.gsh[3 * k + 1] += Y[k] * dg;
+        acc.gsh[3 * k + 2] += Y[k] * dbl;
     }
+    const float dp = ddx * ex + ddy * ey + ddz * ez;
+    acc.gm[0] += (ddx - ex * dp) * ninv;
+    acc.gm[1] += (ddy - ey * dp) * ninv;
+    acc.gm[2] += (ddz - ez * dp) * ninv;
+    acc.go += g1.y;
+    acc.du += du;
+    acc.dv += dv;
+}
+
+// One thread per Gaussian of a group of frames that render the same Gaussians (views of one
+// scene): the gradients of all the group's views are summed in registers and written once
+// (or added to the output when accumulating).  Group g owns blocks [block_base[g],
+// block_base[g+1]) and frames [frame_begin[g], frame_begin[g+1]).
+template <int DEG, bool VEC, int MAXF>
+__global__ void __launch_bounds__(256) k_preprocess_backward_t(const __grid_constant__ BwdPlan<MAXF> m) {
+    constexpr int D = (DEG + 1) * (DEG + 1);
+    constexpr int NF = BwdAcc<DEG>::NF;
+    const int g = find_frame<MAXF>(m.block_base, m.groups, blockIdx.x);
+    const int f0 = m.frame_begin[g], f1 = m.frame_begin[g + 1];
+    const PreprocessBwdArgs& a = m.a[f0];   // Gaussians and outputs shared by the group
+    const int i = (int)(blockIdx.x - m.block_base[g]) * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float* gsh = a.g_sh + (size_t)i * a.sh_stride * 3;
+    const int row = a.sh_stride * 3;   // floats per Gaussian in the SH buffers
+    BwdAcc<DEG> acc;
 #pragma unroll
-    for (int k = 3 * D; k < NF; ++k) gout[k] = 0.f;
+    for (int k = 0; k < 3; ++k) acc.gm[k] = acc.gs[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc.gq[k] = 0.f;
+    acc.go = acc.du = acc.dv = 0.f;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) acc.gsh[k] = 0.f;
+    bool any = false;
+    float mu[3], s[3], f[NF];
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nv = MAXF == 1 ? 1 : f1 - f0;   // a single frame: straight-line code
+    for (int k = 0; k < nv; ++k) {
+        const PreprocessBwdArgs& av = m.a[f0 + k];
+        if (av.radius[i] <= 0) continue;
+        if (!any) {
+            any = true;
+            mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
+            s[0] = a.scales[3 * i]; s[1] = a.scales[3 * i + 1]; s[2] = a.scales[3 * i + 2];
+            q = reinterpret_cast<const float4*>(a.quats)[i];
+            load_sh<D, VEC>(a.sh + (size_t)i * row, f);
+        }
+        bwd_view<DEG>(av, i, mu, s, q, f, acc);
+    }
+    if (!any && a.accumulate) return;   // no view saw it: nothing to add
     if (VEC) {
         float4* g4 = reinterpret_cast<float4*>(gsh);
 #pragma unroll
         for (int k = 0; k < NF / 4; ++k) {
-            float4 v = make_float4(gout[4 * k], gout[4 * k + 1], gout[4 * k + 2], gout[4 * k + 3]);
+            float4 v = make_float4(acc.gsh[4 * k], acc.gsh[4 * k + 1], acc.gsh[4 * k + 2], acc.gsh[4 * k + 3]);
             if (a.accumulate) {
                 const float4 o4 = g4[k];
                 v = make_float4(o4.x + v.x, o4.y + v.y, o4.z + v.z, o4.w + v.w);
@@ -337,28 +372,24 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(PreprocessBwdArgs
     } else {
 #pragma unroll
         for (int k = 0; k < 3 * D; ++k) {
-            if (a.accumulate) gsh[k] += gout[k];
-            else gsh[k] = gout[k];
+            if (a.accumulate) gsh[k] += acc.gsh[k];
+            else gsh[k] = acc.gsh[k];
         }
         if (!a.accumulate)
             for (int k = 3 * D; k < row; ++k) gsh[k] = 0.f;
     }
-    const float dp = ddx * ex + ddy * ey + ddz * ez;
-    gm[0] += (ddx - ex * dp) * ninv;
-    gm[1] += (ddy - ey * dp) * ninv;
-    gm[2] += (ddz - ez * dp) * ninv;
-
+    const float4 gq = make_float4(acc.gq[0], acc.gq[1], acc.gq[2], acc.gq[3]);
     if (a.accumulate) {
-        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] += gm[k]; a.g_scales[3 * i + k] += gs3[k]; }
+        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] += acc.gm[k]; a.g_scales[3 * i + k] += acc.gs[k]; }
         const float4 o4 = reinterpret_cast<float4*>(a.g_quats)[i];
         reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(o4.x + gq.x, o4.y + gq.y, o4.z + gq.z, o4.w + gq.w);
-        a.g_opacities[i] += g1.y;
-        if (a.g_mean2d) { a.g_mean2d[2 * i] += du; a.g_mean2d[2 * i + 1] += dv; }
+        a.g_opacities[i] += acc.go;
+        if (a.g_mean2d) { a.g_mean2d[2 * i] += acc.du; a.g_mean2d[2 * i + 1] += acc.dv; }
     } else {
-        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = gm[k]; a.g_scales[3 * i + k] = gs3[k]; }
+        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = acc.gm[k]; a.g_scales[3 * i + k] = acc.gs[k]; }
         reinterpret_cast<float4*>(a.g_quats)[i] = gq;
-        a.g_opacities[i] = g1.y;
-        if (a.g_mean2d) { a.g_mean2d[2 * i] = du; a.g_mean2d[2 * i + 1] = dv; }
+        a.g_opacities[i] = acc.go;
+        if (a.g_mean2d) { a.g_mean2d[2 * i] = acc.du; a.g_mean2d[2 * i + 1] = acc.dv; }
     }
 }
 
@@ -380,44 +411,57 @@ bool sh_vectorisable(const float* sh, int sh_stride, const float* gsh = nullptr)
     return base && (3 * sh_stride) % 4 == 0;
 }
 
-template <int DEG>
-void preprocess_deg(const PreprocessArgs& a, bool vec, cudaStream_t s) {
-    const int grid = (a.n + 255) / 256;
-    if (vec) k_preprocess_t<DEG, true><<<grid, 256, 0, s>>>(a);
-    else k_preprocess_t<DEG, false><<<grid, 256, 0, s>>>(a);
+template <int DEG, int MAXF>
+void preprocess_deg(const Multi<PreprocessArgs, MAXF>& m, bool vec, cudaStream_t s) {
+    if (vec) k_preprocess_t<DEG, true, MAXF><<<m.base[m.frames], 256, 0, s>>>(m);
+    else k_preprocess_t<DEG, false, MAXF><<<m.base[m.frames], 256, 0, s>>>(m);
 }
 
-template <int DEG>
-void preprocess_bwd_deg(const PreprocessBwdArgs& a, bool vec, cudaStream_t s) {
-    const int grid = (a.n + 255) / 256;
-    if (vec) k_preprocess_backward_t<DEG, true><<<grid, 256, 0, s>>>(a);
-    else k_preprocess_backward_t<DEG, false><<<grid, 256, 0, s>>>(a);
+template <int DEG, int MAXF>
+void preprocess_bwd_deg(const BwdPlan<MAXF>& m, bool vec, cudaStream_t s) {
+    if (vec) k_preprocess_backward_t<DEG, true, MAXF><<<m.block_base[m.groups], 256, 0, s>>>(m);
+    else k_preprocess_backward_t<DEG, false, MAXF><<<m.block_base[m.groups], 256, 0, s>>>(m);
 }
 
 }  // namespace
 
-cudaError_t launch_preprocess(const PreprocessArgs& a, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
+// Frames of one launch share the SH degree and the SH row alignment; the caller groups them.
+template <int MAXF>
+cudaError_t launch_preprocess(Multi<PreprocessArgs, MAXF>& m, cudaStream_t s) {
+    m.base[0] = 0;
+    for (int f = 0; f < m.frames; ++f) m.base[f + 1] = m.base[f] + (uint32_t)((m.a[f].n + 255) / 256);
+    if (m.base[m.frames] == 0) return cudaSuccess;
+    const PreprocessArgs& a = m.a[0];
     const bool vec = sh_vectorisable(a.sh, a.sh_stride);
     switch (a.sh_degree) {
-        case 0: preprocess_deg<0>(a, vec, s); break;
-        case 1: preprocess_deg<1>(a, vec, s); break;
-        case 2: preprocess_deg<2>(a, vec, s); break;
-        default: preprocess_deg<3>(a, vec, s); break;
+        case 0: preprocess_deg<0>(m, vec, s); break;
+        case 1: preprocess_deg<1>(m, vec, s); break;
+        case 2: preprocess_deg<2>(m, vec, s); break;
+        default: preprocess_deg<3>(m, vec, s); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_preprocess_backward(const PreprocessBwdArgs& a, cudaStream_t s) {
-    if (a.n <= 0) return cudaSuccess;
+template <int MAXF>
+cudaError_t launch_preprocess_backward(BwdPlan<MAXF>& m, cudaStream_t s) {
+    m.block_base[0] = 0;
+    for (int g = 0; g < m.groups; ++g)
+        m.block_base[g + 1] = m.block_base[g] + (uint32_t)((m.a[m.frame_begin[g]].n + 255) / 256);
+    if (m.block_base[m.groups] == 0) return cudaSuccess;
+    const PreprocessBwdArgs& a = m.a[0];
     const bool vec = sh_vectorisable(a.sh, a.sh_stride, a.g_sh);
     switch (a.sh_degree) {
-        case 0: preprocess_bwd_deg<0>(a, vec, s); break;
-        case 1: preprocess_bwd_deg<1>(a, vec, s); break;
-        case 2: preprocess_bwd_deg<2>(a, vec, s); break;
-        default: preprocess_bwd_deg<3>(a, vec, s); break;
+        case 0: preprocess_bwd_deg<0>(m, vec, s); break;
+        case 1: preprocess_bwd_deg<1>(m, vec, s); break;
+        case 2: preprocess_bwd_deg<2>(m, vec, s); break;
+        default: preprocess_bwd_deg<3>(m, vec, s); break;
     }
     return cudaGetLastError();
 }
+
+template cudaError_t launch_preprocess<1>(Multi<PreprocessArgs, 1>&, cudaStream_t);
+template cudaError_t launch_preprocess<kMaxFrames>(Multi<PreprocessArgs, kMaxFrames>&, cudaStream_t);
+template cudaError_t launch_preprocess_backward<1>(BwdPlan<1>&, cudaStream_t);
+template cudaError_t launch_preprocess_backward<kMaxFrames>(BwdPlan<kMaxFrames>&, cudaStream_t);
 
 }  // namespace gs

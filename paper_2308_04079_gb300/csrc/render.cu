@@ -92,14 +92,16 @@ __device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, fl
     return __fmaf_rn(p, p, qq);
 }
 
-template <int PX>
-__global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
+template <int PX, int MAXF>
+__global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__ Multi<RenderFwdArgs, MAXF> m) {
+    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
+    const RenderFwdArgs& a = m.a[f];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
     float2* s_lim = reinterpret_cast<float2*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
     const CamK& c = a.cam;
-    const int tile = blockIdx.x;
+    const int tile = (int)(blockIdx.x - m.base[f]);
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
     const int nthreads = blockDim.x;
     const int ly = threadIdx.x >> 2, c0 = threadIdx.x & 3;
@@ -184,8 +186,10 @@ __global__ void __launch_bounds__(64) k_render_forward_t(RenderFwdArgs a) {
     }
 }
 
-template <int PX>
-__global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
+template <int PX, int MAXF>
+__global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant__ Multi<RenderBwdArgs, MAXF> m) {
+    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);
+    const RenderBwdArgs& a = m.a[f];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(RenderBwdArgs a) {
         reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * a.batch);
     __shared__ uint32_t s_max;
     const CamK& c = a.cam;
-    const int tile = blockIdx.x;
+    const int tile = (int)(blockIdx.x - m.base[f]);
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
     const int nthreads = blockDim.x;
     const int ly = threadIdx.x >> 2, c0 = threadIdx.x & 3;
@@ -335,20 +339,41 @@ size_t bwd_smem(int batch) {
 
 }  // namespace
 
-cudaError_t launch_render_forward(const RenderFwdArgs& a, int tiles, cudaStream_t s) {
-    if (tiles <= 0) return cudaSuccess;
+// Tiles of every frame, in frame order (frames without Gaussians still get their background
+// and transmittance written); all frames of a batch share the tile shape and the batch depth.
+template <typename A, int MAXF>
+static uint32_t tile_split(Multi<A, MAXF>& m) {
+    m.base[0] = 0;
+    for (int f = 0; f < m.frames; ++f)
+        m.base[f + 1] = m.base[f] + (uint32_t)(m.a[f].cam.tiles_x * m.a[f].cam.tiles_y);
+    return m.base[m.frames];
+}
+
+template <int MAXF>
+cudaError_t launch_render_forward(Multi<RenderFwdArgs, MAXF>& m, cudaStream_t s) {
+    const uint32_t tiles = tile_split(m);
+    if (tiles == 0) return cudaSuccess;
+    const RenderFwdArgs& a = m.a[0];
     const int nt = 4 * a.cam.tile_h;
-    if (a.cam.tile_w == 16) k_render_forward_t<4><<<tiles, nt, fwd_smem(a.batch), s>>>(a);
-    else k_render_forward_t<2><<<tiles, nt, fwd_smem(a.batch), s>>>(a);
+    if (a.cam.tile_w == 16) k_render_forward_t<4, MAXF><<<tiles, nt, fwd_smem(a.batch), s>>>(m);
+    else k_render_forward_t<2, MAXF><<<tiles, nt, fwd_smem(a.batch), s>>>(m);
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_backward(const RenderBwdArgs& a, int tiles, cudaStream_t s) {
-    if (tiles <= 0) return cudaSuccess;
+template <int MAXF>
+cudaError_t launch_render_backward(Multi<RenderBwdArgs, MAXF>& m, cudaStream_t s) {
+    const uint32_t tiles = tile_split(m);
+    if (tiles == 0) return cudaSuccess;
+    const RenderBwdArgs& a = m.a[0];
     const int nt = 4 * a.cam.tile_h;
-    if (a.cam.tile_w == 16) k_render_backward_t<4><<<tiles, nt, bwd_smem(a.batch), s>>>(a);
-    else k_render_backward_t<2><<<tiles, nt, bwd_smem(a.batch), s>>>(a);
+    if (a.cam.tile_w == 16) k_render_backward_t<4, MAXF><<<tiles, nt, bwd_smem(a.batch), s>>>(m);
+    else k_render_backward_t<2, MAXF><<<tiles, nt, bwd_smem(a.batch), s>>>(m);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_render_forward<1>(Multi<RenderFwdArgs, 1>&, cudaStream_t);
+template cudaError_t launch_render_forward<kMaxFrames>(Multi<RenderFwdArgs, kMaxFrames>&, cudaStream_t);
+template cudaError_t launch_render_backward<1>(Multi<RenderBwdArgs, 1>&, cudaStream_t);
+template cudaError_t launch_render_backward<kMaxFrames>(Multi<RenderBwdArgs, kMaxFrames>&, cudaStream_t);
 
 }  // namespace gs

@@ -80,12 +80,16 @@ extern "C" gs_status gs_depth_order_static(int n, const float* depth, const int*
     if (n == 0) return GS_OK;
     if (cudaMemsetAsync(sc->hist, 0, sizeof(sc->hist) + sizeof(sc->counters), s) != cudaSuccess) return GS_ERR_CUDA;
 
-    DepthHistArgs h{n, depth, radius, &sc->hist[0][0], sc->lookback[0], &status->num_visible};
+    Multi<DepthHistArgs, 1> h;
+    h.frames = 1;
+    h.a[0] = DepthHistArgs{n, depth, radius, &sc->hist[0][0], sc->lookback[0], &status->num_visible};
     if (launch_depth_hist(h, s) != cudaSuccess) return GS_ERR_CUDA;
     const int chunks = (n + kSortTile - 1) / kSortTile;
     for (int p = 0; p < kDepthPasses; ++p) {
         const bool last = p + 1 == kDepthPasses;
-        SortPassArgs<uint32_t> a;
+        Multi<SortPassArgs<uint32_t>, 1> m;
+        m.frames = 1;
+        SortPassArgs<uint32_t>& a = m.a[0];
         a.keys_in = p == 0 ? nullptr : sc->keys[(p + 1) % 2];
         a.vals_in = p == 0 ? nullptr : sc->vals[(p + 1) % 2];
         a.depth_src = depth;
@@ -100,7 +104,7 @@ extern "C" gs_status gs_depth_order_static(int n, const float* depth, const int*
         a.lookback_next = last ? nullptr : sc->lookback[(p + 1) % 2];
         a.chunk_counter = &sc->counters[p];
         a.status = status;
-        if (launch_onesweep(a, chunks, s) != cudaSuccess) return GS_ERR_CUDA;
+        if (launch_onesweep(m, chunks, s) != cudaSuccess) return GS_ERR_CUDA;
     }
     return GS_OK;
 }

@@ -203,6 +203,76 @@ class Frame:
         self.last_status = st
 
 
+def _gradients_struct(grads: dict) -> abi.gs_gradients:
+    gr = abi.gs_gradients()
+    gr.means, gr.scales, gr.quats = _ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"])
+    gr.opacities, gr.sh, gr.mean2d = _ptr(grads["opacities"]), _ptr(grads["sh"]), _ptr(grads.get("mean2d"))
+    return gr
+
+
+class FrameBatch:
+    """Several frames (views of one or more scenes) rendered with one launch per kernel:
+    ``frames[v]`` renders ``gaussians[v]``.  Frames that render the same GaussianTensors and
+    receive the same gradient dict have their gradients summed (see gs_batch_render_backward)."""
+
+    def __init__(self, frames: list, gaussians: list):
+        if not 1 <= len(frames) <= abi.GS_MAX_BATCH or len(frames) != len(gaussians):
+            raise ValueError("a batch holds 1..32 frames, one GaussianTensors each")
+        self.frames = frames
+        self.gaussians = gaussians
+
+    def _structs(self):
+        return [f.frame for f in self.frames]
+
+    def preprocess(self) -> None:
+        abi.gs_batch_preprocess(self._structs(), [g.struct() for g in self.gaussians], _stream())
+
+    def bin_sort(self) -> None:
+        abi.gs_batch_bin_sort(self._structs(), _stream())
+
+    def ensure_binned(self) -> None:
+        """preprocess + bin_sort of every frame; frames whose capacity was too small grow and
+        the batch is binned again."""
+        for _ in range(2):
+            self.preprocess()
+            self.bin_sort()
+            grown = False
+            for f in self.frames:
+                code, st = f.status()
+                if code == abi.GS_ERR_CAPACITY:
+                    f._alloc(int(st.num_instances * 1.25) + 1024)
+                    grown = True
+                elif code == abi.GS_ERR_TIMEOUT:
+                    raise abi.GSError(code, "gs_batch_bin_sort")
+                f.last_status = st
+            if not grown:
+                return
+        raise abi.GSError(abi.GS_ERR_CAPACITY, "gs_batch_bin_sort")
+
+    def outputs(self):
+        return [f.outputs() for f in self.frames]
+
+    def render_forward(self, bg, outs) -> None:
+        """bg: per-view (r, g, b) or one triple for all; outs: per-view (rgb, T, last)."""
+        bgs = self._bgs(bg)
+        abi.gs_batch_render_forward(self._structs(), bgs, [o[0].data_ptr() for o in outs],
+                                    [o[1].data_ptr() for o in outs], [o[2].data_ptr() for o in outs], _stream())
+
+    def render_backward(self, bg, dL_drgb: list, outs, grads: list, accumulate: bool = False) -> None:
+        """dL_drgb: per-view tensors; outs: the forward's per-view (rgb, T, last); grads:
+        per-view gradient dicts (the same dict for views whose gradients are summed)."""
+        abi.gs_batch_render_backward(self._structs(), [g.struct() for g in self.gaussians], self._bgs(bg),
+                                     [d.data_ptr() for d in dL_drgb], [o[1].data_ptr() for o in outs],
+                                     [o[2].data_ptr() for o in outs], [_gradients_struct(g) for g in grads],
+                                     accumulate, _stream())
+
+    def _bgs(self, bg):
+        bg = list(bg)
+        if len(bg) == 3 and not hasattr(bg[0], "__len__"):
+            return [tuple(float(x) for x in bg)] * len(self.frames)
+        return [tuple(float(x) for x in b) for b in bg]
+
+
 def render(g: GaussianTensors, camera, bg=(0.0, 0.0, 0.0), cfg=None, frame: Frame | None = None):
     """Forward render.  Returns (image [3,H,W], T_final [H,W], last [H,W] int32, frame)."""
     g = g.prepared()

@@ -152,3 +152,46 @@ def test_static_depth_order_validates_before_touching_the_device(lib):
     assert L.gs_depth_order_static(10, None, 256, 256, 256, None) == _abi.GS_ERR_INVALID_ARG
     src = open(os.path.join(ROOT, "include", "gs.h")).read()
     assert f"#define GS_STATIC_ORDER_MAX_N {nmax}" in src
+
+
+def _fake_frames(count, width=64, height=64):
+    from paper_2308_04079_gb300 import _abi
+    frames = (_abi.gs_frame * count)()
+    for f in frames:
+        f.n = 10
+        f.cam.width, f.cam.height, f.cam.fx, f.cam.fy, f.cam.near_z = width, height, 50.0, 50.0, 0.2
+        f.cfg = _abi.gs_default_config()
+        f.capacity = 100
+        f.ws = 256
+        f.ws_bytes = _abi.gs_workspace_size(10, width, height, 100, f.cfg)
+    return frames
+
+
+def test_batch_calls_validate_before_touching_the_device(lib):
+    """Batches reject a view count outside [1, 32], frames with different tile shapes and
+    gradient outputs shared between groups of frames, synchronously."""
+    import ctypes as C
+    from paper_2308_04079_gb300 import _abi
+    L = _abi.load()
+    frames = _fake_frames(2)
+    assert L.gs_batch_bin_sort(frames, 0, None) == _abi.GS_ERR_INVALID_ARG
+    big = _fake_frames(_abi.GS_MAX_BATCH + 1)
+    assert L.gs_batch_bin_sort(big, _abi.GS_MAX_BATCH + 1, None) == _abi.GS_ERR_INVALID_ARG
+    frames[1].cfg.tile_w, frames[1].cfg.tile_h = 8, 8
+    frames[1].ws_bytes = _abi.gs_workspace_size(10, 64, 64, 100, frames[1].cfg)
+    assert L.gs_batch_bin_sort(frames, 2, None) == _abi.GS_ERR_INVALID_ARG
+    frames = _fake_frames(2)
+    gs = (_abi.gs_gaussians * 2)()
+    gr = (_abi.gs_gradients * 2)()
+    for k in range(2):
+        g = gs[k]
+        g.n, g.sh_degree, g.sh_stride = 10, 3, 16
+        base = 4096 * (k + 1)                      # two different scenes
+        g.means, g.scales, g.quats, g.opacities, g.sh = base, base + 256, base + 512, base + 768, base + 1024
+        r = gr[k]
+        r.means, r.scales, r.quats, r.opacities, r.sh = 65536, 65536 + 256, 65536 + 512, 65536 + 768, 65536 + 1024
+    bg = (C.c_float * 6)(*([0.0] * 6))
+    ptrs = (C.c_void_p * 2)(256, 256)
+    # different Gaussians writing the same gradient buffers
+    code = L.gs_batch_render_backward(frames, gs, 2, bg, ptrs, ptrs, ptrs, gr, 0, None)
+    assert code == _abi.GS_ERR_INVALID_ARG

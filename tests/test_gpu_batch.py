@@ -1,0 +1,173 @@
+"""Batched stages (gs_batch_*): several frames -- views of uneven size of one scene, or views
+of several scenes -- in one launch per kernel.  Every frame's binning, image, transmittance and
+last contributor equal the single-frame calls bit for bit; each scene's gradients equal the
+per-view calls accumulated over its views (summation order differs: fp32 tolerance); and a
+batched scene is checked against the FP64 oracle on sampled tiles of every view."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+from gpu_util import compare_grads, compare_images, last_contributor_ids
+
+pytestmark = pytest.mark.gpu
+
+GRAD_KEYS = ("means", "scales", "quats", "opacities", "sh", "mean2d")
+
+
+def _single(gt, cams, bg, dimgs, cfg):
+    """Per-view loop through the single-frame API, gradients accumulated over the views."""
+    import torch
+    from paper_2308_04079_gb300 import Frame
+    outs, frames = [], []
+    grads = None
+    for v, cam in enumerate(cams):
+        fr = Frame(gt.n, cam, cfg)
+        fr.ensure_binned(gt)
+        o = fr.outputs()
+        fr.render_forward(bg, *o)
+        if grads is None:
+            grads = fr.new_grads(gt)
+        fr.render_backward(gt, bg, dimgs[v], o[1], o[2], grads, accumulate=v > 0)
+        outs.append(o)
+        frames.append(fr)
+    torch.cuda.synchronize()
+    return frames, outs, grads
+
+
+def _batched(groups, bg, cfg):
+    """groups: list of (GaussianTensors, cams, dimgs) -> per-view frames/outs, per-group grads."""
+    import torch
+    from paper_2308_04079_gb300 import Frame, FrameBatch
+    frames, gauss, dl, gr, grads = [], [], [], [], []
+    for gt, cams, dimgs in groups:
+        gd = None
+        for cam, d in zip(cams, dimgs):
+            fr = Frame(gt.n, cam, cfg)
+            frames.append(fr)
+            gauss.append(gt)
+            dl.append(d)
+            if gd is None:
+                gd = fr.new_grads(gt)
+                grads.append(gd)
+            gr.append(gd)
+    b = FrameBatch(frames, gauss)
+    b.ensure_binned()
+    outs = b.outputs()
+    b.render_forward(bg, outs)
+    b.render_backward(bg, dl, outs, gr)
+    torch.cuda.synchronize()
+    return frames, outs, grads
+
+
+def _views(seed, n, views):
+    import torch
+    from paper_2308_04079_gb300 import GaussianTensors
+    g, cams, _, dimgs = S.config4(k=seed, n=n, views=views)
+    gt = GaussianTensors.from_numpy(g).prepared()
+    return g, gt, cams, [torch.from_numpy(d).cuda() for d in dimgs]
+
+
+def _assert_close_grads(a, b, what):
+    """Batched vs per-view gradients: the screen-space accumulators are float atomics whose
+    order differs run to run, so sums with cancellation differ in their last bits; per tensor
+    relative L2 <= 1e-5, per element <= 1e-2 max(|g|, rms(g))."""
+    a = a.astype(np.float64).reshape(a.shape[0], -1)
+    b = b.astype(np.float64).reshape(b.shape[0], -1)
+    na = np.linalg.norm(a)
+    assert np.linalg.norm(a - b) <= 1e-5 * max(na, 1e-30), what
+    rms = np.sqrt(np.mean(a ** 2)) if a.size else 0.0
+    assert np.all(np.abs(a - b) <= 1e-2 * np.maximum(np.abs(a), rms) + 1e-30), what
+
+
+def _assert_same_frame(fa, oa, fb, ob):
+    import torch
+    _, sa = fa.status()
+    _, sb = fb.status()
+    assert sa.num_instances == sb.num_instances and sa.num_visible == sb.num_visible
+    K = int(sa.num_instances)
+    for name, dt, cnt in (("vals_sorted", torch.int32, K), ("ranges", torch.int32, 2 * fa.tiles)):
+        assert torch.equal(fa.view(name, dt, cnt), fb.view(name, dt, cnt)), name
+    for x, y in zip(oa, ob):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("mode", ["two_phase", "key64"])
+def test_batched_views_equal_per_view_calls(mode):
+    import torch
+    from paper_2308_04079_gb300 import make_config
+    cfg = make_config(sort_mode=mode)
+    _, gt, cams, dimgs = _views(7, 150_000, 6)
+    bg = (0.1, 0.2, 0.3)
+    fs, os_, gs = _single(gt, cams, bg, dimgs, cfg)
+    fb, ob, gb = _batched([(gt, cams, dimgs)], bg, cfg)
+    for v in range(len(cams)):
+        _assert_same_frame(fs[v], os_[v], fb[v], ob[v])
+    for k in GRAD_KEYS:
+        _assert_close_grads(gs[k].cpu().numpy(), gb[0][k].cpu().numpy(), k)
+
+
+def test_batched_scenes_keep_their_gradients_apart():
+    """Three scenes of different sizes, two or three views each, in one batch."""
+    import torch
+    from paper_2308_04079_gb300 import make_config
+    cfg = make_config()
+    bg = (0.0, 0.0, 0.0)
+    groups, singles = [], []
+    for s, (n, views) in enumerate(((20_000, 2), (90_000, 3), (45_000, 2))):
+        _, gt, cams, dimgs = _views(20 + s, n, views)
+        groups.append((gt, cams, dimgs))
+        singles.append(_single(gt, cams, bg, dimgs, cfg))
+    fb, ob, gb = _batched(groups, bg, cfg)
+    v = 0
+    for s, (fs, os_, gs) in enumerate(singles):
+        for k in range(len(fs)):
+            _assert_same_frame(fs[k], os_[k], fb[v], ob[v])
+            v += 1
+        for key in GRAD_KEYS:
+            _assert_close_grads(gs[key].cpu().numpy(), gb[s][key].cpu().numpy(), f"scene {s} {key}")
+
+
+def test_batched_views_match_the_oracle_on_sampled_tiles():
+    """Config-4 form (one scene, uneven views) at 300k Gaussians: every view's image on 12
+    sampled tiles, and the gradient summed over all views with dL/dpixel kept on those tiles,
+    against the FP64 oracle."""
+    import torch
+    from paper_2308_04079_gb300 import make_config
+    g, gt, cams, _ = _views(3, 300_000, 5)
+    rng = np.random.default_rng(99)
+    bg = (0.0, 0.0, 0.0)
+    masks, dimgs, pixsel = [], [], []
+    for v, cam in enumerate(cams):
+        TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
+        m = np.zeros(TX * TY, np.uint8)
+        m[rng.choice(TX * TY, 12, replace=False)] = 1
+        pix = np.repeat(np.repeat(m.reshape(TY, TX), 16, 0), 16, 1)[:cam.height, :cam.width].astype(bool)
+        d = np.where(pix[None], S.upstream_grad(700 + v, cam.height, cam.width), 0.0).astype(np.float32)
+        masks.append(m)
+        dimgs.append(d)
+        pixsel.append(pix)
+    fb, ob, gb = _batched([(gt, cams, [torch.from_numpy(d).cuda() for d in dimgs])], bg, make_config())
+    total = None
+    for v, cam in enumerate(cams):
+        orc = oracle.render_forward(g, cam, bg, tile_mask=masks[v])
+        last = ob[v][2].cpu().numpy()
+        run = dict(img=ob[v][0].cpu().numpy().astype(np.float64), T=ob[v][1].cpu().numpy().astype(np.float64),
+                   last_id=last_contributor_ids(fb[v], last))
+        pix = pixsel[v]
+        compare_images(dict(img=run["img"][:, pix], T=run["T"][pix], last_id=run["last_id"][pix]),
+                       dict(img=orc["img"][:, pix], T=orc["T"][pix], last_id=orc["last_id"][pix],
+                            pix_amb=orc["pix_amb"][pix]), max_amb_frac=0.05)
+        ob_v = oracle.render_backward(g, cam, dimgs[v], bg, tile_mask=masks[v])
+        if total is None:
+            total = {k: ob_v[k].copy() for k in ("means", "scales", "quats", "opacities", "sh")}
+            amb = ob_v["gauss_amb"].copy()
+        else:
+            for k in total:
+                total[k] += ob_v[k]
+            amb |= ob_v["gauss_amb"]
+    touched = np.abs(total["opacities"]) > 0
+    keep = touched & (amb == 0)
+    assert keep.sum() > 100 and (touched & ~keep).sum() <= 0.05 * touched.sum()
+    got = {k: gb[0][k].cpu().numpy().astype(np.float64) for k in ("means", "scales", "quats", "opacities", "sh")}
+    compare_grads(got, total, keep)
