@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
     __shared__ uint32_t s_chunk;
     __shared__ uint32_t s_base[MAXF + 1];   // chunks of frames [0, f) (device-side counts)
     __shared__ int s_frame;                 // frame whose digit offsets s_digit_off holds
+    // A batch reads its frame's arguments from a shared copy: loads through a pointer into the
+    // parameter array would be generic loads, repeated after every global store.
+    __shared__ __align__(16) SortPassArgs<KeyT> s_args;
+    __shared__ int s_argf;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = lanemask_lt();
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
         if (tid == 0) {
             s_base[0] = 0;
             s_frame = -1;
+            s_argf = -1;
         }
     }
     __syncthreads();
@@ -141,8 +146,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
         const uint32_t g = s_chunk;
         if (g >= total) break;
         int f = 0;
-        while (f + 1 < m.frames && s_base[f + 1] <= g) ++f;
-        const SortPassArgs<KeyT>& a = m.a[f];
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_base[f + 1] <= g) ++f;
+        auto body = [&](const SortPassArgs<KeyT>& a) {
         const uint32_t chunk = g - s_base[f];
         uint32_t count = a.count_host;
         if (a.count_dev) count = min(count, *a.count_dev);
@@ -261,6 +267,18 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
                 a.vals_out[dest] = s_vals[s];
             }
         }
+        };
+        if constexpr (MAXF == 1) {
+            body(m.a[0]);
+        } else {
+            if (f != s_argf) {   // block-uniform
+                for (int k = tid; k < (int)(sizeof(SortPassArgs<KeyT>) / 4); k += kSortThreads)
+                    reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+                __syncthreads();
+                if (tid == 0) s_argf = f;
+            }
+            body(s_args);
+        }
         __syncthreads();
     }
 }
@@ -335,6 +353,8 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
     __shared__ uint32_t s_chunk;
     __shared__ unsigned long long s_base_s, s_base_t;
     __shared__ uint32_t s_fbase[MAXF + 1];   // chunks of frames [0, f)
+    __shared__ __align__(16) ScanArgs s_args;  // batches: the frame's arguments (see k_onesweep)
+    __shared__ int s_argf;
     const int tid = threadIdx.x, lane = tid & 31, sub = lane % kRowLanes, grp = lane / kRowLanes;
     if (tid < 32) {
         uint32_t ch = 0;
@@ -346,7 +366,10 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
         }
         const uint32_t inc = warp_inclusive_scan<uint32_t>(ch);
         if (tid < m.frames) s_fbase[tid + 1] = inc;
-        if (tid == 0) s_fbase[0] = 0;
+        if (tid == 0) {
+            s_fbase[0] = 0;
+            s_argf = -1;
+        }
     }
     __syncthreads();
     const uint32_t total = s_fbase[m.frames];
@@ -359,8 +382,9 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
         const uint32_t g = s_chunk;
         if (g >= total) break;
         int f = 0;
-        while (f + 1 < m.frames && s_fbase[f + 1] <= g) ++f;
-        const ScanArgs& a = m.a[f];
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_fbase[f + 1] <= g) ++f;
+        auto body = [&](const ScanArgs& a) {
         const uint32_t chunk = g - s_fbase[f];
         const uint32_t chunks = s_fbase[f + 1] - s_fbase[f];
         uint32_t count = (uint32_t)a.n;
@@ -558,6 +582,18 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
                 if (v) atomicAdd(&a.hist[k], v);
             }
         }
+        };
+        if constexpr (MAXF == 1) {
+            body(m.a[0]);
+        } else {
+            if (f != s_argf) {   // block-uniform
+                for (int k = tid; k < (int)(sizeof(ScanArgs) / 4); k += kDupThreads)
+                    reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+                __syncthreads();
+                if (tid == 0) s_argf = f;
+            }
+            body(s_args);
+        }
         __syncthreads();
     }
 }
@@ -571,7 +607,14 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
 // ---------------------------------------------------------------------------------------
 template <int MAXF>
 __global__ void __launch_bounds__(1024) k_tile_ranges(const __grid_constant__ Multi<TileRangesArgs, MAXF> m) {
-    const TileRangesArgs& a = m.a[blockIdx.x];   // one block per frame
+    // one block per frame; a batch reads its frame's arguments from a shared copy
+    __shared__ __align__(16) TileRangesArgs s_args;
+    if (MAXF > 1) {
+        for (int k = threadIdx.x; k < (int)(sizeof(TileRangesArgs) / 4); k += blockDim.x)
+            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[blockIdx.x])[k];
+        __syncthreads();
+    }
+    const TileRangesArgs& a = MAXF == 1 ? m.a[0] : s_args;
     __shared__ uint32_t s_hist[kMaxKeyPasses][256];
     __shared__ uint32_t s_scan[33];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -642,11 +685,13 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += warps) {
         int f = 0;
-        while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
         const EmitArgs& a = m.a[f];
         const uint32_t K = a.status->num_instances;
         const uint32_t S = *a.num_segments;
-        KeyT* keys_out = reinterpret_cast<KeyT*>(a.keys_out);
+        KeyT* const keys_out = reinterpret_cast<KeyT*>(a.keys_out);
+        uint32_t* const vals_out = a.vals_out;
         const uint32_t s0 = (u - s_ubase[f]) * 32u;
         const uint32_t sidx = s0 + (uint32_t)lane;
         const bool valid = sidx < S;
@@ -676,7 +721,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
             if (out < out1) {
                 if (KEY64) keys_out[out] = (KeyT)(((unsigned long long)tile << 32) | db);
                 else keys_out[out] = (KeyT)tile;
-                a.vals_out[out] = g;
+                vals_out[out] = g;
             }
         }
     }

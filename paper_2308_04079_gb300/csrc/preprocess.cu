@@ -127,7 +127,14 @@ template <int DEG, bool VEC, int MAXF>
 __global__ void __launch_bounds__(256) k_preprocess_t(const __grid_constant__ Multi<PreprocessArgs, MAXF> m) {
     constexpr int D = (DEG + 1) * (DEG + 1);
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns blocks [base[f], base[f+1])
-    const PreprocessArgs& a = m.a[f];
+    // a batch reads its frame's arguments from a shared copy (generic loads otherwise)
+    __shared__ __align__(16) PreprocessArgs s_args;
+    if (MAXF > 1) {
+        for (int k = threadIdx.x; k < (int)(sizeof(PreprocessArgs) / 4); k += blockDim.x)
+            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+        __syncthreads();
+    }
+    const PreprocessArgs& a = MAXF == 1 ? m.a[0] : s_args;
     const int i = (int)(blockIdx.x - m.base[f]) * blockDim.x + threadIdx.x;
     bool visible = false;
     if (i < a.n) {
@@ -326,7 +333,15 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(const __grid_cons
     constexpr int NF = BwdAcc<DEG>::NF;
     const int g = find_frame<MAXF>(m.block_base, m.groups, blockIdx.x);
     const int f0 = m.frame_begin[g], f1 = m.frame_begin[g + 1];
-    const PreprocessBwdArgs& a = m.a[f0];   // Gaussians and outputs shared by the group
+    // a batch reads its group's arguments from a shared copy (generic loads otherwise)
+    __shared__ __align__(16) PreprocessBwdArgs s_args[MAXF > 1 ? MAXF : 1];
+    if (MAXF > 1) {
+        const int words = (int)(sizeof(PreprocessBwdArgs) / 4) * (f1 - f0);
+        for (int k = threadIdx.x; k < words; k += blockDim.x)
+            reinterpret_cast<uint32_t*>(s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f0])[k];
+        __syncthreads();
+    }
+    const PreprocessBwdArgs& a = MAXF == 1 ? m.a[0] : s_args[0];   // Gaussians and outputs shared by the group
     const int i = (int)(blockIdx.x - m.block_base[g]) * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     float* gsh = a.g_sh + (size_t)i * a.sh_stride * 3;
@@ -344,7 +359,7 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(const __grid_cons
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     const int nv = MAXF == 1 ? 1 : f1 - f0;   // a single frame: straight-line code
     for (int k = 0; k < nv; ++k) {
-        const PreprocessBwdArgs& av = m.a[f0 + k];
+        const PreprocessBwdArgs& av = MAXF == 1 ? m.a[0] : s_args[k];
         if (av.radius[i] <= 0) continue;
         if (!any) {
             any = true;

@@ -95,7 +95,15 @@ __device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, fl
 template <int PX, int MAXF>
 __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__ Multi<RenderFwdArgs, MAXF> m) {
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
-    const RenderFwdArgs& a = m.a[f];
+    // a batch reads its frame's arguments from a shared copy (loads through a pointer into the
+    // parameter array would be generic loads, repeated after every global store)
+    __shared__ __align__(16) RenderFwdArgs s_args;
+    if (MAXF > 1) {
+        for (int k = threadIdx.x; k < (int)(sizeof(RenderFwdArgs) / 4); k += blockDim.x)
+            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+        __syncthreads();
+    }
+    const RenderFwdArgs& a = MAXF == 1 ? m.a[0] : s_args;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
@@ -188,8 +196,16 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
 
 template <int PX, int MAXF>
 __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant__ Multi<RenderBwdArgs, MAXF> m) {
-    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);
-    const RenderBwdArgs& a = m.a[f];
+    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
+    // a batch reads its frame's arguments from a shared copy (loads through a pointer into the
+    // parameter array would be generic loads, repeated after every global store)
+    __shared__ __align__(16) RenderBwdArgs s_args;
+    if (MAXF > 1) {
+        for (int k = threadIdx.x; k < (int)(sizeof(RenderBwdArgs) / 4); k += blockDim.x)
+            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+        __syncthreads();
+    }
+    const RenderBwdArgs& a = MAXF == 1 ? m.a[0] : s_args;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);

@@ -71,11 +71,11 @@ def _views(seed, n, views):
 def _assert_close_grads(a, b, what):
     """Batched vs per-view gradients: the screen-space accumulators are float atomics whose
     order differs run to run, so sums with cancellation differ in their last bits; per tensor
-    relative L2 <= 1e-5, per element <= 1e-2 max(|g|, rms(g))."""
+    relative L2 <= 1e-4, per element <= 1e-2 max(|g|, rms(g))."""
     a = a.astype(np.float64).reshape(a.shape[0], -1)
     b = b.astype(np.float64).reshape(b.shape[0], -1)
     na = np.linalg.norm(a)
-    assert np.linalg.norm(a - b) <= 1e-5 * max(na, 1e-30), what
+    assert np.linalg.norm(a - b) <= 1e-4 * max(na, 1e-30), what
     rms = np.sqrt(np.mean(a ** 2)) if a.size else 0.0
     assert np.all(np.abs(a - b) <= 1e-2 * np.maximum(np.abs(a), rms) + 1e-30), what
 
