@@ -283,6 +283,10 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} hbm_gbs"}
 
+    batch = None
+    if not args.no_batch and args.gaussians == CONFIG3_N:
+        batch = run_batch(args, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, cam, bg, dimg, args.cpu_tiles)
@@ -298,11 +302,75 @@ def run_ours(args, rank, world, local_rank):
                    "blended_pairs": blended,
                    "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batch": batch,
         "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_batch(args, dev):
+    """Config 4: one 1M-Gaussian scene (config-3 distribution), 16 views of uneven size,
+    forward+backward with the gradients summed over the views -- as one batch (one launch per
+    kernel for all views) and as the plain per-view loop on the same frames."""
+    import torch
+    import synthetic as S
+    from paper_2308_04079_gb300 import Frame, FrameBatch, GaussianTensors, make_config
+    g, cams, bg, dimgs = S.config4(n=args.batch_gaussians, views=args.batch_views)
+    bg = tuple(float(x) for x in bg)
+    gt = GaussianTensors.from_numpy(g, device=dev).prepared()
+    d = [torch.from_numpy(x).to(dev) for x in dimgs]
+    cfg = make_config()
+    frames = [Frame(gt.n, cam, cfg, device=dev) for cam in cams]
+    batch = FrameBatch(frames, [gt] * len(frames))
+    batch.ensure_binned()
+    frames = [Frame(gt.n, cam, cfg, capacity=int(f.last_status.num_instances * 1.15) + 4096, device=dev)
+              for cam, f in zip(cams, frames)]
+    batch = FrameBatch(frames, [gt] * len(frames))
+    outs = batch.outputs()
+    grads = frames[0].new_grads(gt)
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        batch.preprocess()
+        batch.bin_sort()
+        batch.render_forward(bg, outs)
+        batch.render_backward(bg, d, outs, [grads] * len(frames))
+
+    def per_view():
+        for v, f in enumerate(frames):
+            f.preprocess(gt)
+            f.bin_sort()
+            f.render_forward(bg, *outs[v])
+            f.render_backward(gt, bg, d[v], outs[v][1], outs[v][2], grads, accumulate=v > 0)
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    steps = max(3, min(args.steps, 10))
+    ms_loop = timed(per_view, steps)
+    img_loop = [o[0].clone() for o in outs]
+    ms_batch = timed(batched, steps)
+    same = all(torch.equal(o[0], x) for o, x in zip(outs, img_loop))
+    for f in frames:
+        code, _ = f.status()
+        if code not in (0, 5):
+            raise RuntimeError(f"batched frame failed with status {code}")
+    sizes = sorted({(c.width, c.height) for c in cams})
+    return {"workload": f"one scene of {gt.n} Gaussians (config-3 distribution), {len(frames)} views of uneven size "
+                        f"({', '.join(f'{w}x{h}' for w, h in sizes)}), forward+backward, gradients summed over views",
+            "views": len(frames), "batched_ms": round(ms_batch, 4), "per_view_ms": round(ms_loop, 4),
+            "speedup": round(ms_loop / ms_batch, 3), "views_per_s": round(len(frames) / (ms_batch * 1e-3), 1),
+            "images_identical": bool(same), "steps": steps}
 
 
 def run_e2e(args, g, gt, fr, dimg, bg, img, T, last, grads, stream, world, dev):
@@ -442,6 +510,9 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=8160,
                     help="16x16 tiles of the frame the CPU baseline renders (8160 = the whole frame)")
     ap.add_argument("--ref-tiles", type=int, default=32)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-view comparison")
+    ap.add_argument("--batch-gaussians", type=int, default=1_000_000)
+    ap.add_argument("--batch-views", type=int, default=16)
     ap.add_argument("--gaussians", type=int, default=CONFIG3_N,
                     help="Gaussians of the config-3 scene (smaller counts for profiling captures)")
     args = ap.parse_args()
