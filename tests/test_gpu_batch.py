@@ -171,3 +171,40 @@ def test_batched_views_match_the_oracle_on_sampled_tiles():
     assert keep.sum() > 100 and (touched & ~keep).sum() <= 0.05 * touched.sum()
     got = {k: gb[0][k].cpu().numpy().astype(np.float64) for k in ("means", "scales", "quats", "opacities", "sh")}
     compare_grads(got, total, keep)
+
+
+def test_multiscene_graph_with_autotuned_config_matches_plain_calls():
+    """Config-5 form, reduced: three scenes of 20k-80k Gaussians, two views each, the whole
+    forward+backward step captured in one CUDA graph at the tile shape and batch depth the
+    autotuner picks; every scene's images equal the plain per-view calls at that config and
+    its gradients equal their sum over views; replaying the graph reproduces the images."""
+    import torch
+    from paper_2308_04079_gb300 import GaussianTensors
+    from paper_2308_04079_gb300.batching import Scene, SceneBatch, autotune
+    raw, bg = S.config5(k=9, scenes=3, views=2, n_min=20_000, n_max=80_000)
+    bg = tuple(float(x) for x in bg)
+    scenes = [Scene(GaussianTensors.from_numpy(g).prepared(), cams, [torch.from_numpy(d).cuda() for d in dl])
+              for g, cams, dl in raw]
+    cfg, table = autotune(scenes, bg, cands=[((16, 16), 128), ((16, 8), 64), ((8, 8), 64), ((8, 8), 32)], steps=2)
+    # every tile shape at its largest depth, then the other depths of the best shape
+    assert {t for t, _, _ in table} == {(16, 16), (16, 8), (8, 8)} and all(ms > 0 for _, _, ms in table)
+    best = min(table, key=lambda r: r[2])
+    assert (cfg.tile_w, cfg.tile_h) == best[0] and cfg.batch_depth == best[1]
+    sb = SceneBatch(scenes, bg, cfg)
+    sb.capture()
+    sb.replay()
+    torch.cuda.synchronize()
+    sb.check()
+    first = [o[0].clone() for o in sb.outs]
+    sb.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, o[0]) for a, o in zip(first, sb.outs))
+    v = 0
+    for sc in scenes:
+        fs, os_, gs = _single(sc.gaussians, sc.cameras, bg, sc.dL_dimages, cfg)
+        for k in range(len(fs)):
+            for x, y in zip(os_[k], sb.outs[v]):
+                assert torch.equal(x, y)
+            v += 1
+        for key in GRAD_KEYS:
+            _assert_close_grads(gs[key].cpu().numpy(), sb.scene_grads(sc)[key].cpu().numpy(), key)
