@@ -283,9 +283,10 @@ def run_ours(args, rank, world, local_rank):
                 "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": traffic,
                 "peak_kind": f"{peak_kind} hbm_gbs"}
 
-    batch = None
+    batch = multi = None
     if not args.no_batch and args.gaussians == CONFIG3_N:
         batch = run_batch(args, dev)
+        multi = run_multiscene(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -302,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
                    "blended_pairs": blended,
                    "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batch": batch,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batch": batch, "multi_scene": multi,
         "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
     }
     if rank == 0:
@@ -371,6 +372,56 @@ def run_batch(args, dev):
             "views": len(frames), "batched_ms": round(ms_batch, 4), "per_view_ms": round(ms_loop, 4),
             "speedup": round(ms_loop / ms_batch, 3), "views_per_s": round(len(frames) / (ms_batch * 1e-3), 1),
             "images_identical": bool(same), "steps": steps}
+
+
+def run_multiscene(args, dev):
+    """Config 5: 8 independent scenes (log-uniform 50k-2M Gaussians, SH degree 3), 4 views each
+    at mixed resolutions, forward+backward of all 32 frames captured in one CUDA graph at the
+    autotuned tile shape and batch depth; against the plain per-view loop at the same config."""
+    import torch
+    import synthetic as S
+    from paper_2308_04079_gb300 import GaussianTensors
+    from paper_2308_04079_gb300.batching import Scene, SceneBatch, autotune
+    raw, bg = S.config5()
+    bg = tuple(float(x) for x in bg)
+    scenes = [Scene(GaussianTensors.from_numpy(g, device=dev).prepared(), cams,
+                    [torch.from_numpy(d).to(dev) for d in dl]) for g, cams, dl in raw]
+    cfg, table = autotune(scenes, bg, steps=3)
+    sb = SceneBatch(scenes, bg, cfg)
+    sb.capture()
+    steps = max(3, min(args.steps, 10))
+    ms_graph = sb.time_replay(steps)
+    sb.check()
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for f, o, d, gr, g in zip(sb.frames, sb.outs, sb.dl, sb.view_grads, sb.batch.gaussians):
+            f.preprocess(g)
+            f.bin_sort()
+            f.render_forward(sb.bg, *o)
+            f.render_backward(g, sb.bg, d, o[1], o[2], gr, accumulate=id(gr) in plain.done)
+            plain.done.add(id(gr))
+
+    def run_plain():
+        plain.done = set()
+        plain()
+
+    for _ in range(3):
+        run_plain()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        run_plain()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = a.elapsed_time(b) / steps
+    return {"workload": f"{len(scenes)} scenes of {', '.join(str(s.gaussians.n) for s in scenes)} Gaussians, "
+                        f"{len(sb.frames)} frames at mixed resolutions, forward+backward, one CUDA graph",
+            "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch_depth": int(cfg.batch_depth),
+            "autotune": [{"tile": f"{t[0]}x{t[1]}", "batch_depth": d, "ms": round(ms, 4)} for t, d, ms in table],
+            "graph_ms": round(ms_graph, 4), "plain_ms": round(ms_plain, 4), "speedup": round(ms_plain / ms_graph, 3),
+            "frames_per_s": round(len(sb.frames) / (ms_graph * 1e-3), 1), "steps": steps}
 
 
 def run_e2e(args, g, gt, fr, dimg, bg, img, T, last, grads, stream, world, dev):
@@ -510,7 +561,8 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=8160,
                     help="16x16 tiles of the frame the CPU baseline renders (8160 = the whole frame)")
     ap.add_argument("--ref-tiles", type=int, default=32)
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-view comparison")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched multi-view and multi-scene comparisons")
     ap.add_argument("--batch-gaussians", type=int, default=1_000_000)
     ap.add_argument("--batch-views", type=int, default=16)
     ap.add_argument("--gaussians", type=int, default=CONFIG3_N,
