@@ -126,9 +126,9 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 def launches_per_step(layout) -> int:
     """Kernels one step launches: preprocess; binning = [depth histogram + depth passes] +
-    scan + ranges + emit + sort-prepare + instance passes; forward; backward tiles; backward
-    Gaussians."""
-    binning = 4 + layout.key_passes + ((1 + layout.depth_passes) if layout.depth_passes else 0)
+    count + pair scan + segment write + ranges + emit + sort-prepare + instance passes;
+    forward; backward tiles; backward Gaussians."""
+    binning = 6 + layout.key_passes + ((1 + layout.depth_passes) if layout.depth_passes else 0)
     return 1 + binning + 1 + 2
 
 

@@ -284,20 +284,19 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
 }
 
 // ---------------------------------------------------------------------------------------
-// DuplicateWithKeys, first half.  Per Gaussian (in `order`): the 3-sigma tile rectangle, and in
-// each of its rows the interval of tiles the splat can reach (reach_row).  A chained scan with
-// look-back gives each Gaussian its first segment (non-empty row) and first instance; the
-// Gaussian then writes one record per segment (output offset, first tile id, length, Gaussian
-// id) and adds +1 / -1 at the ends of every interval to a per-row difference grid whose prefix
-// sums are the instances of every tile (k_tile_ranges).  In KEY64 mode the depth digits of the
-// four low key passes are constant per Gaussian: their histograms are weighted by its tile count.
+// DuplicateWithKeys.  Per Gaussian (in `order`): the 3-sigma tile rectangle, and in each of its
+// rows the interval of tiles the splat can reach (reach_row).  Pass 1 counts every entry's
+// non-empty rows (segments) and tiles, pass 2 scans those pairs, pass 3 writes one record per
+// segment (first instance, first tile id, Gaussian id), pass 4 (k_emit) expands the records
+// into keys and values.  In KEY64 mode the depth digits of the four low key passes are constant
+// per Gaussian: their histograms are weighted by its tile count.
 // ---------------------------------------------------------------------------------------
 // Look-back words carry (segments, instances) as two 31-bit fields, each saturated at 2^30
 // (above any capacity), so sums over many chunks cannot carry from one field into the other.
 constexpr unsigned long long kPairSat = 1ull << 30;
 constexpr unsigned long long kField = 0x7FFFFFFFull;
 constexpr int kLocalShift = 40;   // block-local packing: segments << 40 | instances (no overflow
-                                  // for 1024 Gaussians of at most 2^24 tiles and 2^13 rows each)
+                                  // for 2048 entries of at most 2^24 tiles and 2^12 rows each)
 
 __device__ __forceinline__ unsigned long long pair_word(unsigned long long segs, unsigned long long tiles) {
     return (min(segs, kPairSat) << 31) | min(tiles, kPairSat);
@@ -345,151 +344,209 @@ __device__ __forceinline__ RowJob row_job(const Reach& e, float u, float v, uint
     return j;
 }
 
+// Per-frame split of entry units (kDupThreads entries each) from device-side entry counts,
+// computed by warp 0 into s_ubase; returns the total number of units.
+template <int MAXF>
+__device__ __forceinline__ uint32_t unit_split(const Multi<ScanArgs, MAXF>& m, uint32_t* s_ubase) {
+    if (threadIdx.x < 32) {
+        uint32_t units = 0;
+        if ((int)threadIdx.x < m.frames) {
+            const ScanArgs& af = m.a[threadIdx.x];
+            uint32_t cnt = (uint32_t)af.n;
+            if (af.count_dev) cnt = min(cnt, *af.count_dev);
+            units = (cnt + kDupThreads - 1) / kDupThreads;
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
+        if ((int)threadIdx.x < m.frames) s_ubase[threadIdx.x + 1] = inc;
+        if (threadIdx.x == 0) s_ubase[0] = 0;
+    }
+    __syncthreads();
+    return s_ubase[m.frames];
+}
+
+// The splat of entry j of the (depth-ordered) list: Gaussian id, rectangle and reach state.
+struct EntrySplat {
+    uint32_t gid;
+    float4 mean;
+    uint32_t rx, ry;   // rectangle columns / rows packed lo | hi << 16 (rows 0: none)
+    Reach e;
+};
+
+__device__ __forceinline__ EntrySplat load_entry(const ScanArgs& a, uint32_t j, uint32_t count) {
+    EntrySplat sp;
+    uint32_t gid = j < count ? (a.order ? a.order[j] : j) : 0u;
+    if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
+    sp.gid = gid;
+    const int rad = j < count ? a.radius[gid] : 0;
+    sp.mean = a.xy[gid];
+    sp.rx = sp.ry = 0;
+    int x0, x1, y0, y1;
+    if (rad > 0 && tile_rect(sp.mean, rad, a.cam, x0, x1, y0, y1)) {
+        sp.rx = (uint32_t)x0 | ((uint32_t)x1 << 16);
+        sp.ry = (uint32_t)y0 | ((uint32_t)y1 << 16);
+    }
+    sp.e = reach_setup(a.conic[gid], a.tau[gid]);
+    return sp;
+}
+
+// DuplicateWithKeys, pass 1: per entry, the number of non-empty tile rows (segments) and of
+// reachable tiles, packed (segments << 32) | tiles into pairs[j].  KEY64: histograms of the
+// four depth digits, weighted by the tile counts.
 template <bool KEY64, int MAXF>
-__global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
-    constexpr int PER = kDupChunk / kDupThreads;
+__global__ void __launch_bounds__(kDupThreads) k_count_tiles(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
+    constexpr int ROUNDS = 32 / kGroups;
     __shared__ uint32_t s_hist[KEY64 ? 4 : 1][256];
+    __shared__ uint32_t s_ubase[MAXF + 1];
+    __shared__ __align__(16) ScanArgs s_args;   // batches: the frame's arguments (see k_onesweep)
+    __shared__ int s_argf;
+    const int tid = threadIdx.x, lane = tid & 31, sub = lane % kRowLanes, grp = lane / kRowLanes;
+    if (KEY64)
+        for (int k = tid; k < 4 * 256; k += kDupThreads) (&s_hist[0][0])[k] = 0;
+    if (tid == 0) s_argf = -1;
+    const uint32_t total = unit_split(m, s_ubase);
+    int hist_f = -1;   // frame whose depth histogram s_hist accumulates (KEY64)
+    auto flush = [&](int hf) {
+        __syncthreads();
+        const ScanArgs& ah = m.a[hf];
+        for (int k = tid; k < 4 * 256; k += kDupThreads) {
+            const uint32_t v = (&s_hist[0][0])[k];
+            if (v) atomicAdd(&ah.hist[k], v);
+            (&s_hist[0][0])[k] = 0;
+        }
+        __syncthreads();
+    };
+    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
+        int f = 0;
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        if (KEY64 && f != hist_f) {
+            if (hist_f >= 0) flush(hist_f);
+            hist_f = f;
+        }
+        auto body = [&](const ScanArgs& a) {
+            uint32_t count = (uint32_t)a.n;
+            if (a.count_dev) count = min(count, *a.count_dev);
+            const uint32_t j = (u - s_ubase[f]) * kDupThreads + tid;
+            const EntrySplat sp = load_entry(a, j, count);
+            const int tw_log2 = a.cam.tile_w == 16 ? 4 : 3;
+            uint32_t nseg = 0, ntile = 0;
+            for (int r = 0; r < ROUNDS; ++r) {
+                const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, r * kGroups + grp);
+                uint32_t sg = 0, t = 0;
+                for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
+                    int txa, txb;
+                    if (base + sub < jb.rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, jb.y0 + base + sub, tw_log2,
+                                                         a.cam.tile_h, jb.x0, jb.x1, txa, txb)) {
+                        sg += 1;
+                        t += (uint32_t)(txb - txa);
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < kRowLanes; o <<= 1) {
+                    sg += __shfl_xor_sync(0xffffffffu, sg, o);
+                    t += __shfl_xor_sync(0xffffffffu, t, o);
+                }
+                // owner lane r * kGroups + q takes the totals of group q
+                const int from = (lane % kGroups) * kRowLanes;
+                const uint32_t ts = __shfl_sync(0xffffffffu, sg, from), tt = __shfl_sync(0xffffffffu, t, from);
+                if (lane / kGroups == r) {
+                    nseg = ts;
+                    ntile = tt;
+                }
+            }
+            if (j < count) a.pairs[j] = ((unsigned long long)nseg << 32) | ntile;
+            if (KEY64 && ntile) {
+                const uint32_t db = __float_as_uint(a.depth[sp.gid]);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], ntile);
+            }
+        };
+        if constexpr (MAXF == 1) {
+            body(m.a[0]);
+        } else {
+            if (f != s_argf) {   // block-uniform
+                __syncthreads();
+                for (int k = tid; k < (int)(sizeof(ScanArgs) / 4); k += kDupThreads)
+                    reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+                __syncthreads();
+                if (tid == 0) s_argf = f;
+                __syncthreads();
+            }
+            body(s_args);
+        }
+    }
+    if (KEY64 && hist_f >= 0) flush(hist_f);
+}
+
+// DuplicateWithKeys, pass 2: exclusive scan of the (segments, tiles) pairs in list order,
+// chunks of kPairChunk entries chained by decoupled look-back; pairs[j] becomes
+// (first segment << 32) | first instance (both clamped to the capacity).  The last chunk
+// records the totals, flags a capacity overflow and closes the last segment.
+template <int MAXF>
+__global__ void __launch_bounds__(kDupThreads) k_scan_pairs(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
+    constexpr int PER = kPairChunk / kDupThreads;
     __shared__ unsigned long long s_scan[33];
     __shared__ uint32_t s_chunk;
     __shared__ unsigned long long s_base_s, s_base_t;
     __shared__ uint32_t s_fbase[MAXF + 1];   // chunks of frames [0, f)
-    __shared__ __align__(16) ScanArgs s_args;  // batches: the frame's arguments (see k_onesweep)
-    __shared__ int s_argf;
-    const int tid = threadIdx.x, lane = tid & 31, sub = lane % kRowLanes, grp = lane / kRowLanes;
+    const int tid = threadIdx.x;
     if (tid < 32) {
         uint32_t ch = 0;
         if (tid < m.frames) {
             const ScanArgs& af = m.a[tid];
             uint32_t cnt = (uint32_t)af.n;
             if (af.count_dev) cnt = min(cnt, *af.count_dev);
-            ch = (cnt + kDupChunk - 1) / kDupChunk;
+            ch = (cnt + kPairChunk - 1) / kPairChunk;
         }
         const uint32_t inc = warp_inclusive_scan<uint32_t>(ch);
         if (tid < m.frames) s_fbase[tid + 1] = inc;
-        if (tid == 0) {
-            s_fbase[0] = 0;
-            s_argf = -1;
-        }
+        if (tid == 0) s_fbase[0] = 0;
     }
     __syncthreads();
     const uint32_t total = s_fbase[m.frames];
-
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(m.a[0].chunk_counter, 1u);
-        if (KEY64)
-            for (int k = tid; k < 4 * 256; k += kDupThreads) (&s_hist[0][0])[k] = 0;
         __syncthreads();
         const uint32_t g = s_chunk;
         if (g >= total) break;
         int f = 0;
         if (MAXF > 1)
             while (f + 1 < m.frames && s_fbase[f + 1] <= g) ++f;
-        auto body = [&](const ScanArgs& a) {
+        const ScanArgs& a = m.a[f];   // a few scalar loads per chunk
+        unsigned long long* const pairs = a.pairs;
+        unsigned long long* const lookback = a.lookback;
         const uint32_t chunk = g - s_fbase[f];
         const uint32_t chunks = s_fbase[f + 1] - s_fbase[f];
         uint32_t count = (uint32_t)a.n;
         if (a.count_dev) count = min(count, *a.count_dev);
-        const CamK& c = a.cam;
-        const int gw = c.tiles_x + 1;
-        const int tw_log2 = c.tile_w == 16 ? 4 : 3;
-        const int th = c.tile_h;
         const unsigned long long cap = a.capacity;
-        // Gaussian j = chunk * 1024 + k * 256 + tid: consecutive lanes take consecutive entries
-        uint32_t gids[PER];
-        int rad[PER];
-        float4 mean[PER], L[PER];
-        float tau[PER];
+        // this thread's PER consecutive entries
+        const uint32_t j0 = chunk * kPairChunk + tid * PER;
+        unsigned long long v[PER];
+        unsigned long long run = 0;   // block-local packing: segments << kLocalShift | tiles
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const uint32_t j = chunk * kDupChunk + k * kDupThreads + tid;
-            uint32_t gid = j < count ? (a.order ? a.order[j] : j) : 0u;
-            if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
-            gids[k] = gid;
+            const unsigned long long p = j0 + k < count ? pairs[j0 + k] : 0ull;
+            v[k] = ((p >> 32) << kLocalShift) | (p & 0xFFFFFFFFull);
+            run += v[k];
         }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const uint32_t j = chunk * kDupChunk + k * kDupThreads + tid;
-            rad[k] = j < count ? a.radius[gids[k]] : 0;
-            mean[k] = a.xy[gids[k]];
-            L[k] = a.conic[gids[k]];
-            tau[k] = a.tau[gids[k]];
-        }
-        uint32_t rx[PER], ry[PER];   // rectangle columns / rows packed lo | hi << 16 (rows 0: none)
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            int x0, x1, y0, y1;
-            const bool vis = rad[k] > 0 && tile_rect(mean[k], rad[k], c, x0, x1, y0, y1);
-            rx[k] = vis ? ((uint32_t)x0 | ((uint32_t)x1 << 16)) : 0u;
-            ry[k] = vis ? ((uint32_t)y0 | ((uint32_t)y1 << 16)) : 0u;
-        }
-        // ---- count the segments and tiles of every splat ----
-        uint32_t nseg[PER], ntile[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const Reach e = reach_setup(L[k], tau[k]);
-            nseg[k] = 0;
-            ntile[k] = 0;
-            for (int r = 0; r < 32 / kGroups; ++r) {
-                const RowJob jb = row_job(e, mean[k].x, mean[k].y, rx[k], ry[k], r * kGroups + grp);
-                uint32_t s = 0, t = 0;
-                for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
-                    int txa, txb;
-                    if (base + sub < jb.rows &&
-                        tile_row(jb.e, a.rect_only, jb.u, jb.v, jb.y0 + base + sub, tw_log2, th, jb.x0, jb.x1, txa, txb)) {
-                        s += 1;
-                        t += (uint32_t)(txb - txa);
-                    }
-                }
-#pragma unroll
-                for (int o = 1; o < kRowLanes; o <<= 1) {
-                    s += __shfl_xor_sync(0xffffffffu, s, o);
-                    t += __shfl_xor_sync(0xffffffffu, t, o);
-                }
-                // owner lane r * kGroups + g takes the totals of group g
-                const int from = (lane % kGroups) * kRowLanes;
-                const uint32_t ts = __shfl_sync(0xffffffffu, s, from), tt = __shfl_sync(0xffffffffu, t, from);
-                if (lane / kGroups == r) {
-                    nseg[k] = ts;
-                    ntile[k] = tt;
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            if (KEY64 && ntile[k]) {
-                const uint32_t db = __float_as_uint(a.depth[gids[k]]);
-#pragma unroll
-                for (int p = 0; p < 4; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], ntile[k]);
-            }
-        }
-        // ---- chunk offsets: block scan (k-major order) + decoupled look-back ----
-        // Thread order inside the chunk is (k, tid); scan each k-slice and chain the slices.
-        unsigned long long excl_k[PER];
-        unsigned long long local_total = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            unsigned long long tot;
-            const unsigned long long ex = block_exclusive_scan<unsigned long long>(
-                ((unsigned long long)nseg[k] << kLocalShift) | ntile[k], s_scan, &tot);
-            excl_k[k] = local_total + ex;
-            local_total += tot;
-        }
+        unsigned long long local_total;
+        const unsigned long long excl = block_exclusive_scan<unsigned long long>(run, s_scan, &local_total);
         const unsigned long long blk_s = local_total >> kLocalShift;
         const unsigned long long blk_t = local_total & ((1ull << kLocalShift) - 1);
-        // Decoupled look-back by warp 0, 32 predecessors per round of loads.
         if (tid < 32) {
-            unsigned long long* my = a.lookback + chunk;
+            unsigned long long* my = lookback + chunk;
             unsigned long long ex_s = 0, ex_t = 0;
             if (tid == 0) st_relaxed64(my, (chunk == 0 ? kScanInc : kScanAgg) | pair_word(blk_s, blk_t));
             if (chunk > 0) {
-                int j = (int)chunk - 1;
+                int jj = (int)chunk - 1;
                 uint32_t spins = 0;
                 while (true) {
-                    const int idx = j - tid;
-                    const unsigned long long v = idx >= 0 ? ld_relaxed64(a.lookback + idx) : kScanInc;
-                    const unsigned long long f = v & kScanFlags;
-                    const uint32_t inc = __ballot_sync(0xffffffffu, f == kScanInc);
-                    const uint32_t zero = __ballot_sync(0xffffffffu, f == 0);
+                    const int idx = jj - tid;
+                    const unsigned long long w = idx >= 0 ? ld_relaxed64(lookback + idx) : kScanInc;
+                    const unsigned long long fl = w & kScanFlags;
+                    const uint32_t inc = __ballot_sync(0xffffffffu, fl == kScanInc);
+                    const uint32_t zero = __ballot_sync(0xffffffffu, fl == 0);
                     const int first_inc = inc ? __ffs(inc) - 1 : 32;
                     const uint32_t upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
                     if (zero & upto) {   // a predecessor in front of the first prefix is not ready
@@ -501,8 +558,8 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
                         continue;
                     }
                     const bool use = tid <= first_inc;
-                    unsigned long long ps = use ? ((v >> 31) & kField) : 0ull;
-                    unsigned long long pt = use ? (v & kField) : 0ull;
+                    unsigned long long ps = use ? ((w >> 31) & kField) : 0ull;
+                    unsigned long long pt = use ? (w & kField) : 0ull;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         ps += __shfl_xor_sync(0xffffffffu, ps, o);
@@ -511,7 +568,7 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
                     ex_s = min(ex_s + ps, kPairSat);
                     ex_t = min(ex_t + pt, kPairSat);
                     if (first_inc < 32) break;
-                    j -= 32;
+                    jj -= 32;
                 }
                 if (tid == 0) st_relaxed64(my, kScanInc | pair_word(ex_s + blk_s, ex_t + blk_t));
             }
@@ -529,26 +586,53 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
             }
         }
         __syncthreads();
-        // ---- write segment records and per-row tile counts ----
-        const uint32_t cap32 = (uint32_t)cap;
+        unsigned long long ss = s_base_s + (excl >> kLocalShift);
+        unsigned long long st = s_base_t + (excl & ((1ull << kLocalShift) - 1));
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const Reach e = reach_setup(L[k], tau[k]);
-            // first segment / instance of this lane's splat, clamped (nothing is written past cap)
-            const uint32_t seg0 = (uint32_t)min(s_base_s + (excl_k[k] >> kLocalShift), cap);
-            const uint32_t off0 = (uint32_t)min(s_base_t + (excl_k[k] & ((1ull << kLocalShift) - 1)), cap);
-            for (int r = 0; r < 32 / kGroups; ++r) {
+            if (j0 + k < count) pairs[j0 + k] = (min(ss, cap) << 32) | min(st, cap);
+            ss += v[k] >> kLocalShift;
+            st += v[k] & ((1ull << kLocalShift) - 1);
+        }
+    }
+}
+
+// DuplicateWithKeys, pass 3: per entry, the segment records (first instance, first tile,
+// Gaussian) of its non-empty rows in row order.
+template <int MAXF>
+__global__ void __launch_bounds__(kDupThreads) k_write_segments(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
+    constexpr int ROUNDS = 32 / kGroups;
+    __shared__ uint32_t s_ubase[MAXF + 1];
+    __shared__ __align__(16) ScanArgs s_args;
+    __shared__ int s_argf;
+    const int tid = threadIdx.x, lane = tid & 31, sub = lane % kRowLanes, grp = lane / kRowLanes;
+    if (tid == 0) s_argf = -1;
+    const uint32_t total = unit_split(m, s_ubase);
+    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
+        int f = 0;
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        auto body = [&](const ScanArgs& a) {
+            uint32_t count = (uint32_t)a.n;
+            if (a.count_dev) count = min(count, *a.count_dev);
+            const uint32_t j = (u - s_ubase[f]) * kDupThreads + tid;
+            const EntrySplat sp = load_entry(a, j, count);
+            const unsigned long long base_pair = j < count ? a.pairs[j] : 0ull;
+            const uint32_t seg0 = (uint32_t)(base_pair >> 32), off0 = (uint32_t)base_pair;
+            const int tw_log2 = a.cam.tile_w == 16 ? 4 : 3;
+            const uint32_t cap32 = (uint32_t)a.capacity;
+            for (int r = 0; r < ROUNDS; ++r) {
                 const int src = r * kGroups + grp;
-                const RowJob jb = row_job(e, mean[k].x, mean[k].y, rx[k], ry[k], src);
+                const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, src);
                 const uint32_t gs0 = __shfl_sync(0xffffffffu, seg0, src);
                 const uint32_t go0 = __shfl_sync(0xffffffffu, off0, src);
-                const uint32_t gid = __shfl_sync(0xffffffffu, gids[k], src);
+                const uint32_t sgid = __shfl_sync(0xffffffffu, sp.gid, src);
                 uint32_t cs = 0, ct = 0;   // segments / tiles of the rows before this pass
                 for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
                     const int ty = jb.y0 + base + sub;
                     int txa = 0, txb = 0;
-                    const bool ok = base + sub < jb.rows &&
-                                    tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2, th, jb.x0, jb.x1, txa, txb);
+                    const bool ok = base + sub < jb.rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2,
+                                                                     a.cam.tile_h, jb.x0, jb.x1, txa, txb);
                     const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
                     uint32_t is = ok ? 1u : 0u, it = len;   // inclusive scans over the group's lanes
 #pragma unroll
@@ -561,112 +645,49 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_tiles(const __grid_constan
                         }
                     }
                     if (ok) {
-                        atomicAdd(&a.diff[ty * gw + txa], 1);
-                        atomicAdd(&a.diff[ty * gw + txb], -1);
                         const uint32_t seg = gs0 + cs + is - 1u;
                         if (seg < cap32) {
                             a.seg_off[seg] = min(go0 + ct + it - len, cap32);
-                            a.seg_tile[seg] = (uint32_t)(ty * c.tiles_x + txa);
-                            a.seg_gid[seg] = gid;
+                            a.seg_tile[seg] = (uint32_t)(ty * a.cam.tiles_x + txa);
+                            a.seg_gid[seg] = sgid;
                         }
                     }
                     cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
                     ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
                 }
             }
-        }
-        if (KEY64) {
-            __syncthreads();
-            for (int k = tid; k < 4 * 256; k += kDupThreads) {
-                const uint32_t v = (&s_hist[0][0])[k];
-                if (v) atomicAdd(&a.hist[k], v);
-            }
-        }
         };
         if constexpr (MAXF == 1) {
             body(m.a[0]);
         } else {
             if (f != s_argf) {   // block-uniform
+                __syncthreads();
                 for (int k = tid; k < (int)(sizeof(ScanArgs) / 4); k += kDupThreads)
                     reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
                 __syncthreads();
                 if (tid == 0) s_argf = f;
+                __syncthreads();
             }
             body(s_args);
         }
-        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------------------
-// IdentifyTileRanges from instance counts (one block): row-wise prefix sums of the difference
-// grid give the instances of every tile; their exclusive scan in tile-id order gives
-// [start, end) (clamped to the capacity; [0, 0) for empty tiles), exactly the ranges of the
-// sorted instance array.  Also adds the digit histograms of the tile-id radix passes (tile ids
-// are the key bits from key_shift on).
-// ---------------------------------------------------------------------------------------
-template <int MAXF>
-__global__ void __launch_bounds__(1024) k_tile_ranges(const __grid_constant__ Multi<TileRangesArgs, MAXF> m) {
-    // one block per frame; a batch reads its frame's arguments from a shared copy
-    __shared__ __align__(16) TileRangesArgs s_args;
-    if (MAXF > 1) {
-        for (int k = threadIdx.x; k < (int)(sizeof(TileRangesArgs) / 4); k += blockDim.x)
-            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[blockIdx.x])[k];
-        __syncthreads();
-    }
-    const TileRangesArgs& a = MAXF == 1 ? m.a[0] : s_args;
-    __shared__ uint32_t s_hist[kMaxKeyPasses][256];
-    __shared__ uint32_t s_scan[33];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int TX = a.tiles_x, TY = a.tiles_y, gw = TX + 1;
-    for (int k = tid; k < kMaxKeyPasses * 256; k += nt) (&s_hist[0][0])[k] = 0;
-    for (int y = tid; y < TY; y += nt) {
-        int run = 0;
-        for (int x = 0; x <= TX; ++x) { run += a.diff[y * gw + x]; a.diff[y * gw + x] = run; }
-    }
-    __syncthreads();
-    const uint32_t T = (uint32_t)(TX * TY);
-    const unsigned long long cap = a.capacity;
-    unsigned long long carry = 0;
-    for (uint32_t base = 0; base < T; base += (uint32_t)nt) {
-        const uint32_t t = base + tid;
-        uint32_t cnt = 0;
-        if (t < T) cnt = (uint32_t)a.diff[(t / TX) * gw + (t % TX)];
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(cnt, s_scan, &tot);
-        if (t < T) {
-            const unsigned long long s0 = carry + ex, s1 = s0 + cnt;
-            a.ranges[2 * t] = cnt ? (uint32_t)min(s0, cap) : 0u;       // empty tiles: [0, 0)
-            a.ranges[2 * t + 1] = cnt ? (uint32_t)min(s1, cap) : 0u;
-            if (cnt) {
-                for (int p = 0; p < a.tile_passes; ++p) {
-                    const int bit = a.key_shift + 8 * p;
-                    const uint32_t d = bit >= 32 ? ((uint32_t)(((unsigned long long)t << 32) >> bit) & 0xFFu)
-                                                 : ((t >> bit) & 0xFFu);
-                    atomicAdd(&s_hist[p][d], cnt);
-                }
-            }
-        }
-        carry += tot;
-    }
-    __syncthreads();
-    for (int k = tid; k < a.tile_passes * 256; k += nt) {
-        const uint32_t v = (&s_hist[0][0])[k];
-        if (v) atomicAdd(&a.hist[k], v);
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// DuplicateWithKeys, second half: a warp takes 32 consecutive segment records, whose outputs
-// form one contiguous run; every lane finds the segment of each output position it writes by a
-// 5-step search over the lanes' segment ends, so keys and values are written coalesced.
-// Nothing is written after a capacity overflow or a timed-out scan.
+// DuplicateWithKeys, pass 4: a warp takes 32 consecutive segment records, whose outputs form
+// one contiguous run; every lane finds the segment of each output position it writes by a
+// 5-step search over the lanes' segment ends, so keys and values are written coalesced.  A
+// block takes 256 records (one frame per block unit); the digit histograms of the tile-id
+// radix passes are accumulated in shared memory on the way.  Nothing is written after a
+// capacity overflow or a timed-out scan.
 // ---------------------------------------------------------------------------------------
 template <bool KEY64, int MAXF>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ Multi<EmitArgs, MAXF> m) {
     using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
-    __shared__ uint32_t s_ubase[MAXF + 1];   // 32-segment units of frames [0, f)
-    const int tid = threadIdx.x, lane = tid & 31;
+    constexpr int UNIT = kEmitThreads;   // segment records per block unit
+    __shared__ uint32_t s_ubase[MAXF + 1];   // block units of frames [0, f)
+    __shared__ uint32_t s_hist[kMaxTilePasses][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 32) {
         uint32_t units = 0;
         if (tid < m.frames) {
@@ -674,25 +695,42 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
             const uint32_t S = *af.num_segments;
             if (blockIdx.x == 0) af.status->num_segments = S;
             // nothing is emitted for a frame after a capacity overflow or a timed-out scan
-            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout))) units = (S + 31u) / 32u;
+            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout))) units = (S + UNIT - 1) / UNIT;
         }
         const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
         if (tid < m.frames) s_ubase[tid + 1] = inc;
         if (tid == 0) s_ubase[0] = 0;
     }
+    for (int k = tid; k < kMaxTilePasses * 256; k += kEmitThreads) (&s_hist[0][0])[k] = 0;
     __syncthreads();
     const uint32_t total = s_ubase[m.frames];
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += warps) {
+    int hist_f = -1;   // frame whose histograms s_hist accumulates
+    auto flush = [&](int hf) {
+        __syncthreads();
+        const EmitArgs& ah = m.a[hf];
+        for (int k = tid; k < ah.tile_passes * 256; k += kEmitThreads) {
+            const uint32_t v = (&s_hist[0][0])[k];
+            if (v) atomicAdd(&ah.hist[k], v);
+        }
+        for (int k = tid; k < kMaxTilePasses * 256; k += kEmitThreads) (&s_hist[0][0])[k] = 0;
+        __syncthreads();
+    };
+    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
         int f = 0;
         if (MAXF > 1)
             while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        if (f != hist_f) {
+            if (hist_f >= 0) flush(hist_f);
+            hist_f = f;
+        }
         const EmitArgs& a = m.a[f];
         const uint32_t K = a.status->num_instances;
         const uint32_t S = *a.num_segments;
+        const int passes = a.tile_passes;
         KeyT* const keys_out = reinterpret_cast<KeyT*>(a.keys_out);
         uint32_t* const vals_out = a.vals_out;
-        const uint32_t s0 = (u - s_ubase[f]) * 32u;
+        const uint32_t s0 = (u - s_ubase[f]) * UNIT + warp * 32u;
+        if (s0 >= S) continue;   // warp-uniform
         const uint32_t sidx = s0 + (uint32_t)lane;
         const bool valid = sidx < S;
         const uint32_t beg = valid ? a.seg_off[sidx] : K;
@@ -705,6 +743,19 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
         const uint32_t out0 = __shfl_sync(0xffffffffu, beg, 0);
         const uint32_t last_lane = min(31u, S - 1u - s0);
         const uint32_t out1 = min(__shfl_sync(0xffffffffu, end, last_lane), K);
+        // digits above the lowest of the tile ids [tile0, tile0 + len): constant over runs of
+        // 256^p ids, so the segment's owner adds one count per run
+        if (valid && end <= K && end > beg) {
+            const uint32_t t_end = tile0 + (end - beg);
+            for (int p = 1; p < passes; ++p) {
+                const int sh = 8 * p;
+                for (uint32_t t = tile0; t < t_end;) {
+                    const uint32_t run_end = min(t_end, ((t >> sh) + 1u) << sh);
+                    atomicAdd(&s_hist[p][(t >> sh) & 0xFFu], run_end - t);
+                    t = run_end;
+                }
+            }
+        }
         for (uint32_t base = out0; base < out1; base += 32u) {   // warp-uniform trip count
             const uint32_t out = base + (uint32_t)lane;
             // segment of position out: the first lane whose segment ends after it
@@ -722,7 +773,53 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
                 if (KEY64) keys_out[out] = (KeyT)(((unsigned long long)tile << 32) | db);
                 else keys_out[out] = (KeyT)tile;
                 vals_out[out] = g;
+                // lowest tile-id digit: consecutive outputs mostly hold consecutive tiles
+                atomicAdd(&s_hist[0][tile & 0xFFu], 1u);
             }
+        }
+    }
+    if (hist_f >= 0) flush(hist_f);
+}
+
+// IdentifyTileRanges (App. C): after the sort, a tile's range starts where its id differs
+// from the previous key's and ends where the next key's differs (ranges were zeroed, so empty
+// tiles keep [0, 0)).
+template <bool KEY64, int MAXF>
+__global__ void __launch_bounds__(256) k_ranges(const __grid_constant__ Multi<RangesArgs, MAXF> m) {
+    using KeyT = typename std::conditional<KEY64, unsigned long long, uint32_t>::type;
+    constexpr uint32_t UNIT = 1024;   // positions per unit
+    __shared__ uint32_t s_ubase[MAXF + 1];
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        uint32_t units = 0;
+        if (tid < m.frames) {
+            const RangesArgs& af = m.a[tid];
+            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout)))
+                units = (uint32_t)((min((unsigned long long)af.status->num_instances, af.capacity) + UNIT - 1) / UNIT);
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
+        if (tid < m.frames) s_ubase[tid + 1] = inc;
+        if (tid == 0) s_ubase[0] = 0;
+    }
+    __syncthreads();
+    const uint32_t total = s_ubase[m.frames];
+    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
+        int f = 0;
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        const RangesArgs& a = m.a[f];
+        const uint32_t K = (uint32_t)min((unsigned long long)a.status->num_instances, a.capacity);
+        const KeyT* const keys = reinterpret_cast<const KeyT*>(a.keys);
+        uint32_t* const ranges = a.ranges;
+        const uint32_t tiles = (uint32_t)a.tiles;
+        for (uint32_t i = (u - s_ubase[f]) * UNIT + tid; i < min(K, (u - s_ubase[f] + 1) * UNIT); i += 256) {
+            const uint32_t t = (uint32_t)(KEY64 ? (keys[i] >> 32) : keys[i]);
+            const uint32_t tp = i > 0 ? (uint32_t)(KEY64 ? (keys[i - 1] >> 32) : keys[i - 1]) : 0xFFFFFFFFu;
+            if (t != tp) {
+                if (t < tiles) ranges[2 * t] = i;
+                if (i > 0 && tp < tiles) ranges[2 * tp + 1] = i;
+            }
+            if (i + 1 == K && t < tiles) ranges[2 * t + 1] = K;
         }
     }
 }
@@ -766,17 +863,23 @@ cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_ch
 template <int MAXF>
 cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s) {
     if (key64)
-        k_scan_tiles<true, MAXF><<<persistent_grid((const void*)k_scan_tiles<true, MAXF>, kDupThreads), kDupThreads, 0,
-                                   s>>>(m);
-    else
-        k_scan_tiles<false, MAXF><<<persistent_grid((const void*)k_scan_tiles<false, MAXF>, kDupThreads), kDupThreads,
+        k_count_tiles<true, MAXF><<<persistent_grid((const void*)k_count_tiles<true, MAXF>, kDupThreads), kDupThreads,
                                     0, s>>>(m);
+    else
+        k_count_tiles<false, MAXF><<<persistent_grid((const void*)k_count_tiles<false, MAXF>, kDupThreads),
+                                     kDupThreads, 0, s>>>(m);
+    k_scan_pairs<MAXF><<<persistent_grid((const void*)k_scan_pairs<MAXF>, kDupThreads), kDupThreads, 0, s>>>(m);
+    k_write_segments<MAXF><<<persistent_grid((const void*)k_write_segments<MAXF>, kDupThreads), kDupThreads, 0, s>>>(
+        m);
     return cudaGetLastError();
 }
 
 template <int MAXF>
-cudaError_t launch_tile_ranges(const Multi<TileRangesArgs, MAXF>& m, cudaStream_t s) {
-    k_tile_ranges<MAXF><<<m.frames, 1024, 0, s>>>(m);
+cudaError_t launch_ranges(const Multi<RangesArgs, MAXF>& m, bool key64, cudaStream_t s) {
+    if (key64)
+        k_ranges<true, MAXF><<<persistent_grid((const void*)k_ranges<true, MAXF>, 256), 256, 0, s>>>(m);
+    else
+        k_ranges<false, MAXF><<<persistent_grid((const void*)k_ranges<false, MAXF>, 256), 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 
@@ -827,7 +930,7 @@ cudaError_t launch_clear(const Multi<ClearArgs, kMaxFrames>& m, cudaStream_t s) 
     template cudaError_t launch_onesweep<unsigned long long, F>(const Multi<SortPassArgs<unsigned long long>, F>&, \
                                                                 int, cudaStream_t);                           \
     template cudaError_t launch_scan_tiles<F>(const Multi<ScanArgs, F>&, bool, cudaStream_t);                  \
-    template cudaError_t launch_tile_ranges<F>(const Multi<TileRangesArgs, F>&, cudaStream_t);                 \
+    template cudaError_t launch_ranges<F>(const Multi<RangesArgs, F>&, bool, cudaStream_t);                    \
     template cudaError_t launch_emit<F>(const Multi<EmitArgs, F>&, bool, cudaStream_t);                        \
     template cudaError_t launch_sort_prepare<F>(const Multi<SortPrepareArgs, F>&, cudaStream_t);
 

@@ -25,10 +25,9 @@ int bits_for(uint32_t v) {
 struct Layout {
     size_t control, xy, depth, conic, rgb, radius, tau;
     size_t gkey[2], gval[2];
-    size_t scan_lb, sort_lb[2];
+    size_t pairs, scan_lb, sort_lb[2];
     size_t ikey[2], ival[2];
     size_t ranges, grad2d, total;
-    size_t diff, diff_count;
     size_t sort_lb_rows, scan_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes;
 };
@@ -74,9 +73,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->radius = take(nn * sizeof(int));
     L->tau = take(nn * sizeof(float));
     for (int k = 0; k < 2; ++k) { L->gkey[k] = take(nn * 4); L->gval[k] = take(nn * 4); }
-    L->diff_count = (size_t)(L->tiles_x + 1) * (L->tiles_y + 1);
-    L->diff = take(L->diff_count * sizeof(int));
-    L->scan_lb_rows = (nn + kDupChunk - 1) / kDupChunk;
+    L->pairs = take(nn * sizeof(unsigned long long));
+    L->scan_lb_rows = (nn + kPairChunk - 1) / kPairChunk;
     L->scan_lb = take(L->scan_lb_rows * sizeof(unsigned long long));
     const size_t rows_n = (nn + kSortTile - 1) / kSortTile, rows_c = (cc + kSortTileMin - 1) / kSortTileMin;
     L->sort_lb_rows = rows_n > rows_c ? rows_n : rows_c;
@@ -300,13 +298,13 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         void* ws = fs.f[v]->ws;
         Control* ctl = control_of(fs, v);
         clr[v] = ClearArgs{};
-        // flags + num_instances, every counter and histogram, the difference grid, the scan look-back
+        // flags + num_instances, every counter and histogram, the tile ranges, the scan look-back
         clr[v].ptr[0] = reinterpret_cast<uint32_t*>(&ctl->status);
         clr[v].words[0] = 2;
         clr[v].ptr[1] = &ctl->counters[0];
         clr[v].words[1] = (sizeof(Control) - offsetof(Control, counters)) / 4;
-        clr[v].ptr[2] = at<uint32_t>(ws, L.diff);
-        clr[v].words[2] = L.diff_count;
+        clr[v].ptr[2] = at<uint32_t>(ws, L.ranges);
+        clr[v].words[2] = (unsigned long long)L.tiles * 2;
         clr[v].ptr[3] = at<uint32_t>(ws, L.scan_lb);
         clr[v].words[3] = L.scan_lb_rows * 2;
     }
@@ -376,15 +374,15 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.seg_off = a.seg_tile + (f->capacity > 0 ? f->capacity : 1);
         a.seg_gid = at<uint32_t>(ws, L.ival[1]);
         a.num_segments = &ctl->counters[30];
-        a.diff = at<int>(ws, L.diff);
         a.capacity = f->capacity;
         a.hist = &ctl->hist_keys[0][0];
+        a.pairs = at<unsigned long long>(ws, L.pairs);
         a.lookback = at<unsigned long long>(ws, L.scan_lb);
         a.chunk_counter = &ctl0->counters[0];
         a.status = &ctl->status;
     }
     if (launch_scan_tiles(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
-    Multi<TileRangesArgs, MAXF> tr;
+    Multi<RangesArgs, MAXF> tr;
     tr.frames = fs.count;
     Multi<EmitArgs, MAXF> e;
     e.frames = fs.count;
@@ -393,16 +391,15 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         const Layout& L = fs.L[v];
         void* ws = f->ws;
         Control* ctl = control_of(fs, v);
-        TileRangesArgs& t = tr.a[v];
-        t.diff = at<int>(ws, L.diff);
-        t.tiles_x = L.tiles_x;
-        t.tiles_y = L.tiles_y;
+        RangesArgs& t = tr.a[v];
+        t.keys = at<void>(ws, keys_sorted_off(L));
         t.ranges = at<uint32_t>(ws, L.ranges);
-        t.tile_passes = key64 ? L.key_passes - 4 : L.key_passes;
-        t.key_shift = key64 ? 32 : 0;
-        t.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
+        t.tiles = L.tiles;
         t.capacity = f->capacity;
+        t.status = &ctl->status;
         EmitArgs& a = e.a[v];
+        a.tile_passes = key64 ? L.key_passes - 4 : L.key_passes;
+        a.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
         a.n = f->n;
         a.seg_off = d.a[v].seg_off;
         a.seg_tile = d.a[v].seg_tile;
@@ -414,10 +411,10 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.capacity = f->capacity;
         a.status = &ctl->status;
     }
-    if (launch_tile_ranges(tr, s) != cudaSuccess) return GS_ERR_CUDA;
     if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
-    if (key64) return key_sort<unsigned long long>(fs, s);
-    return key_sort<uint32_t>(fs, s);
+    st = key64 ? key_sort<unsigned long long>(fs, s) : key_sort<uint32_t>(fs, s);
+    if (st != GS_OK) return st;
+    return ok(launch_ranges(tr, key64, s));
 }
 
 template <int MAXF>

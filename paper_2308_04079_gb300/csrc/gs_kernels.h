@@ -21,11 +21,13 @@ struct SortTile {
 constexpr int kSortTile = SortTile<uint32_t>::keys;            // 4096
 constexpr int kSortTileMin = SortTile<unsigned long long>::keys; // 3072
 constexpr int kMaxKeyPasses = 8;
+constexpr int kMaxTilePasses = 3;   // tile ids below 2^24
 constexpr int kDepthPasses = 4;
 
-// Scan of tiles per Gaussian: 256 threads, 4 Gaussians per thread.
+// Tiles per Gaussian: 256 threads, one list entry per thread; the scan of the per-entry
+// (segments, tiles) pairs takes chunks of 2048 entries.
 constexpr int kDupThreads = 256;
-constexpr int kDupChunk = 1024;
+constexpr int kPairChunk = 2048;
 // Instance emission: 256 threads, one warp per 32 segment records.
 constexpr int kEmitThreads = 256;
 
@@ -158,6 +160,7 @@ struct ScanArgs {
     const float4* conic;       // (l11, l21, l22, o)
     const float* tau;          // alpha-threshold level per Gaussian
     int rect_only;             // 1: every tile of the 3-sigma rectangle (GS_TILES_RECT)
+    unsigned long long* pairs; // [entries] (segments << 32 | tiles), then their exclusive prefix
     const int* radius;
     const float* depth;
     CamK cam;
@@ -165,22 +168,20 @@ struct ScanArgs {
     uint32_t* seg_tile;        // [capacity] first tile id of every segment
     uint32_t* seg_gid;         // [capacity] Gaussian of every segment
     uint32_t* num_segments;
-    int* diff;                 // [tiles_y * (tiles_x + 1)] per-row difference grid, zeroed
     unsigned long long capacity;
     uint32_t* hist;            // [4][256] depth-digit histograms (KEY64 only)
-    unsigned long long* lookback;  // [chunks], zeroed
+    unsigned long long* lookback;  // [entries / kPairChunk], zeroed
     uint32_t* chunk_counter;
     gs_device_status* status;
 };
 
-struct TileRangesArgs {
-    int* diff;                 // per-row difference grid, turned into per-tile counts in place
-    int tiles_x, tiles_y;
-    uint32_t* ranges;
-    uint32_t* hist;            // [tile_passes][256] histograms of the tile-id passes
-    int tile_passes;
-    int key_shift;             // bit position of the tile id inside the key (0 or 32)
+// Tile ranges from the sorted keys (uint32 tile ids, or 64-bit keys with the tile id high).
+struct RangesArgs {
+    const void* keys;
+    uint32_t* ranges;          // [2 * tiles], zeroed
+    int tiles;
     unsigned long long capacity;
+    const gs_device_status* status;
 };
 
 struct EmitArgs {
@@ -192,6 +193,8 @@ struct EmitArgs {
     const float* depth;
     void* keys_out;
     uint32_t* vals_out;
+    uint32_t* hist;            // [tile_passes][256] digit histograms of the tile-id radix passes
+    int tile_passes;
     unsigned long long capacity;
     gs_device_status* status;  // num_segments is reported here
 };
@@ -246,7 +249,7 @@ template <int MAXF> cudaError_t launch_depth_hist(Multi<DepthHistArgs, MAXF>& m,
 template <typename KeyT, int MAXF>
 cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_chunks, cudaStream_t s);
 template <int MAXF> cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s);
-template <int MAXF> cudaError_t launch_tile_ranges(const Multi<TileRangesArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_ranges(const Multi<RangesArgs, MAXF>& m, bool key64, cudaStream_t s);
 template <int MAXF> cudaError_t launch_emit(const Multi<EmitArgs, MAXF>& m, bool key64, cudaStream_t s);
 template <int MAXF> cudaError_t launch_sort_prepare(const Multi<SortPrepareArgs, MAXF>& m, cudaStream_t s);
 template <int MAXF> cudaError_t launch_render_forward(Multi<RenderFwdArgs, MAXF>& m, cudaStream_t s);
