@@ -16,8 +16,9 @@
 //   position of the last blended Gaussian.
 // Backward: the tile's list is walked back to front from the largest last position in the tile;
 //   each pixel only processes positions below its own last position, recovers
-//   T_i = T_{i+1} / (1 - a_i) from the stored final T, and keeps R, the colour behind the current
-//   Gaussian normalised by the transmittance in front of it (R starts at bg):
+//   T_i = T_{i+1} / (1 - a_i) from the stored final T, and keeps R . dL/dC, the projection of
+//   the colour behind the current Gaussian (normalised by the transmittance in front of it; R
+//   starts at bg) on the pixel's dL/dC, which is all the recurrence needs:
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
 //   Through a = o G (zero when clamped), with g = Sigma'^-1 d: d(power)/d(mean) = g and
 //   d(power)/d(Sigma') = g g^T / 2.  A thread sums its pixels' dL/d(mean2D, Sigma', opacity,
@@ -40,7 +41,7 @@ constexpr float kScaleLog2 = 0.84932180028801907f;
 // 1 / kScaleLog2^2 = 2 ln 2: converts scaled (p, q) products back to natural units.
 constexpr float kTwoLn2 = 1.3862943611198906f;
 // At most this many contributing lanes add their own sums instead of a warp reduction.
-constexpr int kDirectLanes = 2;
+constexpr int kDirectLanes = 8;
 
 struct Staged {
     float4 a;   // (ox, oy, thr, lo): tile-relative offset, skip threshold, log2(opacity)
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     const float log2_amin = __log2f(a.cfg.alpha_min);
     const size_t P = (size_t)c.W * c.H;
 
-    float T[PX], Rr[PX], Rg[PX], Rb[PX], dLr[PX], dLg[PX], dLb[PX];
+    // Per pixel: T, R . dL/dC (only this projection of the colour behind is ever needed) and dL/dC.
+    float T[PX], Rd[PX], dLr[PX], dLg[PX], dLb[PX];
     uint32_t mylast[PX];
     uint32_t tmax = 0;
 #pragma unroll
@@ -244,9 +246,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
             dLg[j] = a.dL_drgb[P + p];
             dLb[j] = a.dL_drgb[2 * P + p];
         }
-        Rr[j] = a.bg[0];
-        Rg[j] = a.bg[1];
-        Rb[j] = a.bg[2];
+        Rd[j] = a.bg[0] * dLr[j] + a.bg[1] * dLg[j] + a.bg[2] * dLb[j];
         tmax = max(tmax, mylast[j]);
     }
     if (threadIdx.x == 0) s_max = 0;
@@ -283,6 +283,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
             float p0, dp, q, qq;
             splat_row(st, lyf, c0f, p0, dp, q, qq);
             if (pos < tmax && qq <= st.a.z) {                      // s >= q^2: else the whole row skips
+                const float4 col = s_rgb[k];
+                const float qv = __fmul_rn(st.b.z, q);
 #pragma unroll
                 for (int j = 0; j < PX; ++j) {
                     float p;
@@ -293,41 +295,42 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                     const float oG = exp2f(__fsub_rn(st.a.w, s));
                     const float alpha = fminf(amax, oG);
                     const float one_m = __fsub_rn(1.0f, alpha);
-                    const float Ti = T[j] / one_m;
+                    const float Ti = __fdividef(T[j], one_m);   // one_m >= 0.01: 2-ulp division
                     const float w = alpha * Ti;
-                    const float4 col = s_rgb[k];
                     g[6] += w * dLr[j];
                     g[7] += w * dLg[j];
                     g[8] += w * dLb[j];
-                    const float dalpha =
-                        Ti * ((col.x - Rr[j]) * dLr[j] + (col.y - Rg[j]) * dLg[j] + (col.z - Rb[j]) * dLb[j]);
-                    Rr[j] = alpha * col.x + one_m * Rr[j];
-                    Rg[j] = alpha * col.y + one_m * Rg[j];
-                    Rb[j] = alpha * col.z + one_m * Rb[j];
+                    // dL/dalpha = T_i (c_i - R_{i+1}) . dL/dC;  R_i . dL/dC = R_{i+1} . dL/dC + alpha (c_i - R_{i+1}) . dL/dC
+                    const float diff = col.x * dLr[j] + col.y * dLg[j] + col.z * dLb[j] - Rd[j];
+                    const float dalpha = Ti * diff;
+                    Rd[j] = fmaf(alpha, diff, Rd[j]);
                     T[j] = Ti;
                     if (oG <= amax) {
-                        g[5] += oG * st.b.w * dalpha;                 // G = oG / o
-                        const float dpow = oG * dalpha;               // dL/d(power)
-                        // g = Sigma'^-1 d = L (p, q) in natural units
-                        const float gx = st.b.x * p * kTwoLn2;
-                        const float gy = (st.b.y * p + st.b.z * q) * kTwoLn2;
-                        const float h = 0.5f * dpow;
-                        g[0] += gx * dpow;
-                        g[1] += gy * dpow;
-                        g[2] += h * gx * gx;
-                        g[3] += h * gx * gy;
-                        g[4] += h * gy * gy;
+                        // dpow = dL/d(power); g = Sigma'^-1 d = 2 ln 2 (u, v) with (u, v) = L' (p, q):
+                        // sums of dpow (u, v) and dpow (u, v)(u, v)^T here, the constant factors
+                        // 1/o, 2 ln 2 and (2 ln 2)^2 / 2 once per splat below
+                        const float dpow = oG * dalpha;
+                        const float u = st.b.x * p;
+                        const float v = fmaf(st.b.y, p, qv);
+                        const float du = dpow * u, dv = dpow * v;
+                        g[0] += du;
+                        g[1] += dv;
+                        g[2] = fmaf(du, u, g[2]);
+                        g[3] = fmaf(du, v, g[3]);
+                        g[4] = fmaf(dv, v, g[4]);
+                        g[5] += dpow;
                     }
                 }
             }
             const uint32_t who = __ballot_sync(0xffffffffu, contrib);
             if (who == 0) continue;
             float* dst = a.grad2d + 12 * (size_t)s_idx[k];
+            const float k1 = kTwoLn2, k2 = 0.5f * kTwoLn2 * kTwoLn2, ko = st.b.w;
             if (__popc(who) <= kDirectLanes) {
                 // few contributing lanes: each adds its own sums (cheaper than a butterfly)
                 if (contrib) {
-                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(g[0], g[1], g[2], g[3]));
-                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(g[4], g[5], g[6], g[7]));
+                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(k1 * g[0], k1 * g[1], k2 * g[2], k2 * g[3]));
+                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(k2 * g[4], ko * g[5], g[6], g[7]));
                     atomicAdd(dst + 8, g[8]);
                 }
             } else {
@@ -337,8 +340,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                     for (int o = 16; o > 0; o >>= 1) g[v] += __shfl_xor_sync(0xffffffffu, g[v], o);
                 }
                 if ((threadIdx.x & 31) == 0) {
-                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(g[0], g[1], g[2], g[3]));
-                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(g[4], g[5], g[6], g[7]));
+                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(k1 * g[0], k1 * g[1], k2 * g[2], k2 * g[3]));
+                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(k2 * g[4], ko * g[5], g[6], g[7]));
                     atomicAdd(dst + 8, g[8]);
                 }
             }
