@@ -41,8 +41,8 @@ constexpr unsigned long long kScanInc = 2ull << 62;
 constexpr unsigned long long kScanFlags = 3ull << 62;
 
 template <typename KeyT>
-__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift) {
-    return (uint32_t)(k >> shift) & 0xFFu;
+__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask) {
+    return (uint32_t)(k >> shift) & mask;
 }
 
 __device__ __forceinline__ void backoff(uint32_t spins) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
         uint32_t* wh = s_hist[warp];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t d = digit_of(key[i], a.shift);
+            const uint32_t d = digit_of(key[i], a.shift, a.mask);
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             const uint32_t below = peers & lt;
             const uint32_t prev = wh[d];
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
         // Stage keys and values in local sorted order.
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t dd = digit_of(key[i], a.shift);
+            const uint32_t dd = digit_of(key[i], a.shift, a.mask);
             const uint32_t p = s_block_start[dd] + s_hist[warp][dd] + pos_local[i];
             s_keys[p] = key[i];
             const uint32_t pos = wbase + i * 32 + lane;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
         for (int k = 0; k < ITEMS; ++k) {
             const uint32_t s = tid + k * kSortThreads;
             const KeyT kk = s_keys[s];
-            const uint32_t dd = digit_of(kk, a.shift);
+            const uint32_t dd = digit_of(kk, a.shift, a.mask);
             const uint32_t dest = s_global[dd] + (s - s_block_start[dd]);
             if (dest < count) {
                 a.keys_out[dest] = kk;
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kDupThreads) k_write_segments(const __grid_con
 // one contiguous run; every lane finds the segment of each output position it writes by a
 // 5-step search over the lanes' segment ends, so keys and values are written coalesced.  A
 // block takes 256 records (one frame per block unit); the digit histograms of the tile-id
-// radix passes are accumulated in shared memory on the way.  Nothing is written after a
+// radix passes (tile_digit_bits bits each) are accumulated in shared memory on the way.  Nothing is written after a
 // capacity overflow or a timed-out scan.
 // ---------------------------------------------------------------------------------------
 template <bool KEY64, int MAXF>
@@ -727,6 +727,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
         const uint32_t K = a.status->num_instances;
         const uint32_t S = *a.num_segments;
         const int passes = a.tile_passes;
+        const int wbits = a.tile_digit_bits;
+        const uint32_t dmask = (1u << wbits) - 1u;
         KeyT* const keys_out = reinterpret_cast<KeyT*>(a.keys_out);
         uint32_t* const vals_out = a.vals_out;
         const uint32_t s0 = (u - s_ubase[f]) * UNIT + warp * 32u;
@@ -748,10 +750,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
         if (valid && end <= K && end > beg) {
             const uint32_t t_end = tile0 + (end - beg);
             for (int p = 1; p < passes; ++p) {
-                const int sh = 8 * p;
+                const int sh = wbits * p;
                 for (uint32_t t = tile0; t < t_end;) {
                     const uint32_t run_end = min(t_end, ((t >> sh) + 1u) << sh);
-                    atomicAdd(&s_hist[p][(t >> sh) & 0xFFu], run_end - t);
+                    atomicAdd(&s_hist[p][(t >> sh) & dmask], run_end - t);
                     t = run_end;
                 }
             }
@@ -774,7 +776,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
                 else keys_out[out] = (KeyT)tile;
                 vals_out[out] = g;
                 // lowest tile-id digit: consecutive outputs mostly hold consecutive tiles
-                atomicAdd(&s_hist[0][tile & 0xFFu], 1u);
+                if (passes > 0) atomicAdd(&s_hist[0][tile & dmask], 1u);
             }
         }
     }

@@ -29,7 +29,7 @@ struct Layout {
     size_t ikey[2], ival[2];
     size_t ranges, grad2d, total;
     size_t sort_lb_rows, scan_lb_rows;
-    int tiles_x, tiles_y, tiles, key_passes, depth_passes;
+    int tiles_x, tiles_y, tiles, key_passes, depth_passes, tile_passes, tile_digit_bits;
 };
 
 bool valid_cfg(const gs_raster_config* c) {
@@ -53,12 +53,16 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->tiles_x = (W + cfg->tile_w - 1) / cfg->tile_w;
     L->tiles_y = (H + cfg->tile_h - 1) / cfg->tile_h;
     L->tiles = L->tiles_x * L->tiles_y;
+    // tile ids take ceil(bits / 8) radix passes of 8-bit digits (measured faster on 1080p
+    // frames than equal-width digits: 8 + 5 bits beat 7 + 6)
     const int tile_bits = bits_for((uint32_t)(L->tiles - 1));
+    L->tile_passes = (tile_bits + 7) / 8;
+    L->tile_digit_bits = L->tile_passes ? 8 : 0;
     if (cfg->sort_mode == GS_SORT_KEY64) {
-        L->key_passes = (32 + tile_bits + 7) / 8;
+        L->key_passes = 4 + L->tile_passes;
         L->depth_passes = 0;
     } else {
-        L->key_passes = (tile_bits + 7) / 8;
+        L->key_passes = L->tile_passes;
         L->depth_passes = kDepthPasses;
     }
     const size_t nn = (size_t)(n > 0 ? n : 1);
@@ -277,7 +281,11 @@ gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
             a.vals_out = at<uint32_t>(ws, L.ival[(p + 1) % 2]);
             a.count_dev = &ctl->status.num_instances;
             a.count_host = live ? (uint32_t)fs.f[v]->capacity : 0u;
-            a.shift = 8 * p;
+            // KEY64: four 8-bit depth digits, then the tile-id digits from bit 32
+            const bool depth_digit = sizeof(KeyT) == 8 && p < 4;
+            const int tp = sizeof(KeyT) == 8 ? p - 4 : p;
+            a.shift = depth_digit ? 8 * p : (sizeof(KeyT) == 8 ? 32 : 0) + tp * L.tile_digit_bits;
+            a.mask = depth_digit ? 0xFFu : (1u << L.tile_digit_bits) - 1u;
             a.hist = ctl->hist_keys[p < kMaxKeyPasses ? p : 0];
             a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
             a.lookback_next = (p + 1 < L.key_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
@@ -345,6 +353,7 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
                 a.count_dev = nullptr;
                 a.count_host = (uint32_t)fs.f[v]->n;
                 a.shift = 8 * p;
+                a.mask = 0xFFu;
                 a.hist = ctl->hist_depth[p];
                 a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
                 a.lookback_next = (p + 1 < kDepthPasses) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
@@ -398,7 +407,8 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         t.capacity = f->capacity;
         t.status = &ctl->status;
         EmitArgs& a = e.a[v];
-        a.tile_passes = key64 ? L.key_passes - 4 : L.key_passes;
+        a.tile_passes = L.tile_passes;
+        a.tile_digit_bits = L.tile_digit_bits;
         a.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
         a.n = f->n;
         a.seg_off = d.a[v].seg_off;

@@ -144,7 +144,8 @@ struct SortPassArgs {
     uint32_t* vals_out;
     const uint32_t* count_dev; // null: count_host
     uint32_t count_host;       // element count bound (capacity)
-    int shift;
+    int shift;                 // digit = (key >> shift) & mask
+    uint32_t mask;
     const uint32_t* hist;      // [256] digit counts of this pass
     uint32_t* lookback;        // [chunks][256], zeroed
     uint32_t* lookback_next;   // rows to zero for the next pass, or null
@@ -195,6 +196,7 @@ struct EmitArgs {
     uint32_t* vals_out;
     uint32_t* hist;            // [tile_passes][256] digit histograms of the tile-id radix passes
     int tile_passes;
+    int tile_digit_bits;       // bits per tile-id digit (<= 8)
     unsigned long long capacity;
     gs_device_status* status;  // num_segments is reported here
 };
