@@ -51,7 +51,7 @@ KERNEL_NAMES = {"preprocess": "k_preprocess_t", "render_forward": "k_render_forw
 # DRAM bytes (read + write) per launch of each single-kernel stage on the 3M-Gaussian 1080p
 # frame, from the ncu capture summarised in the named file under profiles/; None where no
 # capture of the current kernel exists.
-TRAFFIC = {}   # re-captured after each change of the kernel
+TRAFFIC = {"render_backward_tiles": 106_690_000}   # profiles/k_render_backward_config3.md
 
 
 def env_int(k, d):
