@@ -286,6 +286,7 @@ gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
             const int tp = sizeof(KeyT) == 8 ? p - 4 : p;
             a.shift = depth_digit ? 8 * p : (sizeof(KeyT) == 8 ? 32 : 0) + tp * L.tile_digit_bits;
             a.mask = depth_digit ? 0xFFu : (1u << L.tile_digit_bits) - 1u;
+            a.ballot_rank = tp == 0;   // lowest tile-id byte: spread digits
             a.hist = ctl->hist_keys[p < kMaxKeyPasses ? p : 0];
             a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
             a.lookback_next = (p + 1 < L.key_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
@@ -354,6 +355,7 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
                 a.count_host = (uint32_t)fs.f[v]->n;
                 a.shift = 8 * p;
                 a.mask = 0xFFu;
+                a.ballot_rank = 0;
                 a.hist = ctl->hist_depth[p];
                 a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
                 a.lookback_next = (p + 1 < kDepthPasses) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;

@@ -146,6 +146,7 @@ struct SortPassArgs {
     uint32_t count_host;       // element count bound (capacity)
     int shift;                 // digit = (key >> shift) & mask
     uint32_t mask;
+    int ballot_rank;           // rank digits with ballots (spread digits) instead of match_any
     const uint32_t* hist;      // [256] digit counts of this pass
     uint32_t* lookback;        // [chunks][256], zeroed
     uint32_t* lookback_next;   // rows to zero for the next pass, or null

@@ -100,6 +100,7 @@ extern "C" gs_status gs_depth_order_static(int n, const float* depth, const int*
         a.count_host = (uint32_t)n;
         a.shift = 8 * p;
         a.mask = 0xFFu;
+        a.ballot_rank = 0;
         a.hist = sc->hist[p];
         a.lookback = sc->lookback[p % 2];
         a.lookback_next = last ? nullptr : sc->lookback[(p + 1) % 2];
