@@ -256,6 +256,43 @@ gs_status gs_batch_render_backward(const gs_frame* frames, const gs_gaussians* g
                                    const uint32_t* const* last, const gs_gradients* grads, int accumulate,
                                    cudaStream_t stream);
 
+/* ---- Training step (Sec. 5.1, Algorithm 1): loss and parameter update ---------------------
+ * L = (1 - lambda) L1 + lambda (1 - SSIM) of a rendered image against a target (the paper uses
+ * lambda = 0.2), with its gradient with respect to the rendered image.  SSIM per channel with an
+ * 11x11 Gaussian window (sigma 1.5), C1 = 0.01^2, C2 = 0.03^2, zero padding, averaged over all
+ * pixels and channels; L1 the mean absolute difference; d|x - y|/dx = sign(x - y) (0 at x = y).
+ *   img, target  device float[3, H, W] planar
+ *   ws           device workspace of gs_loss_workspace_size(width, height) bytes, 256-aligned
+ *   out_loss     device float[3]: L, L1, mean SSIM
+ *   dL_dimg      device float[3, H, W]
+ * Asynchronous on `stream`.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+size_t gs_loss_workspace_size(int width, int height);
+gs_status gs_loss_l1_dssim(const float* img, const float* target, int width, int height, float lambda, void* ws,
+                           size_t ws_bytes, float* out_loss, float* dL_dimg, cudaStream_t stream);
+
+/* Activation of a parameter tensor: the rasterizer sees act(raw) (Sec. 5.1: sigmoid for the
+ * opacity, exp for the scales). */
+enum { GS_ACT_NONE = 0, GS_ACT_EXP = 1, GS_ACT_SIGMOID = 2 };
+
+/* One parameter tensor of an Adam step; `grad` is the gradient with respect to act(param). */
+typedef struct gs_adam_group {
+    float* param;             /* device float[n], raw values, updated in place                  */
+    const float* grad;        /* device float[n]                                                */
+    float* m;                 /* device float[n], first moment, updated in place (zero at start) */
+    float* v;                 /* device float[n], second moment, updated in place               */
+    float* activated;         /* device float[n] or NULL: receives act(updated param)           */
+    uint64_t n;
+    float lr;                 /* learning rate of this step (schedules are the caller's)        */
+    int activation;           /* GS_ACT_*                                                       */
+} gs_adam_group;
+
+/* Adam (Kingma & Ba) with bias correction, step >= 1, over up to 8 groups in one launch:
+ *   g = grad * act'(param); m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ *   param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_adam_step(const gs_adam_group* groups, int count, float beta1, float beta2, float eps, int step,
+                       cudaStream_t stream);
+
 /* Depth ordering without workspace or allocation (no counterpart in the paper; it is the
  * first phase of the GS_SORT_TWO_PHASE binning schedule offered on its own).
  * Writes order[0..n): the indices i with radius[i] > 0 sorted by the fp32 bits of depth[i]

@@ -71,6 +71,13 @@ class gs_device_status(ctypes.Structure):
                 ("num_segments", c_uint32), ("reserved", c_uint32)]
 
 
+class gs_adam_group(ctypes.Structure):
+    _fields_ = [("param", c_void_p), ("grad", c_void_p), ("m", c_void_p), ("v", c_void_p), ("activated", c_void_p),
+                ("n", c_uint64), ("lr", c_float), ("activation", c_int)]
+
+
+GS_ACT_NONE, GS_ACT_EXP, GS_ACT_SIGMOID = 0, 1, 2
+
 # (name, restype, argtypes) of every entry point declared in include/gs.h
 SIGNATURES = [
     ("gs_default_config", None, [ctypes.POINTER(gs_raster_config)]),
@@ -97,6 +104,10 @@ SIGNATURES = [
     ("gs_batch_render_backward", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(gs_gaussians), c_int,
                                          ctypes.POINTER(c_float), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                          ctypes.POINTER(c_void_p), ctypes.POINTER(gs_gradients), c_int, c_void_p]),
+    ("gs_loss_workspace_size", c_size_t, [c_int, c_int]),
+    ("gs_loss_l1_dssim", c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_void_p, c_size_t, c_void_p, c_void_p,
+                                 c_void_p]),
+    ("gs_adam_step", c_int, [ctypes.POINTER(gs_adam_group), c_int, c_float, c_float, c_float, c_int, c_void_p]),
     ("gs_depth_order_static", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("gs_status_string", ctypes.c_char_p, [c_int]),
 ]
@@ -242,3 +253,18 @@ def gs_batch_render_backward(frames, gaussians, bg, dL_drgb, T, last, grads, acc
     p_last, k3 = _ptrs(last)
     _check(load().gs_batch_render_backward(fr, gg, len(frames), b, p_d, p_T, p_last, gr, int(bool(accumulate)),
                                            stream), "gs_batch_render_backward")
+
+
+def gs_loss_workspace_size(width: int, height: int) -> int:
+    return int(load().gs_loss_workspace_size(width, height))
+
+
+def gs_loss_l1_dssim(img: int, target: int, width: int, height: int, lam: float, ws: int, ws_bytes: int,
+                     out_loss: int, dL_dimg: int, stream: int) -> None:
+    _check(load().gs_loss_l1_dssim(img, target, width, height, lam, ws, ws_bytes, out_loss, dL_dimg, stream),
+           "gs_loss_l1_dssim")
+
+
+def gs_adam_step(groups, beta1: float, beta2: float, eps: float, step: int, stream: int) -> None:
+    arr = (gs_adam_group * len(groups))(*groups)
+    _check(load().gs_adam_step(arr, len(groups), beta1, beta2, eps, step, stream), "gs_adam_step")
