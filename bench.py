@@ -304,6 +304,32 @@ def run_ours(args, rank, world, local_rank):
         render_only = {"what": "preprocess + bin_sort + render_forward of the same frame", "ms": round(r_ms, 4),
                        "frames_per_s": round(1e3 / r_ms, 1)}
 
+    # one training iteration (Sec. 5.1): forward, L1 + D-SSIM loss against a synthetic target
+    # view, backward, Adam with the activations, on the same scene
+    train = None
+    if not args.no_batch:
+        from paper_2308_04079_gb300.training import GaussianModel, Trainer
+        model = GaussianModel.from_numpy(g, device=dev)
+        trainer = Trainer(model, bg=bg)
+        target = torch.from_numpy(np.random.default_rng(77).random((3, cam.height, cam.width),
+                                                                   dtype=np.float32)).to(dev)
+        for _ in range(3):
+            trainer.step(cam, target)
+        torch.cuda.synchronize()
+        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ta.record(stream)
+        for _ in range(args.steps):
+            out = trainer.step(cam, target)
+        tb.record(stream)
+        torch.cuda.synchronize()
+        codes = trainer.status()
+        t_ms = ta.elapsed_time(tb) / args.steps
+        train = {"what": "forward + L1/D-SSIM loss (lambda 0.2) + backward + fused activation/Adam of all "
+                         "parameters, synthetic target", "ms": round(t_ms, 4),
+                 "iterations_per_s": round(1e3 / t_ms, 1), "loss": round(float(out[0].item()), 6),
+                 "status": sorted(set(int(c) for c in codes.values()))}
+        del trainer, model
+
     batch = multi = None
     if not args.no_batch and args.gaussians == CONFIG3_N:
         batch = run_batch(args, dev)
@@ -324,7 +350,7 @@ def run_ours(args, rank, world, local_rank):
                    "blended_pairs": blended,
                    "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "batch": batch, "multi_scene": multi,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "batch": batch, "multi_scene": multi,
         "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
     }
     if rank == 0:

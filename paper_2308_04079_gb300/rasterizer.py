@@ -125,6 +125,14 @@ class Frame:
         self.ws[self.layout.status:self.layout.status + ctypes.sizeof(abi.gs_device_status)].zero_()
         self.frame = abi.gs_frame(self.n, self.cam, self.cfg, self.capacity, self.ws.data_ptr(), size)
 
+    def set_camera(self, camera) -> None:
+        """Another camera of the same image size (the workspace layout stays valid)."""
+        cam = camera_struct(camera)
+        if (cam.width, cam.height) != (self.cam.width, self.cam.height):
+            raise ValueError("set_camera keeps the image size")
+        self.camera, self.cam = camera, cam
+        self.frame.cam = cam
+
     @property
     def width(self) -> int:
         return self.cam.width
