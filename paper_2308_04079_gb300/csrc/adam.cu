@@ -29,9 +29,11 @@ struct AdamGroupK {
 
 constexpr int kMaxGroups = 8;
 
+constexpr int kAdamChunk = 1024;   // elements per block unit: 256 threads x 4
+
 struct AdamArgs {
     int groups;
-    unsigned long long base[kMaxGroups + 1];   // element prefix of the groups
+    unsigned long long base[kMaxGroups + 1];   // block-unit prefix of the groups
     AdamGroupK g[kMaxGroups];
     float b1, b2, eps, c1, c2;                 // c1 = 1 - b1^t, c2 = 1 - b2^t
 };
@@ -42,28 +44,65 @@ __device__ __forceinline__ float activate(float raw, int act) {
     return raw;
 }
 
+struct AdamConsts {
+    float b1, b2, eps, c1, c2, lr;
+    int act;
+};
+
+__device__ __forceinline__ float adam_one(const AdamConsts& k, float raw, float g, float& m, float& v, float& act_out) {
+    if (k.act != GS_ACT_NONE) {
+        const float a = activate(raw, k.act);
+        g *= k.act == GS_ACT_EXP ? a : a * (1.0f - a);
+    }
+    m = k.b1 * m + (1.0f - k.b1) * g;
+    v = k.b2 * v + (1.0f - k.b2) * g * g;
+    const float nraw = raw - k.lr * (m / k.c1) / (sqrtf(v / k.c2) + k.eps);
+    act_out = activate(nraw, k.act);
+    return nraw;
+}
+
+// Block unit u of group k covers elements [(u - base[k]) * kAdamChunk, + kAdamChunk); each
+// thread takes 4 consecutive elements, as one 16-byte access when the group allows it.
 __global__ void __launch_bounds__(256) k_adam(const __grid_constant__ AdamArgs a) {
     const unsigned long long total = a.base[a.groups];
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    for (unsigned long long u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
         int k = 0;
-        while (k + 1 < a.groups && a.base[k + 1] <= i) ++k;
+        while (k + 1 < a.groups && a.base[k + 1] <= u) ++k;
         const AdamGroupK& gr = a.g[k];
-        const unsigned long long j = i - a.base[k];
-        const float raw = gr.param[j];
-        float g = gr.grad[j];
-        if (gr.activation != GS_ACT_NONE) {
-            const float act = activate(raw, gr.activation);
-            g *= gr.activation == GS_ACT_EXP ? act : act * (1.0f - act);
+        float* const param = gr.param;
+        const float* const grad = gr.grad;
+        float* const mm = gr.m;
+        float* const vv = gr.v;
+        float* const activated = gr.activated;
+        const unsigned long long n = gr.n;
+        const AdamConsts c{a.b1, a.b2, a.eps, a.c1, a.c2, gr.lr, gr.activation};
+        const unsigned long long j = (u - a.base[k]) * kAdamChunk + 4ull * threadIdx.x;
+        const bool vec = ((reinterpret_cast<uintptr_t>(param) | reinterpret_cast<uintptr_t>(grad) |
+                           reinterpret_cast<uintptr_t>(mm) | reinterpret_cast<uintptr_t>(vv) |
+                           reinterpret_cast<uintptr_t>(activated)) & 15) == 0;
+        if (vec && j + 4 <= n) {
+            float4 p = *reinterpret_cast<const float4*>(param + j);
+            const float4 g = *reinterpret_cast<const float4*>(grad + j);
+            float4 m = *reinterpret_cast<const float4*>(mm + j);
+            float4 v = *reinterpret_cast<const float4*>(vv + j);
+            float4 act;
+            p.x = adam_one(c, p.x, g.x, m.x, v.x, act.x);
+            p.y = adam_one(c, p.y, g.y, m.y, v.y, act.y);
+            p.z = adam_one(c, p.z, g.z, m.z, v.z, act.z);
+            p.w = adam_one(c, p.w, g.w, m.w, v.w, act.w);
+            *reinterpret_cast<float4*>(param + j) = p;
+            *reinterpret_cast<float4*>(mm + j) = m;
+            *reinterpret_cast<float4*>(vv + j) = v;
+            if (activated) *reinterpret_cast<float4*>(activated + j) = act;
+        } else {
+            for (unsigned long long e = j; e < j + 4 && e < n; ++e) {
+                float m = mm[e], v = vv[e], act;
+                param[e] = adam_one(c, param[e], grad[e], m, v, act);
+                mm[e] = m;
+                vv[e] = v;
+                if (activated) activated[e] = act;
+            }
         }
-        const float m = a.b1 * gr.m[j] + (1.0f - a.b1) * g;
-        const float v = a.b2 * gr.v[j] + (1.0f - a.b2) * g * g;
-        gr.m[j] = m;
-        gr.v[j] = v;
-        const float upd = gr.lr * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
-        const float nraw = raw - upd;
-        gr.param[j] = nraw;
-        if (gr.activated) gr.activated[j] = activate(nraw, gr.activation);
     }
 }
 
@@ -85,7 +124,7 @@ extern "C" gs_status gs_adam_step(const gs_adam_group* groups, int count, float 
         if (g.activation != GS_ACT_NONE && g.activation != GS_ACT_EXP && g.activation != GS_ACT_SIGMOID)
             return GS_ERR_INVALID_ARG;
         a.g[k] = AdamGroupK{g.param, g.grad, g.m, g.v, g.activated, g.n, g.lr, g.activation};
-        a.base[k + 1] = a.base[k] + g.n;
+        a.base[k + 1] = a.base[k] + (g.n + kAdamChunk - 1) / kAdamChunk;
     }
     a.b1 = beta1;
     a.b2 = beta2;
@@ -93,8 +132,8 @@ extern "C" gs_status gs_adam_step(const gs_adam_group* groups, int count, float 
     a.c1 = (float)(1.0 - std::pow((double)beta1, step));
     a.c2 = (float)(1.0 - std::pow((double)beta2, step));
     if (a.base[count] == 0) return GS_OK;
-    const unsigned long long blocks = (a.base[count] + 255) / 256;
-    const int cap = persistent_grid((const void*)k_adam, 256) * 4;
+    const unsigned long long blocks = a.base[count];
+    const int cap = persistent_grid((const void*)k_adam, 256) * 8;
     k_adam<<<(int)(blocks < (unsigned long long)cap ? blocks : cap), 256, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
