@@ -75,8 +75,13 @@ __global__ void __launch_bounds__(256) k_depth_hist(const __grid_constant__ Mult
         const bool valid = i < a.n;
         uint32_t key = 0xFFFFFFFFu;
         if (valid && a.radius[i] > 0) key = __float_as_uint(a.depth[i]);
+        // the two low bytes of the depth bits are spread (plain shared atomics rarely collide);
+        // the two high bytes repeat across a warp (one atomic per distinct digit)
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < 2; ++p)
+            if (valid) atomicAdd(&s_hist[p][(key >> (8 * p)) & 0xFFu], 1u);
+#pragma unroll
+        for (int p = 2; p < 4; ++p) {
             const uint32_t d = valid ? (key >> (8 * p)) & 0xFFu : 0x100u;
             const uint32_t peers = __match_any_sync(0xffffffffu, d);
             if (valid && (peers & lt) == 0) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
