@@ -22,9 +22,9 @@
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
 //   Through a = o G (zero when clamped), with g = Sigma'^-1 d: d(power)/d(mean) = g and
 //   d(power)/d(Sigma') = g g^T / 2.  A thread sums its pixels' dL/d(mean2D, Sigma', opacity,
-//   colour); when more than two lanes of a warp contributed, the warp sums its lanes with
-//   shuffles and lane 0 adds the result to the splat's accumulators with vector atomics,
-//   otherwise the contributing lanes add their own sums.
+//   colour); when more than eight lanes of a warp contributed, the warp sums its lanes with a
+//   transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals with one atomic
+//   instruction, otherwise the contributing lanes add their own sums.
 //
 // The forward and the backward evaluate a (pixel, splat) pair with the same staging and the same
 // operation sequence (stage_splat, splat_row, splat_s), so their skip and clamp decisions agree
@@ -68,6 +68,51 @@ __device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, 
     } else {
         lim = make_float2(-1e30f, -1e30f);   // never reaches alpha >= alpha_min
     }
+}
+
+// Sum over the warp of the 9 accumulators v[0..8] by a transposed reduce-scatter: each round
+// halves the values a lane keeps (it sends the half its partner keeps and adds the half it
+// receives), 12 shuffles instead of 45.  Afterwards the total of accumulator slot(lane) is in
+// the even lanes of each pair (slot < 0: padding); see reduce_slot.
+__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane) {
+    float a[5];
+    const bool h16 = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {   // lanes 0-15 keep v[0..4], lanes 16-31 keep v[5..8] (+ padding)
+        const float lo = v[i], hi = i < 4 ? v[5 + i] : 0.f;
+        a[i] = (h16 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h16 ? lo : hi, 16);
+    }
+    float b[3];
+    const bool h8 = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {   // keep a[0..2] or a[3..4] (+ padding)
+        const float lo = a[i], hi = i < 2 ? a[3 + i] : 0.f;
+        b[i] = (h8 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h8 ? lo : hi, 8);
+    }
+    float c[2];
+    const bool h4 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {   // keep b[0..1] or b[2] (+ padding)
+        const float lo = b[i], hi = i < 1 ? b[2] : 0.f;
+        c[i] = (h4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h4 ? lo : hi, 4);
+    }
+    const bool h2 = lane & 2;
+    float d = (h2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, h2 ? c[0] : c[1], 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+
+// Accumulator slot whose warp total warp_reduce9 leaves in `lane` (-1: padding).
+__device__ __forceinline__ int reduce_slot(int lane) {
+    const int base = (lane & 16) ? 5 : 0;   // values kept after the first round
+    int l3[3];
+    if (lane & 8) { l3[0] = base + 3; l3[1] = base + 4; l3[2] = -1; }
+    else { l3[0] = base; l3[1] = base + 1; l3[2] = base + 2; }
+    int l2[2];
+    if (lane & 4) { l2[0] = l3[2]; l2[1] = -1; }
+    else { l2[0] = l3[0]; l2[1] = l3[1]; }
+    const int slot = (lane & 2) ? l2[1] : l2[0];
+    return slot > 8 ? -1 : slot;
 }
 
 // True when no pixel of the warp's tile rows [wy0, wy1] can be within the splat's box: the warp
@@ -261,6 +306,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     __syncthreads();
     const uint32_t count = min(s_max, len);   // last positions never exceed the tile's list
     uint32_t nblend = 0;
+    const int lane = threadIdx.x & 31;
+    const int slot = reduce_slot(lane);
 
     for (int bend = (int)count; bend > 0; bend -= a.batch) {
         const int nb = min(a.batch, bend);
@@ -339,16 +386,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                     atomicAdd(dst + 8, g[8]);
                 }
             } else {
-#pragma unroll
-                for (int v = 0; v < 9; ++v) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) g[v] += __shfl_xor_sync(0xffffffffu, g[v], o);
-                }
-                if ((threadIdx.x & 31) == 0) {
-                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(k1 * g[0], k1 * g[1], k2 * g[2], k2 * g[3]));
-                    atomicAdd(reinterpret_cast<float4*>(dst) + 1, make_float4(k2 * g[4], ko * g[5], g[6], g[7]));
-                    atomicAdd(dst + 8, g[8]);
-                }
+                const float tot = warp_reduce9(g, lane);
+                if (slot >= 0 && !(lane & 1)) atomicAdd(dst + slot, tot * (slot < 2 ? k1 : slot < 5 ? k2 : slot == 5 ? ko : 1.0f));
             }
         }
     }
