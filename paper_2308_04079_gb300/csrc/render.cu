@@ -22,7 +22,7 @@
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
 //   Through a = o G (zero when clamped), with g = Sigma'^-1 d: d(power)/d(mean) = g and
 //   d(power)/d(Sigma') = g g^T / 2.  A thread sums its pixels' dL/d(mean2D, Sigma', opacity,
-//   colour); when more than eight lanes of a warp contributed, the warp sums its lanes with a
+//   colour); when more than twelve lanes of a warp contributed, the warp sums its lanes with a
 //   transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals with one atomic
 //   instruction, otherwise the contributing lanes add their own sums.
 //
@@ -41,7 +41,7 @@ constexpr float kScaleLog2 = 0.84932180028801907f;
 // 1 / kScaleLog2^2 = 2 ln 2: converts scaled (p, q) products back to natural units.
 constexpr float kTwoLn2 = 1.3862943611198906f;
 // At most this many contributing lanes add their own sums instead of a warp reduction.
-constexpr int kDirectLanes = 8;
+constexpr int kDirectLanes = 12;
 
 struct Staged {
     float4 a;   // (ox, oy, thr, lo): tile-relative offset, skip threshold, log2(opacity)
