@@ -330,6 +330,10 @@ def run_ours(args, rank, world, local_rank):
                  "status": sorted(set(int(c) for c in codes.values()))}
         del trainer, model
 
+    density = None
+    if not args.no_batch:
+        density = run_density(args, dev, stream, hbm_peak, peak_kind)
+
     batch = multi = None
     if not args.no_batch and args.gaussians == CONFIG3_N:
         batch = run_batch(args, dev)
@@ -350,11 +354,73 @@ def run_ours(args, rank, world, local_rank):
                    "blended_pairs": blended,
                    "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "batch": batch, "multi_scene": multi,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "density_control": density, "batch": batch,
+        "multi_scene": multi,
         "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_density(args, dev, stream, hbm_peak, peak_kind):
+    """One refinement (Sec. 5.2) of a model of the bench's size: gs_densify over the optimiser
+    state of synthetic.density_state (every decision in play), timed with CUDA events; the
+    roofline counts the bytes the compaction must move."""
+    import torch
+    import synthetic as S
+    from paper_2308_04079_gb300 import _abi
+    from paper_2308_04079_gb300.density import PARAMS, _arrays
+    n = args.gaussians
+    f, m, v, acc, cnt, mr, z = S.density_state(9000, n)
+    up = lambda a: torch.from_numpy(a).to(dev)
+    src, sm, sv = ({k: up(d[k]) for k in PARAMS} for d in (f, m, v))
+    ta, tc, tm, tz = up(acc), up(cnt), up(mr), up(z)
+    del f, m, v, acc, cnt, mr, z
+    cap = 2 * n
+    out, om, ov = ({k: torch.empty((cap,) + tuple(src[k].shape[1:]), dtype=torch.float32, device=dev)
+                    for k in PARAMS} for _ in range(3))
+    stats = [torch.empty(cap, dtype=torch.float32, device=dev) for _ in range(3)]
+    scales = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    opac = torch.empty(cap, dtype=torch.float32, device=dev)
+    result = torch.zeros(2, dtype=torch.int32, device=dev)
+    sb = _abi.gs_densify_scratch_size(n)
+    scratch = torch.empty(sb + 256, dtype=torch.uint8, device=dev)
+    sp = scratch.data_ptr() + (-scratch.data_ptr()) % 256
+    cfg = _abi.gs_density_config()
+    cfg.grad_threshold, cfg.min_opacity, cfg.split_scale = 2e-4, 0.005, 0.03
+    cfg.max_world_scale, cfg.max_screen_radius, cfg.split_factor = 0.3, 20.0, 1.6
+    sh_floats = int(src["sh"][0].numel())
+    args_ = (cfg, n, sh_floats, _arrays(src), _arrays(sm), _arrays(sv), ta.data_ptr(), tc.data_ptr(), tm.data_ptr(),
+             tz.data_ptr(), _arrays(out), _arrays(om), _arrays(ov), stats[0].data_ptr(), stats[1].data_ptr(),
+             stats[2].data_ptr(), scales.data_ptr(), opac.data_ptr(), cap, result.data_ptr(), sp, sb,
+             stream.cuda_stream)
+    for _ in range(3):
+        _abi.gs_densify(*args_)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        _abi.gs_densify(*args_)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    rows, flags = (int(x) for x in result.cpu())
+    # decisions, from the kernel's own outputs: rows = keep + 2 (clone + split)
+    opac_thr = float(np.float32(np.log(0.005 / 0.995)))
+    lo = src["logit_opacities"]
+    smax = src["log_scales"].max(dim=1).values
+    pruned = int(((lo < opac_thr) | (smax > float(np.float32(np.log(0.3)))) | (tm > 20.0)).sum().item())
+    dens = (tc > 0) & (ta / torch.where(tc > 0, tc, torch.ones_like(tc)) > float(np.float32(2e-4)))
+    keep_mask = ~((lo < opac_thr) | (smax > float(np.float32(np.log(0.3)))) | (tm > 20.0))
+    split = int((dens & keep_mask & (smax > float(np.float32(np.log(0.03))))).sum().item())
+    row_bytes = 3 * (4 * (3 + 3 + 4 + 1) + 4 * sh_floats)      # value + 2 moments of the 5 tensors
+    alg = n * 28 + (n - pruned) * (row_bytes - 16) + split * 24 + rows * (row_bytes + 12 + 16)
+    ach = alg / (ms * 1e-3) / 1e9
+    return {"what": "gs_densify: prune / clone / split compaction of the parameters and Adam moments "
+                    "(Sec. 5.2), synthetic optimiser state", "gaussians": n, "rows_out": rows, "flags": flags,
+            "pruned": pruned, "split": split, "ms": round(ms, 4), "algorithmic_bytes": int(alg),
+            "achieved_gbs": round(ach, 1), "frac": round(ach / hbm_peak, 4), "peak": hbm_peak,
+            "peak_kind": f"{peak_kind} hbm_gbs", "l2": "inputs larger than L2"}
 
 
 def run_batch(args, dev):

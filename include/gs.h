@@ -293,6 +293,91 @@ typedef struct gs_adam_group {
 gs_status gs_adam_step(const gs_adam_group* groups, int count, float beta1, float beta2, float eps, int step,
                        cudaStream_t stream);
 
+/* ---- Adaptive density control (Sec. 5.2, the refinement step of Algorithm 1) ---------------
+ * Between refinements the caller accumulates, per view, the magnitude of each Gaussian's
+ * view-space positional gradient (gs_density_stats); a refinement (gs_densify) then removes
+ * transparent or oversized Gaussians, clones small ones with a large mean gradient
+ * (under-reconstruction) and splits large ones (over-reconstruction) into two children
+ * sampled from the original Gaussian with their scale divided by phi (the paper: 1.6).
+ * gs_opacity_reset lowers every opacity to a small value (the paper: every 3000 iterations).
+ * Parameters are the raw tensors the optimiser updates: log scales (scale = exp) and logit
+ * opacities (opacity = sigmoid). */
+
+/* The five parameter tensors of a model (device float arrays, rows contiguous):
+ *   means [n, 3], log_scales [n, 3], quats [n, 4] (q_r, q_i, q_j, q_k), logit_opacities [n],
+ *   sh [n, sh_floats] (the SH coefficients of one Gaussian, any layout). */
+typedef struct gs_param_arrays {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* logit_opacities;
+    float* sh;
+} gs_param_arrays;
+
+typedef struct gs_density_config {
+    float grad_threshold;     /* tau_pos: densify when the mean view-space gradient > this (0.0002) */
+    float min_opacity;        /* epsilon_alpha: prune when opacity < this, in (0, 1)              */
+    float split_scale;        /* tau_S, world units: split when the largest scale > this, else clone */
+    float max_world_scale;    /* prune when the largest scale > this; <= 0 disables               */
+    float max_screen_radius;  /* prune when the largest screen radius seen > this (px); <= 0 disables */
+    float split_factor;       /* phi: split children have scale / phi (1.6)                       */
+} gs_density_config;
+
+/* One view's statistics (after gs_render_backward of `frame`): for every Gaussian that the
+ * frame's preprocessing did not cull (screen radius > 0),
+ *   grad_accum[i] += |(g_u W / 2, g_v H / 2)|   (the mean gradient in normalised device
+ *                                                 coordinates, g = mean2d_grad[i] in pixels),
+ *   grad_count[i] += 1,   max_radius[i] = max(max_radius[i], screen radius).
+ *   mean2d_grad   device float[n, 2], the gradients' mean2d output of gs_render_backward
+ *   grad_accum, grad_count   device float[n], updated in place
+ *   max_radius    device float[n] or NULL, updated in place
+ * Asynchronous.  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_density_stats(const gs_frame* frame, const float* mean2d_grad, float* grad_accum, float* grad_count,
+                           float* max_radius, cudaStream_t stream);
+
+/* Scratch bytes gs_densify needs for n Gaussians (0 for n < 0). */
+size_t gs_densify_scratch_size(int n);
+
+/* One refinement.  Decision of Gaussian i, in fp32 (thresholds moved to the raw domains on
+ * the host in double and rounded to fp32: logit(min_opacity), ln(split_scale),
+ * ln(max_world_scale)), every comparison strict:
+ *   prune  if sigmoid(logit_opacity) < min_opacity, or max scale > max_world_scale (when
+ *          enabled), or max_radius[i] > max_screen_radius (when enabled);
+ *   else densify if grad_count[i] > 0 and grad_accum[i] / grad_count[i] > grad_threshold:
+ *          split if max scale > split_scale, else clone;
+ *   else keep.
+ * Outputs (rows in source order, each source's rows adjacent): keep -> the row with its Adam
+ * moments; clone -> the row with its moments, then an exact copy with zero moments; split ->
+ * two children with means mu + R(q / |q|) diag(exp(log_scales)) z_k (z_k = normals[i][k],
+ * standard normal draws supplied by the caller; identity rotation for q = 0), log_scales
+ * lowered by ln(split_factor), the other tensors copied, zero moments.  The output statistics
+ * (when given) are zeroed.
+ *   params, adam_m, adam_v   input tensors (read only) of n rows
+ *   normals       device float[n, 2, 3] (rows of non-split Gaussians are not read)
+ *   out_*         output tensors with room for out_capacity rows; they must not overlap the
+ *                 inputs.  out_grad_accum, out_grad_count, out_max_radius may be NULL.
+ *   out_scales    device float[out_capacity, 3] or NULL: exp of the output log_scales
+ *   out_opacities device float[out_capacity] or NULL: sigmoid of the output logit_opacities
+ *   result        device uint32[2]: [0] rows produced (may exceed out_capacity), [1] flags
+ *                 (bit 0: out_capacity exceeded -- rows past it are not written; bit 1: a
+ *                 bounded spin-wait gave up -- outputs invalid)
+ *   scratch       device, 256-byte aligned, >= gs_densify_scratch_size(n) bytes
+ * Asynchronous (cudaMemsetAsync + one kernel).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+gs_status gs_densify(const gs_density_config* config, int n, int sh_floats, const gs_param_arrays* params,
+                     const gs_param_arrays* adam_m, const gs_param_arrays* adam_v, const float* grad_accum,
+                     const float* grad_count, const float* max_radius, const float* normals,
+                     const gs_param_arrays* out_params, const gs_param_arrays* out_m, const gs_param_arrays* out_v,
+                     float* out_grad_accum, float* out_grad_count, float* out_max_radius, float* out_scales,
+                     float* out_opacities, int out_capacity, uint32_t* result, void* scratch,
+                     size_t scratch_bytes, cudaStream_t stream);
+
+/* Opacity reset: logit_opacities[i] = min(logit_opacities[i], fp32(logit(max_opacity))); when
+ * given, the opacity moments adam_m, adam_v (device float[n]) are zeroed and opacities
+ * (device float[n]) receives sigmoid of the new values.
+ * Errors: GS_ERR_INVALID_ARG (max_opacity outside (0, 1)), GS_ERR_CUDA. */
+gs_status gs_opacity_reset(float* logit_opacities, float* adam_m, float* adam_v, float* opacities, int n,
+                           float max_opacity, cudaStream_t stream);
+
 /* Depth ordering without workspace or allocation (no counterpart in the paper; it is the
  * first phase of the GS_SORT_TWO_PHASE binning schedule offered on its own).
  * Writes order[0..n): the indices i with radius[i] > 0 sorted by the fp32 bits of depth[i]

@@ -21,7 +21,8 @@ and the 3000-iteration opacity reset; everything else below is a reading):
   * split = two children in place of the original, each with the original's mean plus
     R(q) diag(s) z for a standard normal draw z (the original Gaussian as the sampling
     density, pre-split scale s), raw log-scale lowered by ln(phi) (scale divided by phi), the
-    other attributes copied and optimiser moments zero;
+    other attributes copied and optimiser moments zero (a zero quaternion, which the renderer
+    culls in every view, splits with the identity rotation);
   * outputs keep the source order, each source's outputs adjacent;
   * decisions (integers from floating point) are taken in fp32 as the kernels take them:
     opacity against epsilon_alpha in the raw (logit) domain, scales in the raw (log) domain,
@@ -134,7 +135,8 @@ def densify(params: dict, m: dict, v: dict, accum, count, max_radius, normals, c
             continue
         # split: sample both children from N(mu, R diag(s)^2 R^T)
         q = src["quats"]
-        R = quat_to_rot(q / np.linalg.norm(q))   # the renderer's rotation R(q / |q|)
+        qn = np.linalg.norm(q)
+        R = quat_to_rot(q / qn) if qn > 0 else np.eye(3)   # the renderer's rotation R(q / |q|)
         s = np.exp(src["log_scales"])
         for child in range(2):
             for k in PARAMS:
@@ -159,6 +161,12 @@ def densify(params: dict, m: dict, v: dict, accum, count, max_radius, normals, c
 
 def output_count(code) -> int:
     return int(sum(OUTPUTS[int(c)] for c in np.asarray(code).reshape(-1)))
+
+
+def output_offsets(code) -> np.ndarray:
+    """First output row of every source: the number of rows its predecessors produce."""
+    counts = np.array([OUTPUTS[int(c)] for c in np.asarray(code).reshape(-1)], np.int64)
+    return np.concatenate([[0], np.cumsum(counts)[:-1]]) if counts.size else counts
 
 
 def reset_opacity(logit_opacities, max_opacity: float = 0.01):

@@ -78,6 +78,16 @@ class gs_adam_group(ctypes.Structure):
 
 GS_ACT_NONE, GS_ACT_EXP, GS_ACT_SIGMOID = 0, 1, 2
 
+
+class gs_param_arrays(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("log_scales", c_void_p), ("quats", c_void_p), ("logit_opacities", c_void_p),
+                ("sh", c_void_p)]
+
+
+class gs_density_config(ctypes.Structure):
+    _fields_ = [("grad_threshold", c_float), ("min_opacity", c_float), ("split_scale", c_float),
+                ("max_world_scale", c_float), ("max_screen_radius", c_float), ("split_factor", c_float)]
+
 # (name, restype, argtypes) of every entry point declared in include/gs.h
 SIGNATURES = [
     ("gs_default_config", None, [ctypes.POINTER(gs_raster_config)]),
@@ -108,6 +118,14 @@ SIGNATURES = [
     ("gs_loss_l1_dssim", c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_void_p, c_size_t, c_void_p, c_void_p,
                                  c_void_p]),
     ("gs_adam_step", c_int, [ctypes.POINTER(gs_adam_group), c_int, c_float, c_float, c_float, c_int, c_void_p]),
+    ("gs_density_stats", c_int, [ctypes.POINTER(gs_frame), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("gs_densify_scratch_size", c_size_t, [c_int]),
+    ("gs_densify", c_int, [ctypes.POINTER(gs_density_config), c_int, c_int, ctypes.POINTER(gs_param_arrays),
+                           ctypes.POINTER(gs_param_arrays), ctypes.POINTER(gs_param_arrays), c_void_p, c_void_p,
+                           c_void_p, c_void_p, ctypes.POINTER(gs_param_arrays), ctypes.POINTER(gs_param_arrays),
+                           ctypes.POINTER(gs_param_arrays), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                           c_void_p, c_void_p, c_size_t, c_void_p]),
+    ("gs_opacity_reset", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_float, c_void_p]),
     ("gs_depth_order_static", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("gs_status_string", ctypes.c_char_p, [c_int]),
 ]
@@ -268,3 +286,33 @@ def gs_loss_l1_dssim(img: int, target: int, width: int, height: int, lam: float,
 def gs_adam_step(groups, beta1: float, beta2: float, eps: float, step: int, stream: int) -> None:
     arr = (gs_adam_group * len(groups))(*groups)
     _check(load().gs_adam_step(arr, len(groups), beta1, beta2, eps, step, stream), "gs_adam_step")
+
+
+def gs_density_stats(frame, mean2d_grad: int, grad_accum: int, grad_count: int, max_radius: int | None,
+                     stream: int) -> None:
+    _check(load().gs_density_stats(ctypes.byref(frame), mean2d_grad, grad_accum, grad_count, max_radius, stream),
+           "gs_density_stats")
+
+
+def gs_densify_scratch_size(n: int) -> int:
+    return int(load().gs_densify_scratch_size(n))
+
+
+def gs_densify(cfg: gs_density_config, n: int, sh_floats: int, params: gs_param_arrays, adam_m: gs_param_arrays,
+               adam_v: gs_param_arrays, grad_accum: int, grad_count: int, max_radius: int | None, normals: int,
+               out_params: gs_param_arrays, out_m: gs_param_arrays, out_v: gs_param_arrays,
+               out_grad_accum: int | None, out_grad_count: int | None, out_max_radius: int | None,
+               out_scales: int | None, out_opacities: int | None, out_capacity: int, result: int, scratch: int,
+               scratch_bytes: int, stream: int) -> None:
+    _check(load().gs_densify(ctypes.byref(cfg), n, sh_floats, ctypes.byref(params), ctypes.byref(adam_m),
+                             ctypes.byref(adam_v), grad_accum, grad_count, max_radius, normals,
+                             ctypes.byref(out_params), ctypes.byref(out_m), ctypes.byref(out_v), out_grad_accum,
+                             out_grad_count, out_max_radius, out_scales, out_opacities, out_capacity, result, scratch,
+                             scratch_bytes, stream),
+           "gs_densify")
+
+
+def gs_opacity_reset(logit_opacities: int, adam_m: int | None, adam_v: int | None, opacities: int | None, n: int,
+                     max_opacity: float, stream: int) -> None:
+    _check(load().gs_opacity_reset(logit_opacities, adam_m, adam_v, opacities, n, max_opacity, stream),
+           "gs_opacity_reset")

@@ -1,9 +1,10 @@
-"""Training step around the rasterizer (Sec. 5.1, Algorithm 1 without density control):
-render the Gaussians' activated parameters, L = (1 - lambda) L1 + lambda (1 - SSIM) against a
-target view, back-propagate through the rasterizer, and update the raw parameters with Adam
-(sigmoid opacities, exp scales, exponentially decaying position learning rate).  Every step
-runs in the library's kernels: gs_preprocess, gs_bin_sort, gs_render_forward,
-gs_render_backward, gs_loss_l1_dssim and gs_adam_step."""
+"""Training step around the rasterizer (Sec. 5.1, Algorithm 1): render the Gaussians'
+activated parameters, L = (1 - lambda) L1 + lambda (1 - SSIM) against a target view,
+back-propagate through the rasterizer, and update the raw parameters with Adam (sigmoid
+opacities, exp scales, exponentially decaying position learning rate); with a DensityControl
+attached, also the gradient statistics and the refinement of Sec. 5.2.  Every step runs in the
+library's kernels: gs_preprocess, gs_bin_sort, gs_render_forward, gs_render_backward,
+gs_loss_l1_dssim, gs_adam_step (and gs_density_stats, gs_densify, gs_opacity_reset)."""
 from __future__ import annotations
 
 import math
@@ -92,8 +93,9 @@ class Trainer:
     """One training iteration per call of step(camera, target): forward, loss, backward, Adam."""
 
     def __init__(self, model: GaussianModel, lr: dict | None = None, lam: float = 0.2, betas=(0.9, 0.999),
-                 eps: float = 1e-15, cfg=None, bg=(0.0, 0.0, 0.0)):
+                 eps: float = 1e-15, cfg=None, bg=(0.0, 0.0, 0.0), density=None):
         self.model = model
+        self.density = density
         self.lr = dict(DEFAULT_LR, **(lr or {}))
         self.lam, self.betas, self.eps = float(lam), betas, float(eps)
         self.cfg = cfg if cfg is not None else make_config()
@@ -129,6 +131,8 @@ class Trainer:
         fr.render_forward(self.bg, img, T, last)
         out = loss(img, target, dimg)
         fr.render_backward(g, self.bg, dimg, T, last, self.grads)
+        if self.density is not None:
+            self.density.accumulate(fr, self.grads["mean2d"])
         self.iteration += 1
         t = self.iteration
         lr = self.lr
@@ -148,6 +152,9 @@ class Trainer:
             grp.n, grp.lr, grp.activation = p.numel(), float(rate), act
             groups.append(grp)
         abi.gs_adam_step(groups, self.betas[0], self.betas[1], self.eps, t, _stream())
+        if self.density is not None and self.density.after_step(t):
+            self._frames.clear()      # workspaces and gradients are sized by the Gaussian count
+            self.grads = None
         return out
 
     def status(self):

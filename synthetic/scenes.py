@@ -292,3 +292,24 @@ def tiny_scene(seed: int, n: int = 64, width: int = 48, height: int = 40, deg: i
         sh[:, 1:, :] = 0.1 * rng.standard_normal((n, D - 1, 3))
     cam = look_at_camera([0.0, 0.0, -distance], [0.0, 0.0, 0.0], width, height, fov_x_deg)
     return _pack(means, log_s, quats, logit, sh, deg, name=f"tiny{seed}"), cam
+
+
+def density_state(seed: int, n: int, deg: int = 3):
+    """Optimiser state at a refinement (Sec. 5.2): raw parameters (log scales, logit
+    opacities), Adam moments, view-space gradient statistics and the two standard normal
+    draws per Gaussian that a split consumes.  The spreads put every decision (prune, keep,
+    clone, split) in play at the default thresholds with tau_S around 0.01 to 0.05."""
+    rng = _rng(seed)
+    D = (deg + 1) ** 2
+    params = dict(means=rng.uniform(-3, 3, (n, 3)), log_scales=rng.normal(-4.0, 1.2, (n, 3)),
+                  quats=_unit_quats(rng, n) * rng.uniform(0.5, 2.0, (n, 1)),
+                  logit_opacities=rng.normal(-1.0, 2.5, n), sh=0.3 * rng.standard_normal((n, D, 3)))
+    m = {k: 1e-3 * rng.standard_normal(a.shape) for k, a in params.items()}
+    v = {k: 1e-6 * rng.random(a.shape) for k, a in params.items()}
+    count = rng.integers(0, 40, n).astype(np.float64)
+    accum = count * rng.lognormal(np.log(2e-4), 0.8, n)
+    max_radius = np.floor(rng.exponential(8.0, n)) * (count > 0)
+    normals = rng.standard_normal((n, 2, 3))
+    f = {k: _f32(a) for k, a in params.items()}
+    return (f, {k: _f32(a) for k, a in m.items()}, {k: _f32(a) for k, a in v.items()}, _f32(accum), _f32(count),
+            _f32(max_radius), _f32(normals))

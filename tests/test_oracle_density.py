@@ -152,6 +152,9 @@ def test_outputs_follow_source_order():
     code, out, _, _ = od.densify(params, m, v, acc, cnt, np.zeros(n), z, cfg)
     want = np.repeat(np.arange(n), [od.OUTPUTS[int(c)] for c in code])
     assert np.array_equal(out["means"][:, 0], want)
+    offs = od.output_offsets(code)
+    live = code != od.PRUNE
+    assert np.array_equal(out["means"][offs[live], 0], np.arange(n)[live])
     assert len({int(c) for c in code}) == 4
     assert out["means"].shape[0] == od.output_count(code)
 
