@@ -305,7 +305,7 @@ gs_status gs_adam_step(const gs_adam_group* groups, int count, float beta1, floa
 
 /* The five parameter tensors of a model (device float arrays, rows contiguous):
  *   means [n, 3], log_scales [n, 3], quats [n, 4] (q_r, q_i, q_j, q_k), logit_opacities [n],
- *   sh [n, sh_floats] (the SH coefficients of one Gaussian, any layout). */
+ *   sh [n, sh_floats] (the SH coefficients of one Gaussian, any layout; sh_floats <= 192). */
 typedef struct gs_param_arrays {
     float* means;
     float* log_scales;
@@ -362,7 +362,8 @@ size_t gs_densify_scratch_size(int n);
  *                 (bit 0: out_capacity exceeded -- rows past it are not written; bit 1: a
  *                 bounded spin-wait gave up -- outputs invalid)
  *   scratch       device, 256-byte aligned, >= gs_densify_scratch_size(n) bytes
- * Asynchronous (cudaMemsetAsync + one kernel).  Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
+ * Asynchronous (cudaMemsetAsync + two kernels).  Errors: GS_ERR_INVALID_ARG (also for
+ * n > 2^29 - 1 or sh_floats > 192), GS_ERR_CUDA. */
 gs_status gs_densify(const gs_density_config* config, int n, int sh_floats, const gs_param_arrays* params,
                      const gs_param_arrays* adam_m, const gs_param_arrays* adam_v, const float* grad_accum,
                      const float* grad_count, const float* max_radius, const float* normals,
