@@ -16,6 +16,11 @@ Functions (each a thin ctypes marshaller around ``gs_oracle.c``):
 * :func:`render_backward`  analytic FP64 gradients (Sec. 6 traversal, App. A chain rule).
 * :func:`sh_eval`          real spherical-harmonic basis, bands 0..3, and its gradient.
 * :func:`quat_to_rot`      eq. quat of App. A.
+* :func:`render_forward_isotropic`, :func:`render_backward_isotropic`  the isotropic ablation
+                           of Sec. 7.3 (one scale per Gaussian) through the definitions above.
+
+The Limited-BW ablation of Sec. 7.3 is ``cfg_array(grad_limit=N)``: gradients reach only the
+N front-most blended Gaussians of each pixel.
 
 Every pixel/Gaussian decision that lies within a relative margin of its threshold is
 reported as ambiguous (``pix_amb``, ``gauss_amb``), see the bit constants below.
@@ -53,6 +58,7 @@ DEFAULT_CFG = dict(
     eps_T=1e-3,                    # ambiguity margin, transmittance stop decision (relative)
     T_impact=1e-4 / (2.0 / 255.0), # skip flips behind less light cannot move a pixel by 1e-4
     T_grad=1e-3,                   # flips behind less light are negligible for gradients
+    grad_limit=0,                  # > 0: gradients for the N front-most blended Gaussians only
 )
 
 _lib = None
@@ -119,7 +125,8 @@ def cfg_array(**overrides) -> np.ndarray:
         c[k] = v
     return np.array([c["tile_w"], c["tile_h"], c["alpha_min"], c["alpha_max"], c["T_min"],
                      c["dilation"], c["guard"], c["extent"], c["radius_max"], c["eps_geom"],
-                     c["eps_alpha"], c["eps_T"], c["T_impact"], c["T_grad"]], dtype=np.float64)
+                     c["eps_alpha"], c["eps_T"], c["T_impact"], c["T_grad"], c["grad_limit"]],
+                    dtype=np.float64)
 
 
 def _gauss_args(g):
@@ -228,6 +235,34 @@ def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None 
                                 _p(out["opacities"], D), _p(out["sh"], D), _p(out["uv"], D), _p(out["conic"], D),
                                 _p(out["rgb"], D), _p(out["cov2d"], D), _p(out["pix_amb"], ctypes.c_uint8),
                                 _p(out["gauss_amb"], ctypes.c_uint32))
+    return out
+
+
+class _Anisotropic:
+    """An isotropic parameter set seen through the anisotropic definition."""
+
+    def __init__(self, g):
+        n = int(np.asarray(g.means).shape[0])
+        s = _f64(g.scales).reshape(n)
+        self.means, self.opacities, self.sh, self.sh_degree = g.means, g.opacities, g.sh, g.sh_degree
+        self.scales = np.repeat(s[:, None], 3, axis=1)
+        self.quats = np.tile(np.array([1.0, 0.0, 0.0, 0.0]), (n, 1))
+
+
+def render_forward_isotropic(g, cam, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
+    """The isotropic ablation of Sec. 7.3: one scale s per Gaussian for all three axes, so
+    Sigma = s^2 I whatever the rotation; rendered as the anisotropic Gaussian with scales
+    (s, s, s) and the identity rotation (g.scales is [n]; g.quats is not read)."""
+    return render_forward(_Anisotropic(g), cam, bg, cfg, tile_mask)
+
+
+def render_backward_isotropic(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None,
+                              tile_mask=None) -> dict:
+    """Gradients of the isotropic parameterisation: by the chain rule through s -> (s, s, s),
+    dL/ds is the sum of the anisotropic dL/ds_k; the rotation has no effect (no quats entry)."""
+    out = render_backward(_Anisotropic(g), cam, dL_dimg, bg, cfg, tile_mask)
+    out["scales"] = out["scales"].sum(axis=1)
+    del out["quats"]
     return out
 
 

@@ -68,6 +68,8 @@ typedef struct {
     double T_impact;    /* skip flips in front of which less light than this remains cannot move
                            the pixel by the image tolerance: alpha_min * T * 2 < tolerance */
     double T_grad;      /* a flipped decision behind less light than this is negligible for gradients */
+    int grad_limit;     /* > 0: only the grad_limit front-most blended Gaussians of a pixel receive
+                           gradients (Limited-BW ablation, Sec. 7.3); 0: all of them */
 } ocfg;
 
 static void read_cam(const double* c, ocam* o) {
@@ -84,6 +86,7 @@ static void read_cfg(const double* c, ocfg* o) {
     o->dilation = c[5]; o->guard = c[6]; o->extent = c[7];
     o->radius_max = (int)c[8]; o->eps_geom = c[9]; o->eps_alpha = c[10];
     o->eps_T = c[11]; o->T_impact = c[12]; o->T_grad = c[13];
+    o->grad_limit = (int)c[14];
 }
 
 /* Ambiguity bits (per Gaussian). */
@@ -752,6 +755,11 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                     double rgb[3], Tf; int last; unsigned flags;
                     int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, NULL, &flags, rec, out_gauss_amb);
                     if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
+                    /* with a gradient limit, one decision near its threshold in front can move the
+                       limit by one place: the Gaussians at front ranks N-1 and N may swap roles */
+                    if (S.cfg.grad_limit > 0 && (flags & PIX_ANY) && out_gauss_amb)
+                        for (int k = S.cfg.grad_limit - 1; k <= S.cfg.grad_limit && k < nrec; ++k)
+                            if (k >= 0) mark(out_gauss_amb, rec[k].idx, AMB_PIXEL);
                     double dC[3] = {dL_dimg[p], dL_dimg[P + p], dL_dimg[2 * P + p]};
                     /* R = colour accumulated behind the current Gaussian, normalised by the
                        transmittance in front of it; starts with the background. */
@@ -759,12 +767,16 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                     for (int k = nrec - 1; k >= 0; --k) {
                         const contrib_t* c = &rec[k];
                         const ogauss* g = &S.g[c->idx];
+                        /* rec[k] is the k-th blended Gaussian from the front; with a gradient limit
+                           N only k < N receive gradients, while R still takes in every one */
+                        const int grad = S.cfg.grad_limit <= 0 || k < S.cfg.grad_limit;
                         double dL_dalpha = 0.0;
                         for (int ch = 0; ch < 3; ++ch) {
-                            atomic_add(&d_rgb[3 * c->idx + ch], c->T * c->alpha * dC[ch]);
+                            if (grad) atomic_add(&d_rgb[3 * c->idx + ch], c->T * c->alpha * dC[ch]);
                             dL_dalpha += c->T * (g->rgb[ch] - Rb[ch]) * dC[ch];
                             Rb[ch] = c->alpha * g->rgb[ch] + (1.0 - c->alpha) * Rb[ch];
                         }
+                        if (!grad) continue;
                         if (c->clamped) continue;   /* derivative of min(o G, 0.99) is 0 there */
                         double o = S.opac[c->idx];
                         atomic_add(&d_opac[c->idx], c->G * dL_dalpha);
