@@ -559,11 +559,13 @@ static void mark(unsigned* gamb, int32_t i, unsigned bit) {
  * threshold (see the AMB_* / PIX_* bits).
  */
 static int pixel_forward(const oscene* S, int t, int px, int py, const double* bg, double* out_rgb, double* out_T,
-                         int* out_last, int* out_last_id, unsigned* out_flags, contrib_t* rec, unsigned* gamb) {
+                         int* out_last, int* out_last_id, unsigned* out_flags, contrib_t* rec, unsigned* gamb,
+                         int* out_first_amb) {
     const ocfg* cfg = &S->cfg;
     double pxc = px + 0.5, pyc = py + 0.5;
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     int last = 0, last_id = -1, nrec = 0;
+    int first_amb = -1;   /* blended Gaussians in front of the first decision near its threshold */
     unsigned flags = 0;
     int64_t a = S->tile_start[t], b = S->tile_start[t + 1];
     uint32_t prev_key = 0;
@@ -604,11 +606,13 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         }
         int clamped = oG > cfg->alpha_max;
         double alpha = clamped ? cfg->alpha_max : oG;
+        if (first_amb < 0 && (flags & PIX_ANY)) first_amb = nrec;
         if (alpha < cfg->alpha_min) continue;                   /* skip (App. C) */
         double test_T = T * (1.0 - alpha);
         if (near_threshold(test_T, cfg->T_min, cfg->eps_T)) {
             flags |= PIX_DECISION | PIX_ANY;
             if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);   /* its inclusion may flip */
+            if (first_amb < 0) first_amb = nrec;
         }
         if (test_T < cfg->T_min) break;                         /* stop before exceeding 0.9999 */
         for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * alpha * T;
@@ -630,6 +634,7 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha)) {
             flags |= PIX_DECISION | PIX_ANY;
             mark(gamb, gi, AMB_PIXEL);
+            first_amb = 0;   /* its place in the order is unknown */
         }
     }
     for (int ch = 0; ch < 3; ++ch) out_rgb[ch] = C[ch] + T * bg[ch];
@@ -637,6 +642,7 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
     *out_last = last;
     if (out_last_id) *out_last_id = last_id;
     *out_flags = flags;
+    if (out_first_amb) *out_first_amb = first_amb;
     return nrec;
 }
 
@@ -697,7 +703,7 @@ void orc_render_forward(long n, const double* means, const double* scales, const
                 int px = tx * S.cfg.tile_w + lx, py = ty * S.cfg.tile_h + ly;
                 if (px >= W || py >= H) continue;
                 double rgb[3], Tf; int last, last_id; unsigned flags;
-                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &last_id, &flags, NULL, out_gauss_amb);
+                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &last_id, &flags, NULL, out_gauss_amb, NULL);
                 size_t p = (size_t)py * W + px;
                 if (out_last_id) out_last_id[p] = last_id;
                 for (int ch = 0; ch < 3; ++ch) out_img[ch * P + p] = rgb[ch];
@@ -753,11 +759,14 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                     if (px >= W || py >= H) continue;
                     size_t p = (size_t)py * W + px;
                     double rgb[3], Tf; int last; unsigned flags;
-                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, NULL, &flags, rec, out_gauss_amb);
+                    int first_amb;
+                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, NULL, &flags, rec, out_gauss_amb,
+                                             &first_amb);
                     if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
-                    /* with a gradient limit, one decision near its threshold in front can move the
-                       limit by one place: the Gaussians at front ranks N-1 and N may swap roles */
-                    if (S.cfg.grad_limit > 0 && (flags & PIX_ANY) && out_gauss_amb)
+                    /* with a gradient limit N, a decision near its threshold among the first N
+                       blended Gaussians (order, skip, stop or membership) can move the limit by one
+                       place: the Gaussians at front ranks N-1 and N may swap roles */
+                    if (S.cfg.grad_limit > 0 && first_amb >= 0 && first_amb < S.cfg.grad_limit && out_gauss_amb)
                         for (int k = S.cfg.grad_limit - 1; k <= S.cfg.grad_limit && k < nrec; ++k)
                             if (k >= 0) mark(out_gauss_amb, rec[k].idx, AMB_PIXEL);
                     double dC[3] = {dL_dimg[p], dL_dimg[P + p], dL_dimg[2 * P + p]};
