@@ -59,6 +59,7 @@ DEFAULT_CFG = dict(
     T_impact=1e-4 / (2.0 / 255.0), # skip flips behind less light cannot move a pixel by 1e-4
     T_grad=1e-3,                   # flips behind less light are negligible for gradients
     grad_limit=0,                  # > 0: gradients for the N front-most blended Gaussians only
+    eps_conic=1e-6,                # fp32 Cholesky factor of the conic: relative error, ~8 ulp
 )
 
 _lib = None
@@ -125,7 +126,7 @@ def cfg_array(**overrides) -> np.ndarray:
         c[k] = v
     return np.array([c["tile_w"], c["tile_h"], c["alpha_min"], c["alpha_max"], c["T_min"],
                      c["dilation"], c["guard"], c["extent"], c["radius_max"], c["eps_geom"],
-                     c["eps_alpha"], c["eps_T"], c["T_impact"], c["T_grad"], c["grad_limit"]],
+                     c["eps_alpha"], c["eps_T"], c["T_impact"], c["T_grad"], c["grad_limit"], c["eps_conic"]],
                     dtype=np.float64)
 
 

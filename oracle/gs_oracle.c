@@ -70,6 +70,7 @@ typedef struct {
     double T_grad;      /* a flipped decision behind less light than this is negligible for gradients */
     int grad_limit;     /* > 0: only the grad_limit front-most blended Gaussians of a pixel receive
                            gradients (Limited-BW ablation, Sec. 7.3); 0: all of them */
+    double eps_conic;   /* relative error of the fp32 Cholesky factor of the conic: see power_margin */
 } ocfg;
 
 static void read_cam(const double* c, ocam* o) {
@@ -87,6 +88,7 @@ static void read_cfg(const double* c, ocfg* o) {
     o->radius_max = (int)c[8]; o->eps_geom = c[9]; o->eps_alpha = c[10];
     o->eps_T = c[11]; o->T_impact = c[12]; o->T_grad = c[13];
     o->grad_limit = (int)c[14];
+    o->eps_conic = c[15];
 }
 
 /* Ambiguity bits (per Gaussian). */
@@ -546,6 +548,21 @@ static double eval_power(const ogauss* g, double pxc, double pyc, double* dx, do
     return -0.5 * (g->conic[0] * (*dx) * (*dx) + g->conic[2] * (*dy) * (*dy)) - g->conic[1] * (*dx) * (*dy);
 }
 
+/* Bound on the error of the power that fp32 conic entries can cause (see ocfg.eps_conic): with
+   the conic's Cholesky factor L (conic = L L^T, l11 = sqrt(a), l21 = b / l11, l22^2 = c - l21^2)
+   the power is -(p^2 + q^2) / 2, p = l11 dx + l21 dy, q = l22 dy; relative errors eps in the
+   factor's entries move it by at most eps (|p| (|l11 dx| + |l21 dy|) + q^2), which exceeds
+   eps |power| when the two terms of p cancel (an elongated splat, far from its centre). */
+static double power_margin(const ogauss* g, double dx, double dy, const ocfg* cfg) {
+    if (!(g->conic[0] > 0.0)) return 0.0;
+    double l11 = sqrt(g->conic[0]);
+    double l21 = g->conic[1] / l11;
+    double l22s = g->conic[2] - l21 * l21;
+    double l22 = l22s > 0.0 ? sqrt(l22s) : 0.0;
+    double p = l11 * dx + l21 * dy, q = l22 * dy;
+    return cfg->eps_conic * (fabs(p) * (fabs(l11 * dx) + fabs(l21 * dy)) + q * q);
+}
+
 static void mark(unsigned* gamb, int32_t i, unsigned bit) {
     if (!gamb) return;
 #pragma omp atomic
@@ -578,7 +595,8 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         double power = eval_power(g, pxc, pyc, &dx, &dy);
         double G = exp(power);
         double oG = S->opac[gi] * G;
-        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha)) {
+        const double eps_a = cfg->eps_alpha + power_margin(g, dx, dy, cfg);   /* relative, on o G */
+        if (oG >= cfg->alpha_min * (1.0 - eps_a)) {
             /* tile membership that an fp32 binning may decide differently */
             if ((g->amb & (AMB_CULL | AMB_RECT)) && !in_rect(g->rect_in, tx, ty)) {
                 flags |= PIX_ANY;
@@ -595,12 +613,12 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
             prev_key = key;
             prev_idx = gi;
         }
-        if (near_threshold(oG, cfg->alpha_min, cfg->eps_alpha)) {
+        if (near_threshold(oG, cfg->alpha_min, eps_a)) {
             flags |= PIX_ANY;
             if (T >= cfg->T_impact) flags |= PIX_DECISION;
             if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);
         }
-        if (near_threshold(oG, cfg->alpha_max, cfg->eps_alpha)) {
+        if (near_threshold(oG, cfg->alpha_max, eps_a)) {
             flags |= PIX_CLAMP;
             if (T >= cfg->T_grad) mark(gamb, gi, AMB_CLAMP);
         }
@@ -609,7 +627,8 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         if (first_amb < 0 && (flags & PIX_ANY)) first_amb = nrec;
         if (alpha < cfg->alpha_min) continue;                   /* skip (App. C) */
         double test_T = T * (1.0 - alpha);
-        if (near_threshold(test_T, cfg->T_min, cfg->eps_T)) {
+        /* (1 - alpha) is uncertain by alpha (eps_a - eps_alpha) relative to alpha */
+        if (near_threshold(test_T, cfg->T_min, cfg->eps_T + alpha / (1.0 - alpha) * (eps_a - cfg->eps_alpha))) {
             flags |= PIX_DECISION | PIX_ANY;
             if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);   /* its inclusion may flip */
             if (first_amb < 0) first_amb = nrec;
@@ -631,7 +650,7 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         const ogauss* g = &S->g[gi];
         double dx, dy;
         double oG = S->opac[gi] * exp(eval_power(g, pxc, pyc, &dx, &dy));
-        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha)) {
+        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha - power_margin(g, dx, dy, cfg))) {
             flags |= PIX_DECISION | PIX_ANY;
             mark(gamb, gi, AMB_PIXEL);
             first_amb = 0;   /* its place in the order is unknown */
