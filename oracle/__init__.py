@@ -59,7 +59,7 @@ DEFAULT_CFG = dict(
     T_impact=1e-4 / (2.0 / 255.0), # skip flips behind less light cannot move a pixel by 1e-4
     T_grad=1e-3,                   # flips behind less light are negligible for gradients
     grad_limit=0,                  # > 0: gradients for the N front-most blended Gaussians only
-    eps_conic=1e-6,                # fp32 Cholesky factor of the conic: relative error, ~8 ulp
+    eps_conic=5e-7,                # fp32 Cholesky factor of the conic: relative error, ~4 ulp
 )
 
 _lib = None
