@@ -330,9 +330,10 @@ def run_ours(args, rank, world, local_rank):
                  "status": sorted(set(int(c) for c in codes.values()))}
         del trainer, model
 
-    density = None
+    density = variants = None
     if not args.no_batch:
         density = run_density(args, dev, stream, hbm_peak, peak_kind)
+        variants = run_variants(args, dev, stream, g, cam, bg, d_dimg, ms_per_step)
 
     batch = multi = None
     if not args.no_batch and args.gaussians == CONFIG3_N:
@@ -354,7 +355,8 @@ def run_ours(args, rank, world, local_rank):
                    "blended_pairs": blended,
                    "l2": "inputs larger than L2 (708 MB of Gaussian parameters read per step)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "density_control": density, "batch": batch,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "density_control": density, "variants": variants,
+        "batch": batch,
         "multi_scene": multi,
         "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
     }
@@ -421,6 +423,51 @@ def run_density(args, dev, stream, hbm_peak, peak_kind):
             "pruned": pruned, "split": split, "ms": round(ms, 4), "algorithmic_bytes": int(alg),
             "achieved_gbs": round(ach, 1), "frac": round(ach / hbm_peak, 4), "peak": hbm_peak,
             "peak_kind": f"{peak_kind} hbm_gbs", "l2": "inputs larger than L2"}
+
+
+def run_variants(args, dev, stream, g, cam, bg, d_dimg, plain_ms):
+    """The ablation variants of Sec. 7.3 on the same frame: Limited-BW (gradients for the 10
+    front-most blended splats of each pixel) and isotropic Gaussians (one scale per Gaussian,
+    the geometric mean of the three axes), each a whole forward + backward step."""
+    import torch
+    from paper_2308_04079_gb300 import Frame, GaussianTensors, make_config
+    out = {}
+    iso_scales = np.exp(np.log(np.asarray(g.scales, np.float64)).mean(axis=1)).astype(np.float32)
+    for name, kw in (("limited_bw_n10", dict(grad_limit=10)), ("isotropic", dict(isotropic=True))):
+        cfg = make_config(sort_mode=args.sort_mode, **kw)
+        gt = GaussianTensors.from_numpy(g, device=dev)
+        if kw.get("isotropic"):
+            gt = GaussianTensors(gt.means, torch.from_numpy(iso_scales).to(dev), None, gt.opacities, gt.sh,
+                                 gt.sh_degree)
+        gt = gt.prepared()
+        fr = Frame(gt.n, cam, cfg, device=dev)
+        fr.ensure_binned(gt)
+        fr = Frame(gt.n, cam, cfg, capacity=int(fr.last_status.num_instances * 1.15) + 4096, device=dev)
+        img, T, last = fr.outputs()
+        grads = fr.new_grads(gt)
+
+        def step():
+            fr.preprocess(gt)
+            fr.bin_sort()
+            fr.render_forward(bg, img, T, last)
+            fr.render_backward(gt, bg, d_dimg, T, last, grads)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        code, st = fr.status()
+        ms = a.elapsed_time(b) / args.steps
+        out[name] = {"ms": round(ms, 4), "frames_per_s": round(1e3 / ms, 1), "vs_full_method": round(plain_ms / ms, 3),
+                     "instances": int(st.num_instances), "status": int(code)}
+        del fr, img, T, last, grads, gt
+    out["what"] = ("whole forward + backward step of the Sec. 7.3 ablations on the same frame; vs_full_method = "
+                   "the full method's ms / the variant's ms")
+    return out
 
 
 def run_batch(args, dev):

@@ -82,13 +82,20 @@ typedef struct gs_raster_config {
     float guard;              /* 1.3: reject |x/z| > guard * tan(fov_x/2) or |y/z| > guard * tan(fov_y/2) */
     float extent;             /* 3: screen radius = ceil(extent * sqrt(lambda_max(Sigma')))        */
     int tile_rule;            /* GS_TILES_REACH (default) or GS_TILES_RECT; same images either way */
+    int grad_limit;           /* > 0: only the grad_limit front-most blended splats of each pixel
+                                 receive gradients (the Limited-BW ablation of Sec. 7.3, N = 10 there);
+                                 0: all of them (the paper's method).  The image is unchanged.     */
+    int isotropic;            /* 1: one scale per Gaussian for all three axes (the isotropic ablation
+                                 of Sec. 7.3): scales and their gradients are [n], quaternions are
+                                 neither read nor differentiated (may be NULL); 0: anisotropic      */
 } gs_raster_config;
 
 /* Gaussian parameters (Sec. 4): device pointers, n rows each. */
 typedef struct gs_gaussians {
     const float* means;       /* [n, 3] world-space means mu                                      */
-    const float* scales;      /* [n, 3] s > 0                                                     */
-    const float* quats;       /* [n, 4] (q_r, q_i, q_j, q_k), 16-byte aligned                      */
+    const float* scales;      /* [n, 3] s > 0 ([n] with cfg.isotropic)                            */
+    const float* quats;       /* [n, 4] (q_r, q_i, q_j, q_k), 16-byte aligned (unused with
+                                 cfg.isotropic)                                                   */
     const float* opacities;   /* [n]    o in (0, 1)                                               */
     const float* sh;          /* [n, sh_stride, 3] SH coefficients, bands 0..sh_degree used       */
     int n;                    /* number of Gaussians, >= 0                                        */
@@ -99,8 +106,8 @@ typedef struct gs_gaussians {
 /* Gradient outputs of gs_render_backward: device pointers shaped like gs_gaussians. */
 typedef struct gs_gradients {
     float* means;             /* [n, 3]                                                         */
-    float* scales;            /* [n, 3]                                                         */
-    float* quats;             /* [n, 4]                                                         */
+    float* scales;            /* [n, 3] ([n] with cfg.isotropic: dL/ds summed over the axes)     */
+    float* quats;             /* [n, 4] (not written with cfg.isotropic, may be NULL)            */
     float* opacities;         /* [n]                                                            */
     float* sh;                /* [n, sh_stride, 3]; coefficients beyond the degree get 0         */
     float* mean2d;            /* [n, 2] dL/d(u, v) in pixels (view-space position gradient used
@@ -162,7 +169,8 @@ typedef struct gs_device_status {
 } gs_device_status;
 
 /* Fill cfg with the paper's constants: 16x16 tiles, batch 128, alpha in [1/255, 0.99],
- * T_min 1e-4, dilation 0.3, guard 1.3, extent 3, GS_SORT_TWO_PHASE, GS_TILES_REACH. */
+ * T_min 1e-4, dilation 0.3, guard 1.3, extent 3, GS_SORT_TWO_PHASE, GS_TILES_REACH, no gradient
+ * limit, anisotropic. */
 void gs_default_config(gs_raster_config* cfg);
 
 /* Workspace bytes for a frame; 0 if the arguments are invalid. */

@@ -40,7 +40,8 @@ class gs_camera(ctypes.Structure):
 class gs_raster_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("batch_depth", c_int), ("sort_mode", c_int),
                 ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float), ("dilation", c_float),
-                ("guard", c_float), ("extent", c_float), ("tile_rule", c_int)]
+                ("guard", c_float), ("extent", c_float), ("tile_rule", c_int), ("grad_limit", c_int),
+                ("isotropic", c_int)]
 
 
 class gs_gaussians(ctypes.Structure):

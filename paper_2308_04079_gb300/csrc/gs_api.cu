@@ -27,7 +27,7 @@ struct Layout {
     size_t gkey[2], gval[2];
     size_t pairs, scan_lb, sort_lb[2];
     size_t ikey[2], ival[2];
-    size_t ranges, grad2d, total;
+    size_t ranges, grad2d, pix_count, total;
     size_t sort_lb_rows, scan_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes, tile_passes, tile_digit_bits;
 };
@@ -40,6 +40,7 @@ bool valid_cfg(const gs_raster_config* c) {
     if (c->batch_depth < 1 || c->batch_depth > c->tile_w * c->tile_h) return false;
     if (c->sort_mode != GS_SORT_TWO_PHASE && c->sort_mode != GS_SORT_KEY64) return false;
     if (c->tile_rule != GS_TILES_REACH && c->tile_rule != GS_TILES_RECT) return false;
+    if (c->grad_limit < 0 || (c->isotropic != 0 && c->isotropic != 1)) return false;
     if (!(c->alpha_min > 0.f && c->alpha_min < c->alpha_max && c->alpha_max < 1.f)) return false;
     if (!(c->T_min > 0.f && c->T_min < 1.f) || !(c->dilation >= 0.f) || !(c->guard > 0.f) || !(c->extent > 0.f))
         return false;
@@ -88,6 +89,8 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     for (int k = 0; k < 2; ++k) { L->ikey[k] = take(cc * 8 + 16); L->ival[k] = take(cc * 4); }
     L->ranges = take((size_t)L->tiles * 2 * sizeof(uint32_t));
     L->grad2d = take(nn * 12 * sizeof(float));
+    // blended splats per pixel, written by the forward pass when gradients are limited
+    L->pix_count = cfg->grad_limit > 0 ? take((size_t)W * H * sizeof(uint32_t)) : 0;
     L->total = off;
     return true;
 }
@@ -111,8 +114,9 @@ bool valid_gaussians(const gs_frame* f, const gs_gaussians* g) {
     if (g->sh_degree < 0 || g->sh_degree > 3) return false;
     if (g->sh_stride < (g->sh_degree + 1) * (g->sh_degree + 1)) return false;
     if (g->n > 0) {
-        if (!g->means || !g->scales || !g->quats || !g->opacities || !g->sh) return false;
-        if (reinterpret_cast<uintptr_t>(g->quats) % 16) return false;
+        const bool iso = f->cfg.isotropic != 0;
+        if (!g->means || !g->scales || (!iso && !g->quats) || !g->opacities || !g->sh) return false;
+        if (!iso && reinterpret_cast<uintptr_t>(g->quats) % 16) return false;
         if (reinterpret_cast<uintptr_t>(g->means) % 4 || reinterpret_cast<uintptr_t>(g->scales) % 4 ||
             reinterpret_cast<uintptr_t>(g->opacities) % 4 || reinterpret_cast<uintptr_t>(g->sh) % 4)
             return false;
@@ -141,6 +145,7 @@ CfgK cfg_k(const gs_raster_config& c) {
     CfgK k;
     k.alpha_min = c.alpha_min; k.alpha_max = c.alpha_max; k.T_min = c.T_min;
     k.dilation = c.dilation; k.extent = c.extent; k.radius_max = kRadiusMax;
+    k.grad_limit = c.grad_limit; k.isotropic = c.isotropic;
     return k;
 }
 
@@ -161,7 +166,8 @@ struct FrameSet {
 
 bool same_shape(const gs_raster_config& a, const gs_raster_config& b) {
     return a.tile_w == b.tile_w && a.tile_h == b.tile_h && a.batch_depth == b.batch_depth &&
-           a.sort_mode == b.sort_mode && a.tile_rule == b.tile_rule;
+           a.sort_mode == b.sort_mode && a.tile_rule == b.tile_rule && (a.grad_limit > 0) == (b.grad_limit > 0) &&
+           a.isotropic == b.isotropic;
 }
 
 template <int MAXF>
@@ -452,6 +458,7 @@ gs_status render_forward_impl(const FrameSet<MAXF>& fs, const float* bg, float* 
         a.out_rgb = out_rgb[v];
         a.out_T = out_T[v];
         a.out_last = out_last[v];
+        a.out_count = f->cfg.grad_limit > 0 ? at<uint32_t>(ws, L.pix_count) : nullptr;
     }
     return ok(launch_render_forward(m, s));
 }
@@ -486,6 +493,7 @@ gs_status render_backward_tiles_impl(const FrameSet<MAXF>& fs, const float* bg, 
         a.dL_drgb = dL_drgb[v];
         a.T_final = T[v];
         a.last = last[v];
+        a.count = f->cfg.grad_limit > 0 ? at<uint32_t>(ws, L.pix_count) : nullptr;
         a.grad2d = at<float>(ws, L.grad2d);
         a.blended = reinterpret_cast<unsigned long long*>(&st->blended_pairs);
     }
@@ -505,8 +513,8 @@ bool same_gradients(const gs_gradients& a, const gs_gradients& b) {
 }
 
 bool gradients_overlap(const gs_gradients& a, const gs_gradients& b) {
-    return a.means == b.means || a.scales == b.scales || a.quats == b.quats || a.opacities == b.opacities ||
-           a.sh == b.sh || (a.mean2d && a.mean2d == b.mean2d);
+    return a.means == b.means || a.scales == b.scales || (a.quats && a.quats == b.quats) ||
+           a.opacities == b.opacities || a.sh == b.sh || (a.mean2d && a.mean2d == b.mean2d);
 }
 
 // Groups the frames by the Gaussians they render: a group's gradients are summed into its
@@ -576,8 +584,9 @@ gs_status render_backward_gaussians_impl(const FrameSet<MAXF>& fs, const gs_gaus
 
 bool valid_gradients(const gs_frame* f, const gs_gradients* gr) {
     if (!gr) return false;
-    if (f->n > 0 && (!gr->means || !gr->scales || !gr->quats || !gr->opacities || !gr->sh)) return false;
-    if (f->n > 0 && reinterpret_cast<uintptr_t>(gr->quats) % 16) return false;
+    const bool iso = f->cfg.isotropic != 0;
+    if (f->n > 0 && (!gr->means || !gr->scales || (!iso && !gr->quats) || !gr->opacities || !gr->sh)) return false;
+    if (f->n > 0 && !iso && reinterpret_cast<uintptr_t>(gr->quats) % 16) return false;
     return true;
 }
 
@@ -598,6 +607,8 @@ void gs_default_config(gs_raster_config* cfg) {
     cfg->guard = 1.3f;
     cfg->extent = 3.0f;
     cfg->tile_rule = GS_TILES_REACH;
+    cfg->grad_limit = 0;
+    cfg->isotropic = 0;
 }
 
 size_t gs_workspace_size(int n, int width, int height, uint64_t capacity, const gs_raster_config* cfg) {

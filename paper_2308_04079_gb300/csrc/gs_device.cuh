@@ -28,6 +28,8 @@ struct CamK {
 struct CfgK {
     float alpha_min, alpha_max, T_min, dilation, extent;
     int radius_max;
+    int grad_limit;   // > 0: gradients for the grad_limit front-most blended splats of a pixel only
+    int isotropic;    // 1: one scale per Gaussian, no rotation
 };
 
 constexpr int kRadiusMax = 1 << 24;   // screen radius clamp (pixels)

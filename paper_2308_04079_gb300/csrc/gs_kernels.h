@@ -223,6 +223,7 @@ struct RenderFwdArgs {
     float* out_rgb;
     float* out_T;
     uint32_t* out_last;
+    uint32_t* out_count;       // nullable: blended splats per pixel (for cfg.grad_limit)
 };
 
 struct RenderBwdArgs {
@@ -239,6 +240,7 @@ struct RenderBwdArgs {
     const float* dL_drgb;
     const float* T_final;
     const uint32_t* last;
+    const uint32_t* count;     // blended splats per pixel when cfg.grad_limit > 0, else null
     float* grad2d;             // [n, 12] accumulators, zeroed
     unsigned long long* blended;   // count of back-propagated (pixel, splat) pairs, zeroed
 };

@@ -123,7 +123,7 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, float (&f)
 
 }  // namespace
 
-template <int DEG, bool VEC, int MAXF>
+template <int DEG, bool VEC, int MAXF, bool ISO>
 __global__ void __launch_bounds__(256) k_preprocess_t(const __grid_constant__ Multi<PreprocessArgs, MAXF> m) {
     constexpr int D = (DEG + 1) * (DEG + 1);
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns blocks [base[f], base[f+1])
@@ -140,8 +140,10 @@ __global__ void __launch_bounds__(256) k_preprocess_t(const __grid_constant__ Mu
     if (i < a.n) {
         const CamK& c = a.cam;
         const float mu[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
-        const float s[3] = {a.scales[3 * i], a.scales[3 * i + 1], a.scales[3 * i + 2]};
-        const float4 q = reinterpret_cast<const float4*>(a.quats)[i];
+        // ISO (the isotropic ablation of Sec. 7.3): one scale for all axes and no rotation
+        const float s0 = ISO ? a.scales[i] : a.scales[3 * i];
+        const float s[3] = {s0, ISO ? s0 : a.scales[3 * i + 1], ISO ? s0 : a.scales[3 * i + 2]};
+        const float4 q = ISO ? make_float4(1.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(a.quats)[i];
         const float o = a.opacities[i];
         const bool finite = finite3(mu) && finite3(s) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
                             isfinite(q.w) && isfinite(o);
@@ -327,7 +329,7 @@ __device__ __forceinline__ void bwd_view(const PreprocessBwdArgs& a, int i, cons
 // scene): the gradients of all the group's views are summed in registers and written once
 // (or added to the output when accumulating).  Group g owns blocks [block_base[g],
 // block_base[g+1]) and frames [frame_begin[g], frame_begin[g+1]).
-template <int DEG, bool VEC, int MAXF>
+template <int DEG, bool VEC, int MAXF, bool ISO>
 __global__ void __launch_bounds__(256) k_preprocess_backward_t(const __grid_constant__ BwdPlan<MAXF> m) {
     constexpr int D = (DEG + 1) * (DEG + 1);
     constexpr int NF = BwdAcc<DEG>::NF;
@@ -364,8 +366,13 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(const __grid_cons
         if (!any) {
             any = true;
             mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
-            s[0] = a.scales[3 * i]; s[1] = a.scales[3 * i + 1]; s[2] = a.scales[3 * i + 2];
-            q = reinterpret_cast<const float4*>(a.quats)[i];
+            if (ISO) {   // one scale for all axes, no rotation
+                s[0] = s[1] = s[2] = a.scales[i];
+                q = make_float4(1.f, 0.f, 0.f, 0.f);
+            } else {
+                s[0] = a.scales[3 * i]; s[1] = a.scales[3 * i + 1]; s[2] = a.scales[3 * i + 2];
+                q = reinterpret_cast<const float4*>(a.quats)[i];
+            }
             load_sh<D, VEC>(a.sh + (size_t)i * row, f);
         }
         bwd_view<DEG>(av, i, mu, s, q, f, acc);
@@ -394,15 +401,27 @@ __global__ void __launch_bounds__(256) k_preprocess_backward_t(const __grid_cons
             for (int k = 3 * D; k < row; ++k) gsh[k] = 0.f;
     }
     const float4 gq = make_float4(acc.gq[0], acc.gq[1], acc.gq[2], acc.gq[3]);
+    // ISO: dL/ds is the sum over the axes; there is no rotation gradient
+    const float gs_iso = acc.gs[0] + acc.gs[1] + acc.gs[2];
     if (a.accumulate) {
-        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] += acc.gm[k]; a.g_scales[3 * i + k] += acc.gs[k]; }
-        const float4 o4 = reinterpret_cast<float4*>(a.g_quats)[i];
-        reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(o4.x + gq.x, o4.y + gq.y, o4.z + gq.z, o4.w + gq.w);
+        for (int k = 0; k < 3; ++k) a.g_means[3 * i + k] += acc.gm[k];
+        if (ISO) {
+            a.g_scales[i] += gs_iso;
+        } else {
+            for (int k = 0; k < 3; ++k) a.g_scales[3 * i + k] += acc.gs[k];
+            const float4 o4 = reinterpret_cast<float4*>(a.g_quats)[i];
+            reinterpret_cast<float4*>(a.g_quats)[i] = make_float4(o4.x + gq.x, o4.y + gq.y, o4.z + gq.z, o4.w + gq.w);
+        }
         a.g_opacities[i] += acc.go;
         if (a.g_mean2d) { a.g_mean2d[2 * i] += acc.du; a.g_mean2d[2 * i + 1] += acc.dv; }
     } else {
-        for (int k = 0; k < 3; ++k) { a.g_means[3 * i + k] = acc.gm[k]; a.g_scales[3 * i + k] = acc.gs[k]; }
-        reinterpret_cast<float4*>(a.g_quats)[i] = gq;
+        for (int k = 0; k < 3; ++k) a.g_means[3 * i + k] = acc.gm[k];
+        if (ISO) {
+            a.g_scales[i] = gs_iso;
+        } else {
+            for (int k = 0; k < 3; ++k) a.g_scales[3 * i + k] = acc.gs[k];
+            reinterpret_cast<float4*>(a.g_quats)[i] = gq;
+        }
         a.g_opacities[i] = acc.go;
         if (a.g_mean2d) { a.g_mean2d[2 * i] = acc.du; a.g_mean2d[2 * i + 1] = acc.dv; }
     }
@@ -428,14 +447,26 @@ bool sh_vectorisable(const float* sh, int sh_stride, const float* gsh = nullptr)
 
 template <int DEG, int MAXF>
 void preprocess_deg(const Multi<PreprocessArgs, MAXF>& m, bool vec, cudaStream_t s) {
-    if (vec) k_preprocess_t<DEG, true, MAXF><<<m.base[m.frames], 256, 0, s>>>(m);
-    else k_preprocess_t<DEG, false, MAXF><<<m.base[m.frames], 256, 0, s>>>(m);
+    const dim3 grid(m.base[m.frames]);
+    if (m.a[0].cfg.isotropic) {
+        if (vec) k_preprocess_t<DEG, true, MAXF, true><<<grid, 256, 0, s>>>(m);
+        else k_preprocess_t<DEG, false, MAXF, true><<<grid, 256, 0, s>>>(m);
+    } else {
+        if (vec) k_preprocess_t<DEG, true, MAXF, false><<<grid, 256, 0, s>>>(m);
+        else k_preprocess_t<DEG, false, MAXF, false><<<grid, 256, 0, s>>>(m);
+    }
 }
 
 template <int DEG, int MAXF>
 void preprocess_bwd_deg(const BwdPlan<MAXF>& m, bool vec, cudaStream_t s) {
-    if (vec) k_preprocess_backward_t<DEG, true, MAXF><<<m.block_base[m.groups], 256, 0, s>>>(m);
-    else k_preprocess_backward_t<DEG, false, MAXF><<<m.block_base[m.groups], 256, 0, s>>>(m);
+    const dim3 grid(m.block_base[m.groups]);
+    if (m.a[0].cfg.isotropic) {
+        if (vec) k_preprocess_backward_t<DEG, true, MAXF, true><<<grid, 256, 0, s>>>(m);
+        else k_preprocess_backward_t<DEG, false, MAXF, true><<<grid, 256, 0, s>>>(m);
+    } else {
+        if (vec) k_preprocess_backward_t<DEG, true, MAXF, false><<<grid, 256, 0, s>>>(m);
+        else k_preprocess_backward_t<DEG, false, MAXF, false><<<grid, 256, 0, s>>>(m);
+    }
 }
 
 }  // namespace

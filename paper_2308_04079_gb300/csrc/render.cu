@@ -26,6 +26,11 @@
 //   transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals with one atomic
 //   instruction, otherwise the contributing lanes add their own sums.
 //
+// Limited-BW (cfg.grad_limit = N > 0, the ablation of Sec. 7.3): the forward pass also records
+// the number of blended splats of every pixel (COUNT); the backward pass (LIMIT) keeps the
+// recurrences over all of them but adds gradients only for the N front-most, i.e. it skips the
+// gradient terms of the first (count - N) blended splats it meets from the back.
+//
 // The forward and the backward evaluate a (pixel, splat) pair with the same staging and the same
 // operation sequence (stage_splat, splat_row, splat_s), so their skip and clamp decisions agree
 // bit for bit.
@@ -139,7 +144,7 @@ __device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, fl
     return __fmaf_rn(p, p, qq);
 }
 
-template <int PX, int TPR, int MAXF>
+template <int PX, int TPR, int MAXF, bool COUNT>
 __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__ Multi<RenderFwdArgs, MAXF> m) {
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
     // a batch reads its frame's arguments from a shared copy (loads through a pointer into the
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     const float log2_amin = __log2f(a.cfg.alpha_min);
 
     float T[PX], Cr[PX], Cg[PX], Cb[PX];
-    uint32_t last[PX];
+    uint32_t last[PX], nblended[PX];
     bool done[PX];
     int ndone = 0;
 #pragma unroll
@@ -179,6 +184,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
         T[j] = 1.0f;
         Cr[j] = Cg[j] = Cb[j] = 0.f;
         last[j] = 0;
+        nblended[j] = 0;
         done[j] = !(x0 + c0 + TPR * j < c.W && py < c.H);
         ndone += done[j];
     }
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
                     Cb[j] += w * col.z;
                     T[j] = test;
                     last[j] = b - start + (uint32_t)k + 1u;
+                    if (COUNT) ++nblended[j];
                 }
                 if (ndone == PX) break;
             }
@@ -239,11 +246,12 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
             a.out_rgb[2 * P + p] = Cb[j] + T[j] * a.bg[2];
             a.out_T[p] = T[j];
             a.out_last[p] = last[j];
+            if (COUNT) a.out_count[p] = nblended[j];
         }
     }
 }
 
-template <int PX, int TPR, int MAXF>
+template <int PX, int TPR, int MAXF, bool LIMIT>
 __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant__ Multi<RenderBwdArgs, MAXF> m) {
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
     // a batch reads its frame's arguments from a shared copy (loads through a pointer into the
@@ -281,16 +289,24 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     // Per pixel: T, R . dL/dC (only this projection of the colour behind is ever needed) and dL/dC.
     float T[PX], Rd[PX], dLr[PX], dLg[PX], dLb[PX];
     uint32_t mylast[PX];
+    // LIMIT: the first `skip` blended splats met from the back (all but the grad_limit front-most)
+    // get no gradient; the recurrences for T and R . dL/dC still run through them
+    uint32_t skip[PX], seen[PX];
     uint32_t tmax = 0;
 #pragma unroll
     for (int j = 0; j < PX; ++j) {
         const int px = x0 + c0 + TPR * j;
         mylast[j] = 0;
+        skip[j] = seen[j] = 0;
         T[j] = 1.0f;
         dLr[j] = dLg[j] = dLb[j] = 0.f;
         if (px < c.W && py < c.H) {
             const size_t p = (size_t)py * c.W + px;
             mylast[j] = a.last[p];
+            if (LIMIT) {
+                const uint32_t nb = a.count[p], lim = (uint32_t)a.cfg.grad_limit;
+                skip[j] = nb > lim ? nb - lim : 0u;
+            }
             T[j] = a.T_final[p];
             dLr[j] = a.dL_drgb[p];
             dLg[j] = a.dL_drgb[P + p];
@@ -342,21 +358,23 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                     float p;
                     const float s = splat_s(p0, dp, qq, j, p);
                     if (pos >= mylast[j] || s > st.a.z) continue;
-                    contrib = true;
+                    const bool grad = !LIMIT || seen[j]++ >= skip[j];
+                    contrib |= grad;
                     ++nblend;
                     const float oG = exp2f(__fsub_rn(st.a.w, s));
                     const float alpha = fminf(amax, oG);
                     const float one_m = __fsub_rn(1.0f, alpha);
                     const float Ti = __fdividef(T[j], one_m);   // one_m >= 0.01: 2-ulp division
                     const float w = alpha * Ti;
-                    g[6] += w * dLr[j];
-                    g[7] += w * dLg[j];
-                    g[8] += w * dLb[j];
                     // dL/dalpha = T_i (c_i - R_{i+1}) . dL/dC;  R_i . dL/dC = R_{i+1} . dL/dC + alpha (c_i - R_{i+1}) . dL/dC
                     const float diff = col.x * dLr[j] + col.y * dLg[j] + col.z * dLb[j] - Rd[j];
                     const float dalpha = Ti * diff;
                     Rd[j] = fmaf(alpha, diff, Rd[j]);
                     T[j] = Ti;
+                    if (LIMIT && !grad) continue;
+                    g[6] += w * dLr[j];
+                    g[7] += w * dLg[j];
+                    g[8] += w * dLb[j];
                     if (oG <= amax) {
                         // dpow = dL/d(power); g = Sigma'^-1 d = 2 ln 2 (u, v) with (u, v) = L' (p, q):
                         // sums of dpow (u, v) and dpow (u, v)(u, v)^T here, the constant factors
@@ -418,8 +436,15 @@ cudaError_t launch_render_forward(Multi<RenderFwdArgs, MAXF>& m, cudaStream_t s)
     if (tiles == 0) return cudaSuccess;
     const RenderFwdArgs& a = m.a[0];
     // 4 threads per tile row (measured: 2 per row, one warp per 16x16 tile, is 1.5x slower)
-    if (a.cam.tile_w == 16) k_render_forward_t<4, 4, MAXF><<<tiles, 4 * a.cam.tile_h, fwd_smem(a.batch), s>>>(m);
-    else k_render_forward_t<2, 4, MAXF><<<tiles, 4 * a.cam.tile_h, fwd_smem(a.batch), s>>>(m);
+    const dim3 grid(tiles), block(4 * a.cam.tile_h);
+    const size_t smem = fwd_smem(a.batch);
+    if (a.out_count) {   // gradient-limited frames also record the blended splats per pixel
+        if (a.cam.tile_w == 16) k_render_forward_t<4, 4, MAXF, true><<<grid, block, smem, s>>>(m);
+        else k_render_forward_t<2, 4, MAXF, true><<<grid, block, smem, s>>>(m);
+    } else {
+        if (a.cam.tile_w == 16) k_render_forward_t<4, 4, MAXF, false><<<grid, block, smem, s>>>(m);
+        else k_render_forward_t<2, 4, MAXF, false><<<grid, block, smem, s>>>(m);
+    }
     return cudaGetLastError();
 }
 
@@ -428,8 +453,15 @@ cudaError_t launch_render_backward(Multi<RenderBwdArgs, MAXF>& m, cudaStream_t s
     const uint32_t tiles = tile_split(m);
     if (tiles == 0) return cudaSuccess;
     const RenderBwdArgs& a = m.a[0];
-    if (a.cam.tile_w == 16) k_render_backward_t<4, 4, MAXF><<<tiles, 4 * a.cam.tile_h, bwd_smem(a.batch), s>>>(m);
-    else k_render_backward_t<2, 4, MAXF><<<tiles, 4 * a.cam.tile_h, bwd_smem(a.batch), s>>>(m);
+    const dim3 grid(tiles), block(4 * a.cam.tile_h);
+    const size_t smem = bwd_smem(a.batch);
+    if (a.count) {
+        if (a.cam.tile_w == 16) k_render_backward_t<4, 4, MAXF, true><<<grid, block, smem, s>>>(m);
+        else k_render_backward_t<2, 4, MAXF, true><<<grid, block, smem, s>>>(m);
+    } else {
+        if (a.cam.tile_w == 16) k_render_backward_t<4, 4, MAXF, false><<<grid, block, smem, s>>>(m);
+        else k_render_backward_t<2, 4, MAXF, false><<<grid, block, smem, s>>>(m);
+    }
     return cudaGetLastError();
 }
 

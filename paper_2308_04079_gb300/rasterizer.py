@@ -24,13 +24,18 @@ _SORT_MODES = {"two_phase": abi.GS_SORT_TWO_PHASE, "key64": abi.GS_SORT_KEY64}
 
 
 def make_config(tile=(16, 16), batch_depth: int | None = None, sort_mode: str = "two_phase",
-                tile_rule: str = "reach", **overrides) -> abi.gs_raster_config:
-    """Rasterizer constants (paper defaults) with optional overrides."""
+                tile_rule: str = "reach", grad_limit: int = 0, isotropic: bool = False,
+                **overrides) -> abi.gs_raster_config:
+    """Rasterizer constants (paper defaults) with optional overrides.  grad_limit > 0 and
+    isotropic select the ablation variants of Sec. 7.3 (Limited-BW with N = grad_limit, and
+    one scale per Gaussian with no rotation)."""
     cfg = abi.gs_default_config()
     cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
     cfg.batch_depth = int(batch_depth) if batch_depth else cfg.tile_w * cfg.tile_h
     cfg.sort_mode = _SORT_MODES[sort_mode]
     cfg.tile_rule = _TILE_RULES[tile_rule]
+    cfg.grad_limit = int(grad_limit)
+    cfg.isotropic = int(bool(isotropic))
     for k, v in overrides.items():
         setattr(cfg, k, v)
     return cfg
@@ -59,7 +64,9 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
-def _prep(t: torch.Tensor, align: int = 4) -> torch.Tensor:
+def _prep(t: torch.Tensor | None, align: int = 4) -> torch.Tensor | None:
+    if t is None:
+        return None
     t = t.detach()
     if t.dtype != torch.float32:
         raise TypeError("rasterizer inputs must be float32")
@@ -74,8 +81,8 @@ def _prep(t: torch.Tensor, align: int = 4) -> torch.Tensor:
 @dataclass
 class GaussianTensors:
     means: torch.Tensor      # [N, 3]
-    scales: torch.Tensor     # [N, 3]
-    quats: torch.Tensor      # [N, 4]
+    scales: torch.Tensor     # [N, 3] ([N] for an isotropic configuration)
+    quats: torch.Tensor      # [N, 4] (None for an isotropic configuration)
     opacities: torch.Tensor  # [N]
     sh: torch.Tensor         # [N, D, 3]
     sh_degree: int
@@ -99,7 +106,8 @@ class GaussianTensors:
     def from_numpy(g, device="cuda") -> "GaussianTensors":
         def t(a):
             return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32))).to(device)
-        return GaussianTensors(t(g.means), t(g.scales), t(g.quats), t(g.opacities), t(g.sh), int(g.sh_degree))
+        quats = None if g.quats is None else t(g.quats)
+        return GaussianTensors(t(g.means), t(g.scales), quats, t(g.opacities), t(g.sh), int(g.sh_degree))
 
 
 class Frame:
@@ -190,7 +198,8 @@ class Frame:
 
     def new_grads(self, g: GaussianTensors, with_mean2d: bool = True) -> dict:
         d = dict(means=torch.empty_like(g.means), scales=torch.empty_like(g.scales),
-                 quats=torch.empty_like(g.quats), opacities=torch.empty_like(g.opacities),
+                 quats=None if g.quats is None else torch.empty_like(g.quats),
+                 opacities=torch.empty_like(g.opacities),
                  sh=torch.empty_like(g.sh))
         if with_mean2d:
             d["mean2d"] = torch.empty((g.n, 2), dtype=torch.float32, device=g.means.device)

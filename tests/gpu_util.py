@@ -63,7 +63,7 @@ def gpu_backward(run, bg, dimg_np):
     n = gt.n
     grad2d = fr.view("grad2d", torch.float32, 12 * n).view(n, 12).clone()
     torch.cuda.synchronize()
-    out = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    out = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items() if v is not None}
     g2 = grad2d.cpu().numpy().astype(np.float64)
     out["uv"] = g2[:, 0:2]
     out["cov2d"] = g2[:, 2:5]
