@@ -727,7 +727,19 @@ def main():
     ap.add_argument("--batch-views", type=int, default=16)
     ap.add_argument("--gaussians", type=int, default=CONFIG3_N,
                     help="Gaussians of the config-3 scene (smaller counts for profiling captures)")
+    ap.add_argument("--density-only", action="store_true",
+                    help="time one density-control refinement (gs_densify) of --gaussians Gaussians only")
     args = ap.parse_args()
+    if args.density_only:
+        import torch
+        from paper_2308_04079_gb300 import build as gbuild
+        torch.cuda.set_device(0)
+        if gbuild.needs_build():
+            gbuild.build()
+        hbm_peak, peak_kind = load_peaks()
+        print(json.dumps(run_density(args, torch.device("cuda", 0), torch.cuda.current_stream(), hbm_peak,
+                                     peak_kind)), flush=True)
+        return
     rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         # The CPU oracle runs on rank 0 only; other ranks exit without work.
