@@ -48,10 +48,10 @@ CONFIG3_N = 3_000_000
 KERNEL_NAMES = {"preprocess": "k_preprocess_t", "render_forward": "k_render_forward_t",
                 "render_backward_tiles": "k_render_backward_t",
                 "render_backward_gaussians": "k_preprocess_backward_t"}
-# DRAM bytes (read + write) per launch of each single-kernel stage on the 3M-Gaussian 1080p
-# frame, from the ncu capture summarised in the named file under profiles/; None where no
-# capture of the current kernel exists.
-TRAFFIC = {"render_backward_tiles": 106_690_000}   # profiles/k_render_backward_config3.md
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
+# single-kernel stage on the 3M-Gaussian 1080p frame, taken from a capture of the current
+# kernel; a stage without such a capture reports None.
+TRAFFIC = {"render_backward_tiles": 106_704_896}
 
 
 def env_int(k, d):

@@ -5,7 +5,8 @@ from __future__ import annotations
 
 import numpy as np
 
-# Tolerances:
+# Tolerances, from the fp32 arithmetic of the kernels against the FP64 oracle: pixels and
+# Gaussians with a decision near its threshold (the oracle's ambiguity flags) are excluded.
 IMG_ATOL = 1e-4          # images and final transmittance, absolute per channel (fp32 vs fp64)
 GRAD_REL_L2 = 1e-3       # gradients: per-tensor relative L2 error
 GRAD_ELEM_REL = 1e-2     # gradients: per element, relative to max(|g*|, rms of the tensor)
