@@ -74,8 +74,11 @@ class GaussianModel:
     def n(self) -> int:
         return int(self.means.shape[0])
 
-    def gaussians(self) -> GaussianTensors:
-        return GaussianTensors(self.means, self.scales, self.quats, self.opacities, self.sh, self.sh_degree)
+    def gaussians(self, sh_degree: int | None = None) -> GaussianTensors:
+        """The activated parameters as the rasterizer's input, rendered up to ``sh_degree`` (the
+        buffer keeps all coefficients; the unused ones get zero gradient)."""
+        deg = self.sh_degree if sh_degree is None else min(int(sh_degree), self.sh_degree)
+        return GaussianTensors(self.means, self.scales, self.quats, self.opacities, self.sh, deg)
 
 
 def position_lr(step: int, lr_init: float, lr_final: float, max_steps: int) -> float:
@@ -93,9 +96,12 @@ class Trainer:
     """One training iteration per call of step(camera, target): forward, loss, backward, Adam."""
 
     def __init__(self, model: GaussianModel, lr: dict | None = None, lam: float = 0.2, betas=(0.9, 0.999),
-                 eps: float = 1e-15, cfg=None, bg=(0.0, 0.0, 0.0), density=None):
+                 eps: float = 1e-15, cfg=None, bg=(0.0, 0.0, 0.0), density=None, sh_band_every: int = 0):
+        """sh_band_every > 0: optimise only the zero-order SH band first and add one band every
+        that many iterations (Sec. 7.1 uses 1000); 0: all bands from the start."""
         self.model = model
         self.density = density
+        self.sh_band_every = int(sh_band_every)
         self.lr = dict(DEFAULT_LR, **(lr or {}))
         self.lam, self.betas, self.eps = float(lam), betas, float(eps)
         self.cfg = cfg if cfg is not None else make_config()
@@ -123,7 +129,7 @@ class Trainer:
         """Returns the device tensor (L, L1, mean SSIM) of this iteration's rendering."""
         m = self.model
         fr, (img, T, last), dimg, loss = self._frame(camera)
-        g = m.gaussians()
+        g = m.gaussians(self.active_sh_degree())
         if self.grads is None:
             self.grads = fr.new_grads(g, with_mean2d=True)
         fr.preprocess(g)
@@ -156,6 +162,12 @@ class Trainer:
             self._frames.clear()      # workspaces and gradients are sized by the Gaussian count
             self.grads = None
         return out
+
+    def active_sh_degree(self) -> int:
+        """SH degree rendered at the next iteration under the band schedule."""
+        if self.sh_band_every <= 0:
+            return self.model.sh_degree
+        return min(self.model.sh_degree, self.iteration // self.sh_band_every)
 
     def status(self):
         """Status codes of the frames (synchronises)."""

@@ -119,3 +119,26 @@ def test_training_iteration_matches_the_oracle():
         agree = np.mean(np.sign(dg[big]) == np.sign(dr[big]))
         assert agree >= 0.995, (k, agree)
         assert np.all(np.abs(dg) <= lr[k if k != "means" else "means"] * (1 + 1e-4) + 1e-7), k
+
+
+def test_sh_band_schedule_moves_only_the_active_bands():
+    """Sec. 7.1: zero-order band first, one more band every sh_band_every iterations; the
+    rasterizer zeroes the gradients of the unused coefficients, so Adam leaves them alone."""
+    import torch
+    from paper_2308_04079_gb300.training import GaussianModel, Trainer
+    g, cam = S.tiny_scene(51, n=400, width=80, height=60, deg=3)
+    model = GaussianModel.from_numpy(g)
+    tr = Trainer(model, sh_band_every=2)
+    target = torch.from_numpy(np.random.default_rng(52).random((3, cam.height, cam.width), dtype=np.float32)).cuda()
+    sh0 = model.sh.cpu().numpy().copy()
+    tr.step(cam, target)                       # iteration 0: degree 0
+    torch.cuda.synchronize()
+    sh1 = model.sh.cpu().numpy()
+    assert np.abs(sh1[:, 0] - sh0[:, 0]).max() > 0
+    assert np.array_equal(sh1[:, 1:], sh0[:, 1:])
+    tr.step(cam, target)                       # iteration 1: degree 0
+    tr.step(cam, target)                       # iteration 2: degree 1
+    torch.cuda.synchronize()
+    sh3 = model.sh.cpu().numpy()
+    assert np.abs(sh3[:, 1:4] - sh0[:, 1:4]).max() > 0
+    assert np.array_equal(sh3[:, 4:], sh0[:, 4:])

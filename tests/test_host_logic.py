@@ -1,0 +1,56 @@
+"""Host-side logic of the training loop (no GPU): the density-control schedule of Sec. 5.2,
+the scene extent, the progressive SH band schedule of Sec. 7.1 and the position learning
+rate of the Trainer."""
+import math
+from types import SimpleNamespace
+
+import numpy as np
+import torch
+
+from paper_2308_04079_gb300.density import DensitySchedule, scene_extent
+from paper_2308_04079_gb300.training import GaussianModel, Trainer, position_lr
+from synthetic import look_at_camera
+
+
+def test_density_schedule():
+    s = DensitySchedule()
+    assert not s.refine_at(500) and s.refine_at(600) and not s.refine_at(650)
+    assert s.refine_at(15000) and not s.refine_at(15100)
+    assert s.reset_at(3000) and s.reset_at(6000) and not s.reset_at(3100) and not s.reset_at(18000)
+    assert not s.size_pruning(3000) and s.size_pruning(3001)
+    every = DensitySchedule(start=0, every=1, stop=10, reset_every=0)
+    assert all(every.refine_at(i) for i in range(1, 11)) and not every.reset_at(3)
+
+
+def test_scene_extent():
+    cams = [look_at_camera([3.0 * math.cos(a), 0.0, 3.0 * math.sin(a)], [0, 0, 0], 64, 48, 60.0)
+            for a in np.linspace(0, 2 * math.pi, 8, endpoint=False)]
+    assert abs(scene_extent(cams) - 1.1 * 3.0) < 1e-5          # centres on a circle of radius 3
+    one = [look_at_camera([0.0, 0.0, -4.0], [0, 0, 0], 64, 48, 60.0)]
+    assert abs(scene_extent(one) - 1.1 * 4.0) < 1e-5           # one camera: its distance to the origin
+
+
+def _model(n=5, deg=3):
+    rng = np.random.default_rng(0)
+    g = SimpleNamespace(means=rng.normal(size=(n, 3)), scales=np.full((n, 3), 0.1), quats=np.tile([1.0, 0, 0, 0], (n, 1)),
+                        opacities=np.full(n, 0.5), sh=rng.normal(size=(n, (deg + 1) ** 2, 3)), sh_degree=deg)
+    return GaussianModel.from_numpy(g, device="cpu")
+
+
+def test_sh_band_schedule():
+    m = _model()
+    tr = Trainer(m, sh_band_every=1000)
+    seen = []
+    for it in (0, 999, 1000, 1999, 2000, 3000, 9000):
+        tr.iteration = it
+        seen.append(tr.active_sh_degree())
+    assert seen == [0, 0, 1, 1, 2, 3, 3]
+    assert Trainer(m).active_sh_degree() == 3
+    assert m.gaussians(1).sh_degree == 1 and m.gaussians(7).sh_degree == 3 and m.gaussians().sh_degree == 3
+
+
+def test_position_lr_is_log_linear():
+    assert math.isclose(position_lr(0, 1.6e-4, 1.6e-6, 30000), 1.6e-4)
+    assert math.isclose(position_lr(30000, 1.6e-4, 1.6e-6, 30000), 1.6e-6)
+    assert math.isclose(position_lr(15000, 1.6e-4, 1.6e-6, 30000), 1.6e-5)
+    assert math.isclose(position_lr(90000, 1.6e-4, 1.6e-6, 30000), 1.6e-6)
