@@ -125,10 +125,14 @@ class ClockSampler:
 # Our arm
 # ------------------------------------------------------------------------------------------
 def launches_per_step(layout) -> int:
-    """Kernels one step launches: preprocess; binning = [depth histogram + depth passes] +
-    count + pair scan + segment write + ranges + emit + sort-prepare + instance passes;
-    forward; backward tiles; backward Gaussians."""
-    binning = 6 + layout.key_passes + ((1 + layout.depth_passes) if layout.depth_passes else 0)
+    """Kernels one step launches: preprocess; binning = two-phase: depth histogram + depth
+    passes + one segment pass (count, scan and records) + emit + sort-prepare + instance passes
+    + ranges; KEY64: count + pair scan + segment write + emit + sort-prepare + instance passes +
+    ranges; forward; backward tiles; backward Gaussians."""
+    if layout.depth_passes:
+        binning = (1 + layout.depth_passes) + 1 + 3 + layout.key_passes
+    else:
+        binning = 3 + 3 + layout.key_passes
     return 1 + binning + 1 + 2
 
 

@@ -306,8 +306,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
 // rows the interval of tiles the splat can reach (reach_row).  Pass 1 counts every entry's
 // non-empty rows (segments) and tiles, pass 2 scans those pairs, pass 3 writes one record per
 // segment (first instance, first tile id, Gaussian id), pass 4 (k_emit) expands the records
-// into keys and values.  In KEY64 mode the depth digits of the four low key passes are constant
-// per Gaussian: their histograms are weighted by its tile count.
+// into keys and values.  The two-phase schedule runs passes 1-3 as one kernel (k_segments);
+// KEY64 keeps them apart, its depth digits of the four low key passes being constant per
+// Gaussian: their histograms are weighted by its tile count in pass 1.
 // ---------------------------------------------------------------------------------------
 // Look-back words carry (segments, instances) as two 31-bit fields, each saturated at 2^30
 // (above any capacity), so sums over many chunks cannot carry from one field into the other.
@@ -692,6 +693,249 @@ __global__ void __launch_bounds__(kDupThreads) k_write_segments(const __grid_con
 }
 
 // ---------------------------------------------------------------------------------------
+// DuplicateWithKeys passes 1-3 in one kernel (the two-phase schedule): chunks of kDupThreads
+// depth-ordered entries are claimed in order; a chunk evaluates its splats' reachable tile rows
+// once (8-lane groups, as k_count_tiles), keeps the first kSegSlots non-empty rows of every
+// splat in shared memory, scans (segments, instances) over the chunk, finds the chunk's global
+// offsets by decoupled look-back over its predecessors (bounded spin), and writes the segment
+// records in segment order.  Rows beyond the slots (large splats) are evaluated a second time.
+// ---------------------------------------------------------------------------------------
+constexpr int kSegSlots = 8;
+
+template <int MAXF>
+__global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
+    constexpr int ROUNDS = 32 / kGroups;
+    __shared__ uint2 s_slot[kDupThreads][kSegSlots];   // (tile id, instances of the splat's earlier rows)
+    __shared__ uint32_t s_seg[kDupThreads + 1];        // chunk-local exclusive segment prefix, [256] = total
+    __shared__ uint32_t s_inst[kDupThreads];           // chunk-local exclusive instance prefix
+    __shared__ uint32_t s_gid[kDupThreads];
+    __shared__ unsigned long long s_scan[33];
+    __shared__ uint32_t s_chunk;
+    __shared__ unsigned long long s_base_s, s_base_t;
+    __shared__ uint32_t s_fbase[MAXF + 1];             // chunks of frames [0, f)
+    __shared__ __align__(16) ScanArgs s_args;
+    __shared__ int s_argf;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, sub = lane % kRowLanes, grp = lane / kRowLanes;
+    if (tid < 32) {
+        uint32_t ch = 0;
+        if (tid < m.frames) {
+            const ScanArgs& af = m.a[tid];
+            uint32_t cnt = (uint32_t)af.n;
+            if (af.count_dev) cnt = min(cnt, *af.count_dev);
+            ch = (cnt + kDupThreads - 1) / kDupThreads;
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(ch);
+        if (tid < m.frames) s_fbase[tid + 1] = inc;
+        if (tid == 0) {
+            s_fbase[0] = 0;
+            s_argf = -1;
+        }
+    }
+    __syncthreads();
+    const uint32_t total = s_fbase[m.frames];
+    for (;;) {
+        if (tid == 0) s_chunk = atomicAdd(m.a[0].chunk_counter, 1u);
+        __syncthreads();
+        const uint32_t g = s_chunk;
+        if (g >= total) break;
+        int f = 0;
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_fbase[f + 1] <= g) ++f;
+        auto body = [&](const ScanArgs& a) {
+            uint32_t count = (uint32_t)a.n;
+            if (a.count_dev) count = min(count, *a.count_dev);
+            const uint32_t chunk = g - s_fbase[f];
+            const uint32_t chunks = s_fbase[f + 1] - s_fbase[f];
+            const uint32_t j = chunk * kDupThreads + tid;
+            const EntrySplat sp = load_entry(a, j, count);
+            s_gid[tid] = sp.gid;
+            const int tw_log2 = a.cam.tile_w == 16 ? 4 : 3;
+            const uint32_t tiles_x = (uint32_t)a.cam.tiles_x;
+
+            // rows of the warp's 32 splats, kGroups splats at a time
+            uint32_t nseg = 0, ntile = 0;
+            for (int r = 0; r < ROUNDS; ++r) {
+                const int src = r * kGroups + grp;
+                const int e_local = warp * 32 + src;
+                const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, src);
+                uint32_t cs = 0, ct = 0;   // segments / instances of the rows before this pass
+                for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
+                    const int ty = jb.y0 + base + sub;
+                    int txa = 0, txb = 0;
+                    const bool ok = base + sub < jb.rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2,
+                                                                     a.cam.tile_h, jb.x0, jb.x1, txa, txb);
+                    const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
+                    uint32_t is = ok ? 1u : 0u, it = len;   // inclusive scans over the group's lanes
+#pragma unroll
+                    for (int d = 1; d < kRowLanes; d <<= 1) {
+                        const uint32_t ns = __shfl_up_sync(0xffffffffu, is, d, kRowLanes);
+                        const uint32_t nt = __shfl_up_sync(0xffffffffu, it, d, kRowLanes);
+                        if (sub >= d) {
+                            is += ns;
+                            it += nt;
+                        }
+                    }
+                    if (ok) {
+                        const uint32_t k = cs + is - 1u;
+                        if (k < (uint32_t)kSegSlots)
+                            s_slot[e_local][k] = make_uint2((uint32_t)ty * tiles_x + (uint32_t)txa, ct + it - len);
+                    }
+                    cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
+                    ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
+                }
+                // owner lane r * kGroups + q takes the totals of group q
+                const int from = (lane % kGroups) * kRowLanes;
+                const uint32_t ts = __shfl_sync(0xffffffffu, cs, from), tt = __shfl_sync(0xffffffffu, ct, from);
+                if (lane / kGroups == r) {
+                    nseg = ts;
+                    ntile = tt;
+                }
+            }
+
+            // chunk-local prefix of (segments, instances)
+            const unsigned long long run = ((unsigned long long)nseg << kLocalShift) | ntile;
+            unsigned long long local_total;
+            const unsigned long long excl = block_exclusive_scan<unsigned long long>(run, s_scan, &local_total);
+            s_seg[tid] = (uint32_t)(excl >> kLocalShift);
+            s_inst[tid] = (uint32_t)(excl & ((1ull << kLocalShift) - 1));
+            const unsigned long long blk_s = local_total >> kLocalShift;
+            const unsigned long long blk_t = local_total & ((1ull << kLocalShift) - 1);
+            if (tid == 0) s_seg[kDupThreads] = (uint32_t)blk_s;
+            const unsigned long long cap = a.capacity;
+
+            // global base of the chunk: decoupled look-back
+            if (tid < 32) {
+                unsigned long long* const lookback = a.lookback;
+                unsigned long long* my = lookback + chunk;
+                unsigned long long ex_s = 0, ex_t = 0;
+                if (tid == 0) st_relaxed64(my, (chunk == 0 ? kScanInc : kScanAgg) | pair_word(blk_s, blk_t));
+                if (chunk > 0) {
+                    int jj = (int)chunk - 1;
+                    uint32_t spins = 0;
+                    while (true) {
+                        const int idx = jj - tid;
+                        const unsigned long long w = idx >= 0 ? ld_relaxed64(lookback + idx) : kScanInc;
+                        const unsigned long long fl = w & kScanFlags;
+                        const uint32_t inc = __ballot_sync(0xffffffffu, fl == kScanInc);
+                        const uint32_t zero = __ballot_sync(0xffffffffu, fl == 0);
+                        const int first_inc = inc ? __ffs(inc) - 1 : 32;
+                        const uint32_t upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
+                        if (zero & upto) {   // a predecessor in front of the first prefix is not ready
+                            if (++spins > kSpinLimit) {
+                                if (tid == 0) atomicOr(&a.status->flags, kFlagTimeout);
+                                break;
+                            }
+                            backoff(spins);
+                            continue;
+                        }
+                        const bool use = tid <= first_inc;
+                        unsigned long long ps = use ? ((w >> 31) & kField) : 0ull;
+                        unsigned long long pt = use ? (w & kField) : 0ull;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            ps += __shfl_xor_sync(0xffffffffu, ps, o);
+                            pt += __shfl_xor_sync(0xffffffffu, pt, o);
+                        }
+                        ex_s = min(ex_s + ps, kPairSat);
+                        ex_t = min(ex_t + pt, kPairSat);
+                        if (first_inc < 32) break;
+                        jj -= 32;
+                    }
+                    if (tid == 0) st_relaxed64(my, kScanInc | pair_word(ex_s + blk_s, ex_t + blk_t));
+                }
+                if (tid == 0) {
+                    s_base_s = ex_s;
+                    s_base_t = ex_t;
+                    if (chunk == chunks - 1) {
+                        const unsigned long long segs = min(ex_s + blk_s, kPairSat);
+                        const unsigned long long tiles = min(ex_t + blk_t, kPairSat);
+                        a.status->num_instances = (uint32_t)tiles;
+                        *a.num_segments = (uint32_t)segs;
+                        if (tiles > cap) atomicOr(&a.status->flags, kFlagCapacity);
+                        else a.seg_off[segs] = (uint32_t)tiles;   // end of the last segment
+                    }
+                }
+            }
+            __syncthreads();
+            const unsigned long long base_s = s_base_s, base_t = s_base_t;
+            const uint32_t cap32 = (uint32_t)cap;
+
+            // segment records of the kept rows, in segment order
+            const uint32_t chunk_segs = s_seg[kDupThreads];
+            for (uint32_t sl = (uint32_t)tid; sl < chunk_segs; sl += kDupThreads) {
+                int e = 0;   // the last entry whose first segment is <= sl (it owns segment sl)
+#pragma unroll
+                for (int step = kDupThreads / 2; step > 0; step >>= 1)
+                    if (s_seg[e + step] <= sl) e += step;
+                const uint32_t k = sl - s_seg[e];
+                const unsigned long long seg = base_s + sl;
+                if (k < (uint32_t)kSegSlots && seg < cap) {
+                    const uint2 rec = s_slot[e][k];
+                    a.seg_off[seg] = (uint32_t)min(base_t + s_inst[e] + rec.y, cap);
+                    a.seg_tile[seg] = rec.x;
+                    a.seg_gid[seg] = s_gid[e];
+                }
+            }
+            // rows beyond the slots: evaluated again by the splat's row group
+            if (__any_sync(0xffffffffu, nseg > (uint32_t)kSegSlots)) {   // warp-uniform
+                for (int r = 0; r < ROUNDS; ++r) {
+                    const int src = r * kGroups + grp;
+                    const int e_local = warp * 32 + src;
+                    const uint32_t ns = __shfl_sync(0xffffffffu, nseg, src);
+                    const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, src);
+                    const int rows = ns > (uint32_t)kSegSlots ? jb.rows : 0;
+                    const unsigned long long seg0 = base_s + s_seg[e_local];
+                    const unsigned long long off0 = base_t + s_inst[e_local];
+                    const uint32_t gid = s_gid[e_local];
+                    uint32_t cs = 0, ct = 0;
+                    for (int base = 0; __any_sync(0xffffffffu, base < rows); base += kRowLanes) {
+                        const int ty = jb.y0 + base + sub;
+                        int txa = 0, txb = 0;
+                        const bool ok = base + sub < rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2,
+                                                                      a.cam.tile_h, jb.x0, jb.x1, txa, txb);
+                        const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
+                        uint32_t is = ok ? 1u : 0u, it = len;
+#pragma unroll
+                        for (int d = 1; d < kRowLanes; d <<= 1) {
+                            const uint32_t n1 = __shfl_up_sync(0xffffffffu, is, d, kRowLanes);
+                            const uint32_t n2 = __shfl_up_sync(0xffffffffu, it, d, kRowLanes);
+                            if (sub >= d) {
+                                is += n1;
+                                it += n2;
+                            }
+                        }
+                        if (ok) {
+                            const uint32_t k = cs + is - 1u;
+                            const unsigned long long seg = seg0 + k;
+                            if (k >= (uint32_t)kSegSlots && seg < cap) {
+                                a.seg_off[seg] = (uint32_t)min(off0 + ct + it - len, cap);
+                                a.seg_tile[seg] = (uint32_t)ty * tiles_x + (uint32_t)txa;
+                                a.seg_gid[seg] = gid;
+                            }
+                        }
+                        cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
+                        ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
+                    }
+                }
+            }
+            (void)cap32;
+        };
+        if constexpr (MAXF == 1) {
+            body(m.a[0]);
+        } else {
+            if (f != s_argf) {   // block-uniform
+                for (int k = tid; k < (int)(sizeof(ScanArgs) / 4); k += kDupThreads)
+                    reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
+                __syncthreads();
+                if (tid == 0) s_argf = f;
+            }
+            body(s_args);
+        }
+        __syncthreads();   // shared state is rewritten by the next chunk
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // DuplicateWithKeys, pass 4: a warp takes 32 consecutive segment records, whose outputs form
 // one contiguous run; every lane finds the segment of each output position it writes by a
 // 5-step search over the lanes' segment ends, so keys and values are written coalesced.  A
@@ -882,6 +1126,10 @@ cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_ch
 
 template <int MAXF>
 cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s) {
+    if (!key64) {   // the two-phase schedule: counting, scan and segment records in one pass
+        k_segments<MAXF><<<persistent_grid((const void*)k_segments<MAXF>, kDupThreads), kDupThreads, 0, s>>>(m);
+        return cudaGetLastError();
+    }
     if (key64)
         k_count_tiles<true, MAXF><<<persistent_grid((const void*)k_count_tiles<true, MAXF>, kDupThreads), kDupThreads,
                                     0, s>>>(m);

@@ -79,7 +79,9 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->tau = take(nn * sizeof(float));
     for (int k = 0; k < 2; ++k) { L->gkey[k] = take(nn * 4); L->gval[k] = take(nn * 4); }
     L->pairs = take(nn * sizeof(unsigned long long));
-    L->scan_lb_rows = (nn + kPairChunk - 1) / kPairChunk;
+    // one look-back word per chunk of the segment pass (kDupThreads entries; the KEY64
+    // schedule's scan takes kPairChunk entries per word and needs fewer)
+    L->scan_lb_rows = (nn + kDupThreads - 1) / kDupThreads;
     L->scan_lb = take(L->scan_lb_rows * sizeof(unsigned long long));
     const size_t rows_n = (nn + kSortTile - 1) / kSortTile, rows_c = (cc + kSortTileMin - 1) / kSortTileMin;
     L->sort_lb_rows = rows_n > rows_c ? rows_n : rows_c;

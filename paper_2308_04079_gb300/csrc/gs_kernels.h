@@ -172,7 +172,7 @@ struct ScanArgs {
     uint32_t* num_segments;
     unsigned long long capacity;
     uint32_t* hist;            // [4][256] depth-digit histograms (KEY64 only)
-    unsigned long long* lookback;  // [entries / kPairChunk], zeroed
+    unsigned long long* lookback;  // [entries / kDupThreads], zeroed
     uint32_t* chunk_counter;
     gs_device_status* status;
 };
