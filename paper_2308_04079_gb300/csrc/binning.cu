@@ -698,14 +698,18 @@ __global__ void __launch_bounds__(kDupThreads) k_write_segments(const __grid_con
 // once (8-lane groups, as k_count_tiles), keeps the first kSegSlots non-empty rows of every
 // splat in shared memory, scans (segments, instances) over the chunk, finds the chunk's global
 // offsets by decoupled look-back over its predecessors (bounded spin), and writes the segment
-// records in segment order.  Rows beyond the slots (large splats) are evaluated a second time.
+// records in segment order.  Rows after a splat's last kept row (large splats) are evaluated
+// after the look-back, resuming at that row, so every row is evaluated once.
 // ---------------------------------------------------------------------------------------
-constexpr int kSegSlots = 8;
+constexpr int kSegSlots = 16;   // rows kept per splat (measured on a 1080p frame: 16 beats 8)
+constexpr size_t kSegSlotBytes = sizeof(uint2) * kDupThreads * kSegSlots;
 
 template <int MAXF>
 __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
     constexpr int ROUNDS = 32 / kGroups;
-    __shared__ uint2 s_slot[kDupThreads][kSegSlots];   // (tile id, instances of the splat's earlier rows)
+    // (tile id, instances of the splat's earlier rows) of the kept rows, kSegSlots per entry
+    extern __shared__ __align__(16) uint2 s_slot[];
+    __shared__ uint2 s_resume[kDupThreads];            // after the last kept row: (rectangle row, instances)
     __shared__ uint32_t s_seg[kDupThreads + 1];        // chunk-local exclusive segment prefix, [256] = total
     __shared__ uint32_t s_inst[kDupThreads];           // chunk-local exclusive instance prefix
     __shared__ uint32_t s_gid[kDupThreads];
@@ -778,7 +782,10 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
                     if (ok) {
                         const uint32_t k = cs + is - 1u;
                         if (k < (uint32_t)kSegSlots)
-                            s_slot[e_local][k] = make_uint2((uint32_t)ty * tiles_x + (uint32_t)txa, ct + it - len);
+                            s_slot[e_local * kSegSlots + k] =
+                                make_uint2((uint32_t)ty * tiles_x + (uint32_t)txa, ct + it - len);
+                        if (k == (uint32_t)kSegSlots - 1u)
+                            s_resume[e_local] = make_uint2((uint32_t)(base + sub + 1), ct + it);
                     }
                     cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
                     ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
@@ -870,25 +877,28 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
                 const uint32_t k = sl - s_seg[e];
                 const unsigned long long seg = base_s + sl;
                 if (k < (uint32_t)kSegSlots && seg < cap) {
-                    const uint2 rec = s_slot[e][k];
+                    const uint2 rec = s_slot[e * kSegSlots + k];
                     a.seg_off[seg] = (uint32_t)min(base_t + s_inst[e] + rec.y, cap);
                     a.seg_tile[seg] = rec.x;
                     a.seg_gid[seg] = s_gid[e];
                 }
             }
-            // rows beyond the slots: evaluated again by the splat's row group
+            // rows after the last kept one: evaluated by the splat's row group, resuming where the
+            // first evaluation kept its last row
             if (__any_sync(0xffffffffu, nseg > (uint32_t)kSegSlots)) {   // warp-uniform
                 for (int r = 0; r < ROUNDS; ++r) {
                     const int src = r * kGroups + grp;
                     const int e_local = warp * 32 + src;
                     const uint32_t ns = __shfl_sync(0xffffffffu, nseg, src);
                     const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, src);
-                    const int rows = ns > (uint32_t)kSegSlots ? jb.rows : 0;
+                    const bool more = ns > (uint32_t)kSegSlots;
+                    const int rows = more ? jb.rows : 0;
                     const unsigned long long seg0 = base_s + s_seg[e_local];
                     const unsigned long long off0 = base_t + s_inst[e_local];
                     const uint32_t gid = s_gid[e_local];
-                    uint32_t cs = 0, ct = 0;
-                    for (int base = 0; __any_sync(0xffffffffu, base < rows); base += kRowLanes) {
+                    const uint2 rs = more ? s_resume[e_local] : make_uint2(0u, 0u);
+                    uint32_t cs = more ? (uint32_t)kSegSlots : 0u, ct = rs.y;
+                    for (int base = (int)rs.x; __any_sync(0xffffffffu, base < rows); base += kRowLanes) {
                         const int ty = jb.y0 + base + sub;
                         int txa = 0, txb = 0;
                         const bool ok = base + sub < rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2,
@@ -1127,7 +1137,17 @@ cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_ch
 template <int MAXF>
 cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s) {
     if (!key64) {   // the two-phase schedule: counting, scan and segment records in one pass
-        k_segments<MAXF><<<persistent_grid((const void*)k_segments<MAXF>, kDupThreads), kDupThreads, 0, s>>>(m);
+        static bool attr = false;   // the kept-row table may exceed the 48 KB default
+        if (!attr) {
+            cudaFuncSetAttribute((const void*)k_segments<MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSegSlotBytes);
+            attr = true;
+        }
+        int per = 1, dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_segments<MAXF>, kDupThreads, kSegSlotBytes);
+        k_segments<MAXF><<<sms * (per > 0 ? per : 1), kDupThreads, kSegSlotBytes, s>>>(m);
         return cudaGetLastError();
     }
     if (key64)
