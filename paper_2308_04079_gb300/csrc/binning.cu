@@ -1098,6 +1098,68 @@ __global__ void __launch_bounds__(256) k_ranges(const __grid_constant__ Multi<Ra
     }
 }
 
+// The same for uint32 tile ids, HBM-friendly: a thread takes two quads of keys per unit, each
+// with one 16-byte load, plus the key in front of the quad (an L1 hit: the neighbouring
+// thread's quad).
+template <int MAXF>
+__global__ void __launch_bounds__(256) k_ranges32(const __grid_constant__ Multi<RangesArgs, MAXF> m) {
+    constexpr uint32_t QUADS = 2;
+    constexpr uint32_t UNIT = 256 * QUADS * 4;   // positions per unit
+    __shared__ uint32_t s_ubase[MAXF + 1];
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        uint32_t units = 0;
+        if (tid < m.frames) {
+            const RangesArgs& af = m.a[tid];
+            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout)))
+                units = (uint32_t)((min((unsigned long long)af.status->num_instances, af.capacity) + UNIT - 1) / UNIT);
+        }
+        const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
+        if (tid < m.frames) s_ubase[tid + 1] = inc;
+        if (tid == 0) s_ubase[0] = 0;
+    }
+    __syncthreads();
+    const uint32_t total = s_ubase[m.frames];
+    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
+        int f = 0;
+        if (MAXF > 1)
+            while (f + 1 < m.frames && s_ubase[f + 1] <= u) ++f;
+        const RangesArgs& a = m.a[f];
+        const uint32_t K = (uint32_t)min((unsigned long long)a.status->num_instances, a.capacity);
+        const uint32_t* const keys = reinterpret_cast<const uint32_t*>(a.keys);
+        uint32_t* const ranges = a.ranges;
+        const uint32_t tiles = (uint32_t)a.tiles;
+        uint32_t k[QUADS][4], prev[QUADS], i0[QUADS];
+#pragma unroll
+        for (uint32_t h = 0; h < QUADS; ++h) {
+            i0[h] = ((u - s_ubase[f]) * (UNIT / 4) + h * 256 + (uint32_t)tid) * 4;
+            if (i0[h] + 4 <= K) {
+                const uint4 q = reinterpret_cast<const uint4*>(keys)[i0[h] / 4];
+                k[h][0] = q.x; k[h][1] = q.y; k[h][2] = q.z; k[h][3] = q.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) k[h][e] = i0[h] + e < K ? keys[i0[h] + e] : 0xFFFFFFFFu;
+            }
+            prev[h] = (i0[h] > 0 && i0[h] <= K) ? keys[i0[h] - 1] : 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (uint32_t h = 0; h < QUADS; ++h) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t i = i0[h] + e;
+                if (i >= K) break;
+                const uint32_t t = k[h][e];
+                const uint32_t tp = e == 0 ? (i > 0 ? prev[h] : 0xFFFFFFFFu) : k[h][e - 1];
+                if (t != tp) {
+                    if (t < tiles) ranges[2 * t] = i;
+                    if (i > 0 && tp < tiles) ranges[2 * tp + 1] = i;
+                }
+                if (i + 1 == K && t < tiles) ranges[2 * t + 1] = K;
+            }
+        }
+    }
+}
+
 // Zero the look-back rows of the first instance-sort pass (row count depends on the
 // device-side instance count).
 template <int MAXF>
@@ -1167,7 +1229,7 @@ cudaError_t launch_ranges(const Multi<RangesArgs, MAXF>& m, bool key64, cudaStre
     if (key64)
         k_ranges<true, MAXF><<<persistent_grid((const void*)k_ranges<true, MAXF>, 256), 256, 0, s>>>(m);
     else
-        k_ranges<false, MAXF><<<persistent_grid((const void*)k_ranges<false, MAXF>, 256), 256, 0, s>>>(m);
+        k_ranges32<MAXF><<<persistent_grid((const void*)k_ranges32<MAXF>, 256), 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 
