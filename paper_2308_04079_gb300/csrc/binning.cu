@@ -1199,12 +1199,9 @@ cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_ch
 template <int MAXF>
 cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s) {
     if (!key64) {   // the two-phase schedule: counting, scan and segment records in one pass
-        static bool attr = false;   // the kept-row table may exceed the 48 KB default
-        if (!attr) {
+        if (kSegSlotBytes > 40 * 1024)   // a kept-row table above the default dynamic limit opts in
             cudaFuncSetAttribute((const void*)k_segments<MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSegSlotBytes);
-            attr = true;
-        }
         int per = 1, dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
