@@ -124,6 +124,21 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 # Our arm
 # ------------------------------------------------------------------------------------------
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks (the slowest rank's time); x itself for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def launches_per_step(layout) -> int:
     """Kernels one step launches: preprocess; binning = two-phase: depth histogram + depth
     passes + one segment pass (count, scan and records) + emit + sort-prepare + instance passes
@@ -239,12 +254,9 @@ def run_ours(args, rank, world, local_rank):
     total_ms = t0.elapsed_time(t1)
     stage_ms = {s: float(np.mean([events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps)]))
                 for i, s in enumerate(stages)}
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(tmax.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_rate(world, args.steps, total_ms)
 
     # ---- end to end through the public API with host buffers --------------------------------
     e2e = None
@@ -659,10 +671,7 @@ def run_e2e(args, g, gt, fr, dimg, bg, img, T, last, grads, stream, world, dev):
         stream.wait_event(e)
     z.record(stream)
     torch.cuda.synchronize()
-    ms = torch.tensor([a.elapsed_time(z)], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms, op=torch.distributed.ReduceOp.MAX)
-    val = world * steps / (float(ms.item()) / 1e3)
+    val = job_rate(world, steps, max_over_ranks(a.elapsed_time(z), world, dev))
     return {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "steps": steps, "pipelining": "2 steps in flight: H2D, compute and D2H on separate streams"}
 
