@@ -14,7 +14,9 @@
 // so dSSIM/dx = (w * a) + 2 x (w * b) + y (w * c) with the coefficient maps a, b, c of
 // dS/dmx, dS/dExx, dS/dExy (w is symmetric).  Pass 1 computes the moments, S, L1 and the
 // coefficient maps; pass 2 windows the coefficient maps and forms dL/dx.  Both passes are
-// separable 11-tap convolutions on 32x32 output tiles staged with their halo in shared memory.
+// separable 11-tap convolutions on 32x32 output tiles (the three channels in turn), staged with
+// their halo in shared memory; a thread computes consecutive outputs of each 1-D window from
+// registers, reading each input once for all of them.
 #include "gs_device.cuh"
 #include "gs_kernels.h"
 
@@ -24,6 +26,9 @@ namespace {
 constexpr int kWin = 11, kHalf = 5;
 constexpr int kTile = 32;
 constexpr int kIn = kTile + 2 * kHalf;   // 42
+constexpr int kRowsPer = 4;              // output rows per thread in the vertical passes (256 threads)
+constexpr int kColsPer = 2;              // output columns per thread in the horizontal passes
+static_assert(kTile * kTile == 256 * kRowsPer, "one row group per thread");
 
 // Normalised 1-D Gaussian window, sigma 1.5 (the 2-D window is its outer product), computed by
 // every block into shared memory.
@@ -62,51 +67,77 @@ __global__ void __launch_bounds__(256) k_ssim_forward(LossArgs a) {
     const int tid = threadIdx.x;
     const int bx = blockIdx.x * kTile, by = blockIdx.y * kTile;
     const size_t P = (size_t)a.W * a.H;
-    double sum_s = 0.0, sum_l1 = 0.0;
-    for (int ch = 0; ch < 3; ++ch) {
-        const float* x = a.img + ch * P;
-        const float* y = a.target + ch * P;
-        __syncthreads();
-        for (int k = tid; k < kIn * kIn; k += blockDim.x) {
-            const int r = k / kIn, cc = k % kIn;
-            s_x[r][cc] = load0(x, a.W, a.H, bx + cc - kHalf, by + r - kHalf);
-            s_y[r][cc] = load0(y, a.W, a.H, bx + cc - kHalf, by + r - kHalf);
-        }
-        __syncthreads();
-        for (int k = tid; k < kIn * kTile; k += blockDim.x) {
-            const int r = k / kTile, cc = k % kTile;
-            float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
+    __syncthreads();
+    float w[kWin];   // the window in registers
 #pragma unroll
-            for (int t = 0; t < kWin; ++t) {
-                const float w = c_win[t], xv = s_x[r][cc + t], yv = s_y[r][cc + t];
-                h0 += w * xv;
-                h1 += w * yv;
-                h2 += w * xv * xv;
-                h3 += w * yv * yv;
-                h4 += w * xv * yv;
-            }
-            s_h[0][r][cc] = h0;
-            s_h[1][r][cc] = h1;
-            s_h[2][r][cc] = h2;
-            s_h[3][r][cc] = h3;
-            s_h[4][r][cc] = h4;
+    for (int t = 0; t < kWin; ++t) w[t] = c_win[t];
+    // per-thread sums of at most 3 x 4 terms in [-1, 1] and [0, 1] stay in fp32; blocks and the
+    // grid sum in fp64
+    float sum_s = 0.f, sum_l1 = 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+    const float* x = a.img + ch * P;
+    const float* y = a.target + ch * P;
+    __syncthreads();   // the previous channel's reads of s_x, s_y and s_h are done
+    for (int k = tid; k < kIn * kIn; k += blockDim.x) {
+        const int r = k / kIn, cc = k % kIn;
+        s_x[r][cc] = load0(x, a.W, a.H, bx + cc - kHalf, by + r - kHalf);
+        s_y[r][cc] = load0(y, a.W, a.H, bx + cc - kHalf, by + r - kHalf);
+    }
+    __syncthreads();
+    // horizontal windows: a thread takes kColsPer consecutive columns of one row, reading the
+    // kColsPer + 10 inputs they need once
+    for (int k = tid; k < kIn * (kTile / kColsPer); k += blockDim.x) {
+        const int r = k / (kTile / kColsPer), c0 = (k % (kTile / kColsPer)) * kColsPer;
+        float h[5][kColsPer];
+#pragma unroll
+        for (int mm = 0; mm < 5; ++mm)
+#pragma unroll
+            for (int j = 0; j < kColsPer; ++j) h[mm][j] = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < kColsPer + kWin - 1; ++cc) {
+            const float xv = s_x[r][c0 + cc], yv = s_y[r][c0 + cc];
+            const float xx = xv * xv, yy = yv * yv, xy = xv * yv;
+#pragma unroll
+            for (int j = 0; j < kColsPer; ++j)
+                if (cc - j >= 0 && cc - j < kWin) {
+                    const float wt = w[cc - j];
+                    h[0][j] += wt * xv;
+                    h[1][j] += wt * yv;
+                    h[2][j] += wt * xx;
+                    h[3][j] += wt * yy;
+                    h[4][j] += wt * xy;
+                }
         }
-        __syncthreads();
-        const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-        for (int k = tid; k < kTile * kTile; k += blockDim.x) {
-            const int r = k / kTile, cc = k % kTile;
+#pragma unroll
+        for (int mm = 0; mm < 5; ++mm)
+#pragma unroll
+            for (int j = 0; j < kColsPer; ++j) s_h[mm][r][c0 + j] = h[mm][j];
+    }
+    __syncthreads();
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    // vertical windows: a thread takes kRowsPer consecutive rows of one column, reading the
+    // kRowsPer + 10 rows they need once per map
+    {
+        const int cc = tid % kTile, r0 = (tid / kTile) * kRowsPer;
+        float mom[5][kRowsPer];
+#pragma unroll
+        for (int mm = 0; mm < 5; ++mm) {
+#pragma unroll
+            for (int j = 0; j < kRowsPer; ++j) mom[mm][j] = 0.f;
+#pragma unroll
+            for (int rr = 0; rr < kRowsPer + kWin - 1; ++rr) {
+                const float v = s_h[mm][r0 + rr][cc];
+#pragma unroll
+                for (int j = 0; j < kRowsPer; ++j)
+                    if (rr - j >= 0 && rr - j < kWin) mom[mm][j] += w[rr - j] * v;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRowsPer; ++j) {
+            const int r = r0 + j;
             const int px = bx + cc, py = by + r;
             if (px >= a.W || py >= a.H) continue;
-            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
-#pragma unroll
-            for (int t = 0; t < kWin; ++t) {
-                const float w = c_win[t];
-                mx += w * s_h[0][r + t][cc];
-                my += w * s_h[1][r + t][cc];
-                exx += w * s_h[2][r + t][cc];
-                eyy += w * s_h[3][r + t][cc];
-                exy += w * s_h[4][r + t][cc];
-            }
+            const float mx = mom[0][j], my = mom[1][j], exx = mom[2][j], eyy = mom[3][j], exy = mom[4][j];
             const float A1 = 2.f * mx * my + C1, A2 = 2.f * (exy - mx * my) + C2;
             const float B1 = mx * mx + my * my + C1, B2 = (exx - mx * mx) + (eyy - my * my) + C2;
             const float inv = 1.f / (B1 * B2);
@@ -120,14 +151,16 @@ __global__ void __launch_bounds__(256) k_ssim_forward(LossArgs a) {
             sum_l1 += fabsf(s_x[r + kHalf][cc + kHalf] - s_y[r + kHalf][cc + kHalf]);
         }
     }
+    }
     // block sums (fixed order), then the last block adds the tiles in index order
+    double d_s = sum_s, d_l1 = sum_l1;
     for (int o = 16; o > 0; o >>= 1) {
-        sum_s += __shfl_xor_sync(0xffffffffu, sum_s, o);
-        sum_l1 += __shfl_xor_sync(0xffffffffu, sum_l1, o);
+        d_s += __shfl_xor_sync(0xffffffffu, d_s, o);
+        d_l1 += __shfl_xor_sync(0xffffffffu, d_l1, o);
     }
     if ((tid & 31) == 0) {
-        s_red[0][tid >> 5] = sum_s;
-        s_red[1][tid >> 5] = sum_l1;
+        s_red[0][tid >> 5] = d_s;
+        s_red[1][tid >> 5] = d_l1;
     }
     __syncthreads();
     const int blocks = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -141,12 +174,29 @@ __global__ void __launch_bounds__(256) k_ssim_forward(LossArgs a) {
         s_last = atomicAdd(a.done, 1u) == (unsigned)(blocks - 1);
     }
     __syncthreads();
-    if (s_last && tid == 0) {
+    if (s_last) {   // the last block: its threads sum the tiles' partials in a fixed order
         __threadfence();
+        double p0 = 0.0, p1 = 0.0;
+        for (int b = tid; b < blocks; b += blockDim.x) {
+            p0 += __ldcg(a.partial + 2 * b);
+            p1 += __ldcg(a.partial + 2 * b + 1);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) {
+            s_red[0][tid >> 5] = p0;
+            s_red[1][tid >> 5] = p1;
+        }
+        __syncthreads();
+    }
+    if (s_last && tid == 0) {
         double s0 = 0.0, s1 = 0.0;
-        for (int b = 0; b < blocks; ++b) {
-            s0 += __ldcg(a.partial + 2 * b);
-            s1 += __ldcg(a.partial + 2 * b + 1);
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            s0 += s_red[0][k];
+            s1 += s_red[1][k];
         }
         const double n = 3.0 * (double)P;
         const double ssim = s0 / n, l1 = s1 / n;
@@ -166,49 +216,70 @@ __global__ void __launch_bounds__(256) k_ssim_backward(LossArgs a) {
     const int bx = blockIdx.x * kTile, by = blockIdx.y * kTile;
     const size_t P = (size_t)a.W * a.H;
     const float invN = 1.0f / (3.0f * (float)P);
+    __syncthreads();
+    float w[kWin];   // the window in registers
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) w[t] = c_win[t];
     for (int ch = 0; ch < 3; ++ch) {
-        const float* coef = a.coef + (size_t)ch * 3 * P;
-        __syncthreads();
-        for (int k = tid; k < kIn * kIn; k += blockDim.x) {
-            const int r = k / kIn, cc = k % kIn;
+    const float* coef = a.coef + (size_t)ch * 3 * P;
+    __syncthreads();   // the previous channel's reads of s_c and s_h are done
+    for (int k = tid; k < kIn * kIn; k += blockDim.x) {
+        const int r = k / kIn, cc = k % kIn;
 #pragma unroll
-            for (int mmap = 0; mmap < 3; ++mmap)
-                s_c[mmap][r][cc] = load0(coef + mmap * P, a.W, a.H, bx + cc - kHalf, by + r - kHalf);
-        }
-        __syncthreads();
-        for (int k = tid; k < kIn * kTile; k += blockDim.x) {
-            const int r = k / kTile, cc = k % kTile;
-            float h0 = 0.f, h1 = 0.f, h2 = 0.f;
+        for (int mmap = 0; mmap < 3; ++mmap)
+            s_c[mmap][r][cc] = load0(coef + mmap * P, a.W, a.H, bx + cc - kHalf, by + r - kHalf);
+    }
+    __syncthreads();
+    for (int k = tid; k < kIn * (kTile / kColsPer); k += blockDim.x) {
+        const int r = k / (kTile / kColsPer), c0 = (k % (kTile / kColsPer)) * kColsPer;
+        float h[3][kColsPer];
 #pragma unroll
-            for (int t = 0; t < kWin; ++t) {
-                const float w = c_win[t];
-                h0 += w * s_c[0][r][cc + t];
-                h1 += w * s_c[1][r][cc + t];
-                h2 += w * s_c[2][r][cc + t];
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int j = 0; j < kColsPer; ++j) h[mm][j] = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < kColsPer + kWin - 1; ++cc) {
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm) {
+                const float v = s_c[mm][r][c0 + cc];
+#pragma unroll
+                for (int j = 0; j < kColsPer; ++j)
+                    if (cc - j >= 0 && cc - j < kWin) h[mm][j] += w[cc - j] * v;
             }
-            s_h[0][r][cc] = h0;
-            s_h[1][r][cc] = h1;
-            s_h[2][r][cc] = h2;
         }
-        __syncthreads();
-        for (int k = tid; k < kTile * kTile; k += blockDim.x) {
-            const int r = k / kTile, cc = k % kTile;
-            const int px = bx + cc, py = by + r;
-            if (px >= a.W || py >= a.H) continue;
-            float ca = 0.f, cb = 0.f, cc2 = 0.f;
 #pragma unroll
-            for (int t = 0; t < kWin; ++t) {
-                const float w = c_win[t];
-                ca += w * s_h[0][r + t][cc];
-                cb += w * s_h[1][r + t][cc];
-                cc2 += w * s_h[2][r + t][cc];
+        for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+            for (int j = 0; j < kColsPer; ++j) s_h[mm][r][c0 + j] = h[mm][j];
+    }
+    __syncthreads();
+        {
+            const int cc = tid % kTile, r0 = (tid / kTile) * kRowsPer;
+            float acc[3][kRowsPer];
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm) {
+#pragma unroll
+                for (int j = 0; j < kRowsPer; ++j) acc[mm][j] = 0.f;
+#pragma unroll
+                for (int rr = 0; rr < kRowsPer + kWin - 1; ++rr) {
+                    const float v = s_h[mm][r0 + rr][cc];
+#pragma unroll
+                    for (int j = 0; j < kRowsPer; ++j)
+                        if (rr - j >= 0 && rr - j < kWin) acc[mm][j] += w[rr - j] * v;
+                }
             }
-            const size_t q = (size_t)py * a.W + px;
-            const float xv = a.img[ch * P + q], yv = a.target[ch * P + q];
-            const float d = xv - yv;
-            const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            const float dssim = ca + 2.f * xv * cb + yv * cc2;
-            a.dL_dimg[ch * P + q] = (1.f - a.lambda) * invN * sgn - a.lambda * invN * dssim;
+#pragma unroll
+            for (int j = 0; j < kRowsPer; ++j) {
+                const int r = r0 + j;
+                const int px = bx + cc, py = by + r;
+                if (px >= a.W || py >= a.H) continue;
+                const size_t q = (size_t)py * a.W + px;
+                const float xv = a.img[ch * P + q], yv = a.target[ch * P + q];
+                const float d = xv - yv;
+                const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                const float dssim = acc[0][j] + 2.f * xv * acc[1][j] + yv * acc[2][j];
+                a.dL_dimg[ch * P + q] = (1.f - a.lambda) * invN * sgn - a.lambda * invN * dssim;
+            }
         }
     }
 }
