@@ -693,33 +693,31 @@ __global__ void __launch_bounds__(kDupThreads) k_write_segments(const __grid_con
 }
 
 // ---------------------------------------------------------------------------------------
-// DuplicateWithKeys passes 1-3 in one kernel (the two-phase schedule): chunks of kDupThreads
-// depth-ordered entries are claimed in order; a chunk evaluates its splats' reachable tile rows
-// once (8-lane groups, as k_count_tiles), keeps the first kSegSlots non-empty rows of every
-// splat in shared memory, scans (segments, instances) over the chunk, finds the chunk's global
-// offsets by decoupled look-back over its predecessors (bounded spin), and writes the segment
-// records in segment order.  Rows after a splat's last kept row (large splats) are evaluated
-// after the look-back, resuming at that row, so every row is evaluated once.
+// DuplicateWithKeys passes 1-3 in one kernel (the two-phase schedule).  A chunk of kDupThreads
+// depth-ordered entries is claimed in order; the tile rows of its splats' rectangles are
+// numbered in entry order and thread t evaluates rows t, t + kDupThreads, ... (so large and
+// small splats load the block evenly), keeping (first tile column, length) of the first
+// kSegRowCap rows in shared memory; a block reduction gives the chunk's (segments, instances),
+// a decoupled look-back over the predecessors (bounded spin) its global offsets, and a block
+// scan over the rows in order the segment index and first instance of every non-empty row,
+// whose record is then written.  Rows past kSegRowCap (chunks of very large splats) are
+// evaluated a second time in that last pass.
 // ---------------------------------------------------------------------------------------
-constexpr int kSegSlots = 16;   // rows kept per splat (measured on a 1080p frame: 16 beats 8)
-constexpr size_t kSegSlotBytes = sizeof(uint2) * kDupThreads * kSegSlots;
+constexpr int kSegRowCap = 4096;
 
 template <int MAXF>
 __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant__ Multi<ScanArgs, MAXF> m) {
-    constexpr int ROUNDS = 32 / kGroups;
-    // (tile id, instances of the splat's earlier rows) of the kept rows, kSegSlots per entry
-    extern __shared__ __align__(16) uint2 s_slot[];
-    __shared__ uint2 s_resume[kDupThreads];            // after the last kept row: (rectangle row, instances)
-    __shared__ uint32_t s_seg[kDupThreads + 1];        // chunk-local exclusive segment prefix, [256] = total
-    __shared__ uint32_t s_inst[kDupThreads];           // chunk-local exclusive instance prefix
-    __shared__ uint32_t s_gid[kDupThreads];
+    __shared__ uint32_t s_rowpre[kDupThreads + 1];   // first row of every entry's splat; [256] = rows
+    __shared__ float s_rf[8][kDupThreads];           // per entry: reach state (6), screen mean (u, v)
+    __shared__ uint32_t s_x01[kDupThreads], s_y0[kDupThreads], s_gid[kDupThreads];
+    __shared__ uint32_t s_row[kSegRowCap];           // per row: first tile column | length << 16
     __shared__ unsigned long long s_scan[33];
     __shared__ uint32_t s_chunk;
     __shared__ unsigned long long s_base_s, s_base_t;
-    __shared__ uint32_t s_fbase[MAXF + 1];             // chunks of frames [0, f)
+    __shared__ uint32_t s_fbase[MAXF + 1];           // chunks of frames [0, f)
     __shared__ __align__(16) ScanArgs s_args;
     __shared__ int s_argf;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, sub = lane % kRowLanes, grp = lane / kRowLanes;
+    const int tid = threadIdx.x;
     if (tid < 32) {
         uint32_t ch = 0;
         if (tid < m.frames) {
@@ -737,6 +735,7 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
     }
     __syncthreads();
     const uint32_t total = s_fbase[m.frames];
+    constexpr unsigned long long kOne = 1ull << kLocalShift;   // one segment in the packed pair
     for (;;) {
         if (tid == 0) s_chunk = atomicAdd(m.a[0].chunk_counter, 1u);
         __syncthreads();
@@ -750,65 +749,65 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
             if (a.count_dev) count = min(count, *a.count_dev);
             const uint32_t chunk = g - s_fbase[f];
             const uint32_t chunks = s_fbase[f + 1] - s_fbase[f];
-            const uint32_t j = chunk * kDupThreads + tid;
-            const EntrySplat sp = load_entry(a, j, count);
-            s_gid[tid] = sp.gid;
+            const unsigned long long cap = a.capacity;
             const int tw_log2 = a.cam.tile_w == 16 ? 4 : 3;
             const uint32_t tiles_x = (uint32_t)a.cam.tiles_x;
 
-            // rows of the warp's 32 splats, kGroups splats at a time
-            uint32_t nseg = 0, ntile = 0;
-            for (int r = 0; r < ROUNDS; ++r) {
-                const int src = r * kGroups + grp;
-                const int e_local = warp * 32 + src;
-                const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, src);
-                uint32_t cs = 0, ct = 0;   // segments / instances of the rows before this pass
-                for (int base = 0; __any_sync(0xffffffffu, base < jb.rows); base += kRowLanes) {
-                    const int ty = jb.y0 + base + sub;
-                    int txa = 0, txb = 0;
-                    const bool ok = base + sub < jb.rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2,
-                                                                     a.cam.tile_h, jb.x0, jb.x1, txa, txb);
-                    const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
-                    uint32_t is = ok ? 1u : 0u, it = len;   // inclusive scans over the group's lanes
-#pragma unroll
-                    for (int d = 1; d < kRowLanes; d <<= 1) {
-                        const uint32_t ns = __shfl_up_sync(0xffffffffu, is, d, kRowLanes);
-                        const uint32_t nt = __shfl_up_sync(0xffffffffu, it, d, kRowLanes);
-                        if (sub >= d) {
-                            is += ns;
-                            it += nt;
-                        }
-                    }
-                    if (ok) {
-                        const uint32_t k = cs + is - 1u;
-                        if (k < (uint32_t)kSegSlots)
-                            s_slot[e_local * kSegSlots + k] =
-                                make_uint2((uint32_t)ty * tiles_x + (uint32_t)txa, ct + it - len);
-                        if (k == (uint32_t)kSegSlots - 1u)
-                            s_resume[e_local] = make_uint2((uint32_t)(base + sub + 1), ct + it);
-                    }
-                    cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
-                    ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
-                }
-                // owner lane r * kGroups + q takes the totals of group q
-                const int from = (lane % kGroups) * kRowLanes;
-                const uint32_t ts = __shfl_sync(0xffffffffu, cs, from), tt = __shfl_sync(0xffffffffu, ct, from);
-                if (lane / kGroups == r) {
-                    nseg = ts;
-                    ntile = tt;
-                }
+            // this thread's entry: splat state and rectangle rows
+            {
+                const EntrySplat sp = load_entry(a, chunk * kDupThreads + tid, count);
+                s_rf[0][tid] = sp.e.tm;
+                s_rf[1][tid] = sp.e.ylim;
+                s_rf[2][tid] = sp.e.ystar;
+                s_rf[3][tid] = sp.e.inv11;
+                s_rf[4][tid] = sp.e.l21;
+                s_rf[5][tid] = sp.e.l22;
+                s_rf[6][tid] = sp.mean.x;
+                s_rf[7][tid] = sp.mean.y;
+                s_x01[tid] = sp.rx;
+                s_y0[tid] = sp.ry & 0xFFFFu;
+                s_gid[tid] = sp.gid;
+                const uint32_t rows = (sp.ry >> 16) - (sp.ry & 0xFFFFu);   // 0 when culled
+                unsigned long long tr;
+                const unsigned long long ex = block_exclusive_scan<unsigned long long>(rows, s_scan, &tr);
+                s_rowpre[tid] = (uint32_t)ex;
+                if (tid == 0) s_rowpre[kDupThreads] = (uint32_t)tr;
             }
+            __syncthreads();
+            const uint32_t TR = s_rowpre[kDupThreads];
+            // row fr of the chunk: its entry (the last whose first row is <= fr) and tile columns
+            auto eval_row = [&](uint32_t fr, int& e, int& ty, int& txa, int& txb) -> bool {
+                e = 0;
+#pragma unroll
+                for (int step = kDupThreads / 2; step > 0; step >>= 1)
+                    if (s_rowpre[e + step] <= fr) e += step;
+                Reach r;
+                r.tm = s_rf[0][e];
+                r.ylim = s_rf[1][e];
+                r.ystar = s_rf[2][e];
+                r.inv11 = s_rf[3][e];
+                r.l21 = s_rf[4][e];
+                r.l22 = s_rf[5][e];
+                r.any = r.tm > 0.f;
+                const uint32_t x01 = s_x01[e];
+                ty = (int)s_y0[e] + (int)(fr - s_rowpre[e]);
+                return tile_row(r, a.rect_only, s_rf[6][e], s_rf[7][e], ty, tw_log2, a.cam.tile_h,
+                                (int)(x01 & 0xFFFFu), (int)(x01 >> 16), txa, txb);
+            };
 
-            // chunk-local prefix of (segments, instances)
-            const unsigned long long run = ((unsigned long long)nseg << kLocalShift) | ntile;
+            // rows, evenly over the block; the chunk's (segments, instances)
+            unsigned long long mine = 0;
+            for (uint32_t fr = tid; fr < TR; fr += kDupThreads) {
+                int e, ty, txa = 0, txb = 0;
+                const bool ok = eval_row(fr, e, ty, txa, txb);
+                const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
+                if (fr < (uint32_t)kSegRowCap) s_row[fr] = ok ? ((uint32_t)txa | (len << 16)) : 0u;
+                if (ok) mine += kOne | len;
+            }
             unsigned long long local_total;
-            const unsigned long long excl = block_exclusive_scan<unsigned long long>(run, s_scan, &local_total);
-            s_seg[tid] = (uint32_t)(excl >> kLocalShift);
-            s_inst[tid] = (uint32_t)(excl & ((1ull << kLocalShift) - 1));
+            block_exclusive_scan<unsigned long long>(mine, s_scan, &local_total);
             const unsigned long long blk_s = local_total >> kLocalShift;
-            const unsigned long long blk_t = local_total & ((1ull << kLocalShift) - 1);
-            if (tid == 0) s_seg[kDupThreads] = (uint32_t)blk_s;
-            const unsigned long long cap = a.capacity;
+            const unsigned long long blk_t = local_total & (kOne - 1);
 
             // global base of the chunk: decoupled look-back
             if (tid < 32) {
@@ -865,70 +864,43 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
             }
             __syncthreads();
             const unsigned long long base_s = s_base_s, base_t = s_base_t;
-            const uint32_t cap32 = (uint32_t)cap;
 
-            // segment records of the kept rows, in segment order
-            const uint32_t chunk_segs = s_seg[kDupThreads];
-            for (uint32_t sl = (uint32_t)tid; sl < chunk_segs; sl += kDupThreads) {
-                int e = 0;   // the last entry whose first segment is <= sl (it owns segment sl)
+            // segment records: a block scan over the rows in order numbers the non-empty ones
+            unsigned long long carry = 0;
+            for (uint32_t rb = 0; rb < TR; rb += kDupThreads) {   // block-uniform
+                const uint32_t fr = rb + tid;
+                int e = 0, ty = 0, txa = 0;
+                uint32_t len = 0;
+                if (fr < TR) {
+                    if (fr < (uint32_t)kSegRowCap) {
+                        const uint32_t w = s_row[fr];
+                        len = w >> 16;
+                        if (len) {
 #pragma unroll
-                for (int step = kDupThreads / 2; step > 0; step >>= 1)
-                    if (s_seg[e + step] <= sl) e += step;
-                const uint32_t k = sl - s_seg[e];
-                const unsigned long long seg = base_s + sl;
-                if (k < (uint32_t)kSegSlots && seg < cap) {
-                    const uint2 rec = s_slot[e * kSegSlots + k];
-                    a.seg_off[seg] = (uint32_t)min(base_t + s_inst[e] + rec.y, cap);
-                    a.seg_tile[seg] = rec.x;
-                    a.seg_gid[seg] = s_gid[e];
-                }
-            }
-            // rows after the last kept one: evaluated by the splat's row group, resuming where the
-            // first evaluation kept its last row
-            if (__any_sync(0xffffffffu, nseg > (uint32_t)kSegSlots)) {   // warp-uniform
-                for (int r = 0; r < ROUNDS; ++r) {
-                    const int src = r * kGroups + grp;
-                    const int e_local = warp * 32 + src;
-                    const uint32_t ns = __shfl_sync(0xffffffffu, nseg, src);
-                    const RowJob jb = row_job(sp.e, sp.mean.x, sp.mean.y, sp.rx, sp.ry, src);
-                    const bool more = ns > (uint32_t)kSegSlots;
-                    const int rows = more ? jb.rows : 0;
-                    const unsigned long long seg0 = base_s + s_seg[e_local];
-                    const unsigned long long off0 = base_t + s_inst[e_local];
-                    const uint32_t gid = s_gid[e_local];
-                    const uint2 rs = more ? s_resume[e_local] : make_uint2(0u, 0u);
-                    uint32_t cs = more ? (uint32_t)kSegSlots : 0u, ct = rs.y;
-                    for (int base = (int)rs.x; __any_sync(0xffffffffu, base < rows); base += kRowLanes) {
-                        const int ty = jb.y0 + base + sub;
-                        int txa = 0, txb = 0;
-                        const bool ok = base + sub < rows && tile_row(jb.e, a.rect_only, jb.u, jb.v, ty, tw_log2,
-                                                                      a.cam.tile_h, jb.x0, jb.x1, txa, txb);
-                        const uint32_t len = ok ? (uint32_t)(txb - txa) : 0u;
-                        uint32_t is = ok ? 1u : 0u, it = len;
-#pragma unroll
-                        for (int d = 1; d < kRowLanes; d <<= 1) {
-                            const uint32_t n1 = __shfl_up_sync(0xffffffffu, is, d, kRowLanes);
-                            const uint32_t n2 = __shfl_up_sync(0xffffffffu, it, d, kRowLanes);
-                            if (sub >= d) {
-                                is += n1;
-                                it += n2;
-                            }
+                            for (int step = kDupThreads / 2; step > 0; step >>= 1)
+                                if (s_rowpre[e + step] <= fr) e += step;
+                            ty = (int)s_y0[e] + (int)(fr - s_rowpre[e]);
+                            txa = (int)(w & 0xFFFFu);
                         }
-                        if (ok) {
-                            const uint32_t k = cs + is - 1u;
-                            const unsigned long long seg = seg0 + k;
-                            if (k >= (uint32_t)kSegSlots && seg < cap) {
-                                a.seg_off[seg] = (uint32_t)min(off0 + ct + it - len, cap);
-                                a.seg_tile[seg] = (uint32_t)ty * tiles_x + (uint32_t)txa;
-                                a.seg_gid[seg] = gid;
-                            }
-                        }
-                        cs += __shfl_sync(0xffffffffu, is, kRowLanes - 1, kRowLanes);
-                        ct += __shfl_sync(0xffffffffu, it, kRowLanes - 1, kRowLanes);
+                    } else {
+                        int txb = 0;
+                        if (eval_row(fr, e, ty, txa, txb)) len = (uint32_t)(txb - txa);
                     }
                 }
+                unsigned long long round_total;
+                const unsigned long long ex = block_exclusive_scan<unsigned long long>(len ? (kOne | len) : 0ull, s_scan,
+                                                                                       &round_total);
+                if (len) {
+                    const unsigned long long seg = base_s + ((carry + ex) >> kLocalShift);
+                    const unsigned long long off = base_t + ((carry + ex) & (kOne - 1));
+                    if (seg < cap) {
+                        a.seg_off[seg] = (uint32_t)min(off, cap);
+                        a.seg_tile[seg] = (uint32_t)ty * tiles_x + (uint32_t)txa;
+                        a.seg_gid[seg] = s_gid[e];
+                    }
+                }
+                carry += round_total;
             }
-            (void)cap32;
         };
         if constexpr (MAXF == 1) {
             body(m.a[0]);
@@ -1199,14 +1171,7 @@ cudaError_t launch_onesweep(const Multi<SortPassArgs<KeyT>, MAXF>& m, int max_ch
 template <int MAXF>
 cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaStream_t s) {
     if (!key64) {   // the two-phase schedule: counting, scan and segment records in one pass
-        if (kSegSlotBytes > 40 * 1024)   // a kept-row table above the default dynamic limit opts in
-            cudaFuncSetAttribute((const void*)k_segments<MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSegSlotBytes);
-        int per = 1, dev = 0, sms = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_segments<MAXF>, kDupThreads, kSegSlotBytes);
-        k_segments<MAXF><<<sms * (per > 0 ? per : 1), kDupThreads, kSegSlotBytes, s>>>(m);
+        k_segments<MAXF><<<persistent_grid((const void*)k_segments<MAXF>, kDupThreads), kDupThreads, 0, s>>>(m);
         return cudaGetLastError();
     }
     if (key64)
