@@ -1174,12 +1174,9 @@ cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m, bool key64, cudaSt
         k_segments<MAXF><<<persistent_grid((const void*)k_segments<MAXF>, kDupThreads), kDupThreads, 0, s>>>(m);
         return cudaGetLastError();
     }
-    if (key64)
-        k_count_tiles<true, MAXF><<<persistent_grid((const void*)k_count_tiles<true, MAXF>, kDupThreads), kDupThreads,
-                                    0, s>>>(m);
-    else
-        k_count_tiles<false, MAXF><<<persistent_grid((const void*)k_count_tiles<false, MAXF>, kDupThreads),
-                                     kDupThreads, 0, s>>>(m);
+    // KEY64: count, scan and write the segment records in three passes
+    k_count_tiles<true, MAXF><<<persistent_grid((const void*)k_count_tiles<true, MAXF>, kDupThreads), kDupThreads, 0,
+                                s>>>(m);
     k_scan_pairs<MAXF><<<persistent_grid((const void*)k_scan_pairs<MAXF>, kDupThreads), kDupThreads, 0, s>>>(m);
     k_write_segments<MAXF><<<persistent_grid((const void*)k_write_segments<MAXF>, kDupThreads), kDupThreads, 0, s>>>(
         m);
