@@ -30,12 +30,6 @@ namespace gs {
 
 namespace {
 
-constexpr uint32_t kLbAgg = 0x40000000u;   // look-back word: aggregate of this chunk only
-constexpr uint32_t kLbInc = 0x80000000u;   // look-back word: inclusive prefix up to this chunk
-constexpr uint32_t kLbFlags = 0xC0000000u;
-constexpr uint32_t kLbValue = 0x3FFFFFFFu;
-constexpr int kLbWindow = 8;                // predecessors read per look-back round
-
 constexpr unsigned long long kScanAgg = 1ull << 62;
 constexpr unsigned long long kScanInc = 2ull << 62;
 constexpr unsigned long long kScanFlags = 3ull << 62;
@@ -43,10 +37,6 @@ constexpr unsigned long long kScanFlags = 3ull << 62;
 template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask) {
     return (uint32_t)(k >> shift) & mask;
-}
-
-__device__ __forceinline__ void backoff(uint32_t spins) {
-    if (spins > 64) __nanosleep(spins > 4096 ? 256 : 32);
 }
 
 }  // namespace
@@ -701,7 +691,9 @@ __global__ void __launch_bounds__(kDupThreads) k_write_segments(const __grid_con
 // a decoupled look-back over the predecessors (bounded spin) its global offsets, and a block
 // scan over the rows in order the segment index and first instance of every non-empty row,
 // whose record is then written.  Rows past kSegRowCap (chunks of very large splats) are
-// evaluated a second time in that last pass.
+// evaluated a second time in that last pass.  For the row-segmented tile sort (row_passes > 0)
+// the record is (row key, Gaussian) and the pass also counts the row digits the row passes
+// sort on, in shared memory, added to the frame's histograms when the block leaves it.
 // ---------------------------------------------------------------------------------------
 constexpr int kSegRowCap = 4096;
 
@@ -717,7 +709,22 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
     __shared__ uint32_t s_fbase[MAXF + 1];           // chunks of frames [0, f)
     __shared__ __align__(16) ScanArgs s_args;
     __shared__ int s_argf;
+    __shared__ uint32_t s_rh[2][256];                // row-digit histograms (row-key records)
     const int tid = threadIdx.x;
+    s_rh[0][tid] = 0;
+    s_rh[1][tid] = 0;
+    int rh_f = -1;                                   // frame whose row histograms s_rh holds
+    auto flush_rows = [&](int hf) {                  // block-uniform
+        __syncthreads();
+        const ScanArgs& ah = m.a[hf];
+        for (int p = 0; p < ah.row_passes; ++p) {
+            const uint32_t v = s_rh[p][tid];
+            if (v) atomicAdd(&ah.hist[p * 256 + tid], v);
+        }
+        s_rh[0][tid] = 0;
+        s_rh[1][tid] = 0;
+        __syncthreads();
+    };
     if (tid < 32) {
         uint32_t ch = 0;
         if (tid < m.frames) {
@@ -744,6 +751,10 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
         int f = 0;
         if (MAXF > 1)
             while (f + 1 < m.frames && s_fbase[f + 1] <= g) ++f;
+        if (f != rh_f) {   // block-uniform: chunks are claimed in frame order
+            if (rh_f >= 0) flush_rows(rh_f);
+            rh_f = f;
+        }
         auto body = [&](const ScanArgs& a) {
             uint32_t count = (uint32_t)a.n;
             if (a.count_dev) count = min(count, *a.count_dev);
@@ -858,7 +869,7 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
                         a.status->num_instances = (uint32_t)tiles;
                         *a.num_segments = (uint32_t)segs;
                         if (tiles > cap) atomicOr(&a.status->flags, kFlagCapacity);
-                        else a.seg_off[segs] = (uint32_t)tiles;   // end of the last segment
+                        else if (!a.row_passes) a.seg_off[segs] = (uint32_t)tiles;   // end of the last segment
                     }
                 }
             }
@@ -894,8 +905,14 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
                     const unsigned long long seg = base_s + ((carry + ex) >> kLocalShift);
                     const unsigned long long off = base_t + ((carry + ex) & (kOne - 1));
                     if (seg < cap) {
-                        a.seg_off[seg] = (uint32_t)min(off, cap);
-                        a.seg_tile[seg] = (uint32_t)ty * tiles_x + (uint32_t)txa;
+                        if (a.row_passes) {
+                            a.seg_tile[seg] = row_key((uint32_t)ty, len, (uint32_t)txa);
+                            atomicAdd(&s_rh[0][ty & 0xFF], 1u);
+                            if (a.row_passes > 1) atomicAdd(&s_rh[1][(ty >> 8) & 0xFF], 1u);
+                        } else {
+                            a.seg_off[seg] = (uint32_t)min(off, cap);
+                            a.seg_tile[seg] = (uint32_t)ty * tiles_x + (uint32_t)txa;
+                        }
                         a.seg_gid[seg] = s_gid[e];
                     }
                 }
@@ -915,6 +932,7 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
         }
         __syncthreads();   // shared state is rewritten by the next chunk
     }
+    if (rh_f >= 0) flush_rows(rh_f);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1132,17 +1150,22 @@ __global__ void __launch_bounds__(256) k_ranges32(const __grid_constant__ Multi<
     }
 }
 
-// Zero the look-back rows of the first instance-sort pass (row count depends on the
-// device-side instance count).
+// Zero the look-back rows of the first pass of the instance sort, or of the row sort of the
+// segment records (row count depends on a device-side count).
 template <int MAXF>
 __global__ void k_sort_prepare(const __grid_constant__ Multi<SortPrepareArgs, MAXF> m) {
     for (int f = 0; f < m.frames; ++f) {
         const SortPrepareArgs& a = m.a[f];
-        const uint32_t count = min((unsigned long long)a.status->num_instances, a.capacity);
+        const uint32_t count =
+            min((unsigned long long)(a.count_dev ? *a.count_dev : a.status->num_instances), a.capacity);
+        const size_t stride = (size_t)gridDim.x * blockDim.x;
         const uint32_t rows = (count + a.tile_keys - 1) / a.tile_keys;
         const size_t total = (size_t)rows * 256;
-        for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
-            a.lookback[k] = 0;
+        for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) a.lookback[k] = 0;
+        if (a.lookback2) {
+            const size_t total2 = (size_t)((count + a.tile_keys2 - 1) / a.tile_keys2) * 256;
+            for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total2; k += stride) a.lookback2[k] = 0;
+        }
     }
 }
 

@@ -29,7 +29,10 @@ struct Layout {
     size_t ikey[2], ival[2];
     size_t ranges, grad2d, pix_count, total;
     size_t sort_lb_rows, scan_lb_rows;
+    size_t tile_cnt, col_lb, col_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes, tile_passes, tile_digit_bits;
+    bool row_sort;             // row-segmented tile sort (two-phase, tiles_x <= kRowSortMaxCols)
+    int row_passes, col_bits;
 };
 
 bool valid_cfg(const gs_raster_config* c) {
@@ -66,6 +69,14 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
         L->key_passes = L->tile_passes;
         L->depth_passes = kDepthPasses;
     }
+    // Two-phase frames up to kRowSortMaxCols tile columns sort the segment records by row
+    // (one byte pass per 8 row bits) and then place the instances by column in one pass.
+    L->row_sort = cfg->sort_mode == GS_SORT_TWO_PHASE && L->tiles_x <= kRowSortMaxCols;
+    if (L->row_sort) {
+        L->row_passes = L->tiles_y > 256 ? 2 : 1;
+        L->col_bits = bits_for((uint32_t)L->tiles_x);
+        L->key_passes = L->row_passes + 1;
+    }
     const size_t nn = (size_t)(n > 0 ? n : 1);
     const size_t cc = (size_t)(cap > 0 ? cap : 1);
     size_t off = 0;
@@ -90,6 +101,10 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     // first tiles and offsets (capacity + 1 entries) in ikey[1], Gaussian ids in ival[1].
     for (int k = 0; k < 2; ++k) { L->ikey[k] = take(cc * 8 + 16); L->ival[k] = take(cc * 4); }
     L->ranges = take((size_t)L->tiles * 2 * sizeof(uint32_t));
+    L->tile_cnt = take((size_t)L->tiles * sizeof(uint32_t));
+    // column-count look-back rows, one per chunk of row-sorted segment records
+    L->col_lb_rows = L->row_sort ? (cc + kColChunk - 1) / kColChunk : 0;
+    L->col_lb = L->row_sort ? take(L->col_lb_rows * 256 * sizeof(uint32_t)) : 0;
     L->grad2d = take(nn * 12 * sizeof(float));
     // blended splats per pixel, written by the forward pass when gradients are limited
     L->pix_count = cfg->grad_limit > 0 ? take((size_t)W * H * sizeof(uint32_t)) : 0;
@@ -306,6 +321,121 @@ gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
     return GS_OK;
 }
 
+// Instance radix sort: the segment records expanded into (tile id, Gaussian) instances (KEY64:
+// (tile id << 32 | depth bits)), sorted by key, ranges by neighbour comparison.
+template <int MAXF>
+gs_status tiles_by_radix(const FrameSet<MAXF>& fs, bool key64, cudaStream_t s) {
+    Multi<RangesArgs, MAXF> tr;
+    tr.frames = fs.count;
+    Multi<EmitArgs, MAXF> e;
+    e.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v) {
+        const gs_frame* f = fs.f[v];
+        const Layout& L = fs.L[v];
+        void* ws = f->ws;
+        Control* ctl = control_of(fs, v);
+        RangesArgs& t = tr.a[v];
+        t.keys = at<void>(ws, keys_sorted_off(L));
+        t.ranges = at<uint32_t>(ws, L.ranges);
+        t.tiles = L.tiles;
+        t.capacity = f->capacity;
+        t.status = &ctl->status;
+        EmitArgs& a = e.a[v];
+        a.tile_passes = L.tile_passes;
+        a.tile_digit_bits = L.tile_digit_bits;
+        a.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
+        a.n = f->n;
+        a.seg_tile = at<uint32_t>(ws, L.ikey[1]);
+        a.seg_off = a.seg_tile + (f->capacity > 0 ? f->capacity : 1);
+        a.seg_gid = at<uint32_t>(ws, L.ival[1]);
+        a.num_segments = &ctl->counters[30];
+        a.depth = at<float>(ws, L.depth);
+        a.keys_out = at<void>(ws, L.ikey[0]);
+        a.vals_out = at<uint32_t>(ws, L.ival[0]);
+        a.capacity = f->capacity;
+        a.status = &ctl->status;
+    }
+    if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    const gs_status st = key64 ? key_sort<unsigned long long>(fs, s) : key_sort<uint32_t>(fs, s);
+    if (st != GS_OK) return st;
+    return ok(launch_ranges(tr, key64, s));
+}
+
+// Row-segmented tile sort: the segment records sorted by row, then every instance placed by
+// its column within the row (tilesort.cu).
+template <int MAXF>
+gs_status tiles_by_rows(const FrameSet<MAXF>& fs, cudaStream_t s) {
+    Multi<SortPrepareArgs, MAXF> pm;
+    pm.frames = fs.count;
+    int max_passes = 0;
+    for (int v = 0; v < fs.count; ++v) {
+        const Layout& L = fs.L[v];
+        void* ws = fs.f[v]->ws;
+        Control* ctl = control_of(fs, v);
+        pm.a[v] = SortPrepareArgs{at<uint32_t>(ws, L.sort_lb[0]), kSortTile, &ctl->status,
+                                  (unsigned long long)fs.f[v]->capacity, &ctl->counters[30],
+                                  at<uint32_t>(ws, L.col_lb), kColChunk};
+        max_passes = std::max(max_passes, L.row_passes);
+    }
+    if (launch_sort_prepare(pm, s) != cudaSuccess) return GS_ERR_CUDA;
+    Control* ctl0 = control_of(fs, 0);
+    for (int p = 0; p < max_passes; ++p) {
+        Multi<SortPassArgs<uint32_t>, MAXF> m;
+        m.frames = fs.count;
+        for (int v = 0; v < fs.count; ++v) {
+            const Layout& L = fs.L[v];
+            void* ws = fs.f[v]->ws;
+            Control* ctl = control_of(fs, v);
+            SortPassArgs<uint32_t>& a = m.a[v];
+            const bool live = p < L.row_passes;
+            a.keys_in = at<uint32_t>(ws, L.ikey[p % 2]);
+            a.vals_in = at<uint32_t>(ws, L.ival[p % 2]);
+            a.depth_src = nullptr;
+            a.radius_src = nullptr;
+            a.keys_out = at<uint32_t>(ws, L.ikey[(p + 1) % 2]);
+            a.vals_out = at<uint32_t>(ws, L.ival[(p + 1) % 2]);
+            a.count_dev = &ctl->counters[30];
+            a.count_host = live ? (uint32_t)fs.f[v]->capacity : 0u;
+            a.shift = kRowKeyRowShift + 8 * p;
+            a.mask = 0xFFu;
+            a.ballot_rank = 0;   // rows repeat across a warp's records
+            a.hist = ctl->hist_keys[p];
+            a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
+            a.lookback_next = (p + 1 < L.row_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
+            a.chunk_counter = &ctl0->counters[8 + p];
+            a.status = &ctl->status;
+        }
+        if (launch_onesweep(m, 0, s) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    Multi<ColArgs, MAXF> c;
+    c.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v) {
+        const Layout& L = fs.L[v];
+        void* ws = fs.f[v]->ws;
+        Control* ctl = control_of(fs, v);
+        ColArgs& a = c.a[v];
+        const int rp = L.row_passes;
+        a.geom = at<uint32_t>(ws, L.ikey[rp % 2]);
+        a.gid = at<uint32_t>(ws, L.ival[rp % 2]);
+        a.num_segments = &ctl->counters[30];
+        a.capacity = fs.f[v]->capacity;
+        a.tiles_x = L.tiles_x;
+        a.tiles = L.tiles;
+        a.col_bits = L.col_bits;
+        a.tile_cnt = at<uint32_t>(ws, L.tile_cnt);
+        a.lookback = at<uint32_t>(ws, L.col_lb);
+        a.ranges = at<uint32_t>(ws, L.ranges);
+        a.keys_out = at<uint32_t>(ws, L.ikey[(rp + 1) % 2]);   // = keys_sorted_off (key_passes = rp + 1)
+        a.vals_out = at<uint32_t>(ws, L.ival[(rp + 1) % 2]);
+        a.chunk_counter = &ctl0->counters[16];
+        a.status = &ctl->status;
+    }
+    if (launch_col_count(c, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (launch_tile_scan(c, s) != cudaSuccess) return GS_ERR_CUDA;
+    for (int v = 0; v < fs.count; ++v) c.a[v].chunk_counter = &ctl0->counters[17];
+    return ok(launch_col_scatter(c, s));
+}
+
 template <int MAXF>
 gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
     const bool key64 = fs.f[0]->cfg.sort_mode == GS_SORT_KEY64;
@@ -320,8 +450,10 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         clr[v].words[0] = 2;
         clr[v].ptr[1] = &ctl->counters[0];
         clr[v].words[1] = (sizeof(Control) - offsetof(Control, counters)) / 4;
-        clr[v].ptr[2] = at<uint32_t>(ws, L.ranges);
-        clr[v].words[2] = (unsigned long long)L.tiles * 2;
+        // the radix schedule leaves empty tiles' ranges as zeroed; the row sort writes every
+        // range and needs its tile counts zeroed
+        clr[v].ptr[2] = at<uint32_t>(ws, L.row_sort ? L.tile_cnt : L.ranges);
+        clr[v].words[2] = (unsigned long long)L.tiles * (L.row_sort ? 1 : 2);
         clr[v].ptr[3] = at<uint32_t>(ws, L.scan_lb);
         clr[v].words[3] = L.scan_lb_rows * 2;
     }
@@ -389,9 +521,17 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.radius = at<int>(ws, L.radius);
         a.depth = at<float>(ws, L.depth);
         a.cam = cam_k(f, L);
-        a.seg_tile = at<uint32_t>(ws, L.ikey[1]);
-        a.seg_off = a.seg_tile + (f->capacity > 0 ? f->capacity : 1);
-        a.seg_gid = at<uint32_t>(ws, L.ival[1]);
+        if (L.row_sort) {   // (row key, Gaussian) records, the input of the first row pass
+            a.seg_tile = at<uint32_t>(ws, L.ikey[0]);
+            a.seg_off = nullptr;
+            a.seg_gid = at<uint32_t>(ws, L.ival[0]);
+            a.row_passes = L.row_passes;
+        } else {
+            a.seg_tile = at<uint32_t>(ws, L.ikey[1]);
+            a.seg_off = a.seg_tile + (f->capacity > 0 ? f->capacity : 1);
+            a.seg_gid = at<uint32_t>(ws, L.ival[1]);
+            a.row_passes = 0;
+        }
         a.num_segments = &ctl->counters[30];
         a.capacity = f->capacity;
         a.hist = &ctl->hist_keys[0][0];
@@ -401,40 +541,18 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.status = &ctl->status;
     }
     if (launch_scan_tiles(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
-    Multi<RangesArgs, MAXF> tr;
-    tr.frames = fs.count;
-    Multi<EmitArgs, MAXF> e;
-    e.frames = fs.count;
+    FrameSet<MAXF> radix, rows;
     for (int v = 0; v < fs.count; ++v) {
-        const gs_frame* f = fs.f[v];
-        const Layout& L = fs.L[v];
-        void* ws = f->ws;
-        Control* ctl = control_of(fs, v);
-        RangesArgs& t = tr.a[v];
-        t.keys = at<void>(ws, keys_sorted_off(L));
-        t.ranges = at<uint32_t>(ws, L.ranges);
-        t.tiles = L.tiles;
-        t.capacity = f->capacity;
-        t.status = &ctl->status;
-        EmitArgs& a = e.a[v];
-        a.tile_passes = L.tile_passes;
-        a.tile_digit_bits = L.tile_digit_bits;
-        a.hist = key64 ? &ctl->hist_keys[4][0] : &ctl->hist_keys[0][0];
-        a.n = f->n;
-        a.seg_off = d.a[v].seg_off;
-        a.seg_tile = d.a[v].seg_tile;
-        a.seg_gid = d.a[v].seg_gid;
-        a.num_segments = d.a[v].num_segments;
-        a.depth = d.a[v].depth;
-        a.keys_out = at<void>(ws, L.ikey[0]);
-        a.vals_out = at<uint32_t>(ws, L.ival[0]);
-        a.capacity = f->capacity;
-        a.status = &ctl->status;
+        FrameSet<MAXF>& g = fs.L[v].row_sort ? rows : radix;
+        g.f[g.count] = fs.f[v];
+        g.L[g.count] = fs.L[v];
+        ++g.count;
     }
-    if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
-    st = key64 ? key_sort<unsigned long long>(fs, s) : key_sort<uint32_t>(fs, s);
-    if (st != GS_OK) return st;
-    return ok(launch_ranges(tr, key64, s));
+    if (radix.count) {
+        st = tiles_by_radix(radix, key64, s);
+        if (st != GS_OK) return st;
+    }
+    return rows.count ? tiles_by_rows(rows, s) : GS_OK;
 }
 
 template <int MAXF>

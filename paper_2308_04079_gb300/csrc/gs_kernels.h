@@ -10,6 +10,19 @@
 
 namespace gs {
 
+// Decoupled look-back words of the radix passes and the column count: a 30-bit count with
+// a flag saying whether it covers this chunk only or every chunk up to it.
+constexpr uint32_t kLbAgg = 0x40000000u;
+constexpr uint32_t kLbInc = 0x80000000u;
+constexpr uint32_t kLbFlags = 0xC0000000u;
+constexpr uint32_t kLbValue = 0x3FFFFFFFu;
+constexpr int kLbWindow = 8;                // predecessors read per look-back round
+
+// Bounded spin-waits poll at full rate for a while, then sleep between polls.
+__device__ __forceinline__ void backoff(uint32_t spins) {
+    if (spins > 64) __nanosleep(spins > 4096 ? 256 : 32);
+}
+
 // Radix sort: 256 threads, 8-bit digits; 16 keys per thread for 32-bit keys, 12 for 64-bit keys
 // (keys and values of a chunk are staged in shared memory, which must stay below 48 KB).
 constexpr int kSortThreads = 256;
@@ -59,7 +72,8 @@ __device__ __forceinline__ int find_frame(const uint32_t* base, int frames, uint
 // Control block at the start of the workspace.
 struct Control {
     gs_device_status status;
-    uint32_t counters[32];                      // chunk-claim counters: [0] scan, [1..4] depth, [8..15] keys;
+    uint32_t counters[32];                      // chunk-claim counters: [0] scan, [1..4] depth, [8..15] keys
+                                                // (or rows), [16] column count, [17] column pass;
                                                 // [30] segment records, [31] visible Gaussians
                                                 // counted by the binning stage
     uint32_t hist_depth[kDepthPasses][256];     // digit histograms, depth sort
@@ -167,11 +181,13 @@ struct ScanArgs {
     const float* depth;
     CamK cam;
     uint32_t* seg_off;         // [capacity + 1] first instance of every segment; [S] = K
-    uint32_t* seg_tile;        // [capacity] first tile id of every segment
+    uint32_t* seg_tile;        // [capacity] first tile id of every segment (row_passes > 0: row key)
     uint32_t* seg_gid;         // [capacity] Gaussian of every segment
+    int row_passes;            // > 0: row-segmented tile sort (row_key records, no seg_off, digit
+                               // histograms of the row's row_passes bytes into hist)
     uint32_t* num_segments;
     unsigned long long capacity;
-    uint32_t* hist;            // [4][256] depth-digit histograms (KEY64 only)
+    uint32_t* hist;            // [4][256] depth-digit histograms (KEY64), row digits (row_passes > 0)
     unsigned long long* lookback;  // [entries / kDupThreads], zeroed
     uint32_t* chunk_counter;
     gs_device_status* status;
@@ -207,6 +223,42 @@ struct SortPrepareArgs {
     int tile_keys;             // keys per chunk of the pass that follows
     const gs_device_status* status;
     unsigned long long capacity;
+    const uint32_t* count_dev; // keys of that pass; null: the instance count
+    uint32_t* lookback2;       // optional second table (256 words per row), or null
+    int tile_keys2;            // keys per row of the second table
+};
+
+// Row-segmented tile sort (TWO_PHASE, tiles_x <= kRowSortMaxCols).  A segment record is one
+// splat's run of reachable tiles in one tile row, as the key
+//   row_key = row << 17 | length << 8 | first column
+// (row < 4096, length <= 255, column <= 254).  The records, emitted in depth order, are
+// stable-sorted by row (1 or 2 byte passes of k_onesweep over the segments, not the instances);
+// then per chunk of kSortTile row-sorted records: per-tile instance counts and, per column,
+// the counts of the chunk's last row (look-back inside a row); a scan of the tile counts gives
+// the ranges; the column pass expands the records into instances and stable-ranks them by
+// column within their row, writing each to its final slot.
+constexpr int kRowSortMaxCols = 255;
+constexpr int kColChunk = 2048;   // row-sorted records per chunk of the count and column passes
+constexpr int kRowKeyRowShift = 17;
+__host__ __device__ constexpr uint32_t row_key(uint32_t row, uint32_t len, uint32_t col) {
+    return row << kRowKeyRowShift | len << 8 | col;
+}
+
+struct ColArgs {
+    const uint32_t* geom;          // [S] row-sorted row keys
+    const uint32_t* gid;           // [S] their Gaussians
+    const uint32_t* num_segments;  // S (device)
+    unsigned long long capacity;
+    int tiles_x, tiles;
+    int col_bits;                  // bits of tiles_x: column digits and the padding digit fit
+    uint32_t* tile_cnt;            // [tiles] instances per tile (zeroed; the count pass adds)
+    uint32_t* lookback;            // [chunks][256] per column: counts of a chunk's last row
+                                   // (inclusive within the row), zeroed before the count pass
+    uint32_t* ranges;              // [2 * tiles]
+    uint32_t* keys_out;            // [K] tile id per instance
+    uint32_t* vals_out;            // [K] Gaussian per instance
+    uint32_t* chunk_counter;       // zeroed
+    gs_device_status* status;
 };
 
 struct RenderFwdArgs {
@@ -257,6 +309,9 @@ template <int MAXF> cudaError_t launch_scan_tiles(const Multi<ScanArgs, MAXF>& m
 template <int MAXF> cudaError_t launch_ranges(const Multi<RangesArgs, MAXF>& m, bool key64, cudaStream_t s);
 template <int MAXF> cudaError_t launch_emit(const Multi<EmitArgs, MAXF>& m, bool key64, cudaStream_t s);
 template <int MAXF> cudaError_t launch_sort_prepare(const Multi<SortPrepareArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_col_count(const Multi<ColArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_tile_scan(const Multi<ColArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_col_scatter(const Multi<ColArgs, MAXF>& m, cudaStream_t s);
 template <int MAXF> cudaError_t launch_render_forward(Multi<RenderFwdArgs, MAXF>& m, cudaStream_t s);
 template <int MAXF> cudaError_t launch_render_backward(Multi<RenderBwdArgs, MAXF>& m, cudaStream_t s);
 cudaError_t launch_clear(const Multi<ClearArgs, kMaxFrames>& m, cudaStream_t s);

@@ -28,7 +28,8 @@ def _oracle_count(sp, W, H, tile=(16, 16), rule="reach"):
     return oracle.instance_count(sp["uv"], sp["radius"], W, H, tile[0], tile[1], **kw)
 
 
-def _bin_gpu(sp, W, H, tile, mode, capacity, rule="reach"):
+def _frame(sp, W, H, tile, mode, capacity, rule="reach"):
+    """A frame whose workspace holds the screen-space splats sp, ready for gs_bin_sort."""
     import torch
     from paper_2308_04079_gb300 import Frame, make_config
     n = sp["uv"].shape[0]
@@ -45,6 +46,11 @@ def _bin_gpu(sp, W, H, tile, mode, capacity, rule="reach"):
         fr.view("tau", torch.float32, n).copy_(torch.from_numpy(sp["tau"]))
         fr.view("depth", torch.float32, n).copy_(torch.from_numpy(sp["depth"]))
         fr.view("radius", torch.int32, n).copy_(torch.from_numpy(sp["radius"]))
+    return fr
+
+
+def _bin_gpu(sp, W, H, tile, mode, capacity, rule="reach"):
+    fr = _frame(sp, W, H, tile, mode, capacity, rule)
     fr.bin_sort()
     code, st = fr.status()
     return fr, code, st
@@ -57,6 +63,11 @@ CASES = [
     (4, 20000, 1000, 333, (16, 8), 25, 0),
     (5, 1, 64, 64, (16, 16), 10, 0),
     (6, 5000, 1920, 1080, (16, 16), 3, 0),
+    # two-phase frames wider than 255 tiles keep the instance radix sort; taller than 256 tile
+    # rows take two row passes; 255 columns fill every column digit but the padding one
+    (7, 20000, 4400, 200, (16, 16), 20, 0),
+    (8, 20000, 640, 4200, (16, 16), 20, 1),
+    (9, 15000, 2040, 300, (8, 8), 12, 0),
 ]
 
 
@@ -125,3 +136,31 @@ def test_bin_sort_deterministic_and_modes_agree():
         fr, code, st = _bin_gpu(sp, 1280, 720, (16, 16), mode, K)
         outs.append(fr.view("vals_sorted", torch.int32, K).cpu().numpy().copy())
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_batch_mixing_row_sort_and_radix_frames():
+    """One gs_batch_bin_sort over frames that take the row-segmented tile sort (one or two row
+    passes) and a frame wider than 255 tiles that takes the instance radix sort: every frame
+    equals the oracle bit for bit."""
+    import torch
+    from paper_2308_04079_gb300 import FrameBatch, _abi
+    shapes = [(640, 480, 30), (4400, 200, 20), (640, 4200, 20), (1920, 1080, 40)]
+    sps, frames, refs = [], [], []
+    for k, (W, H, rmax) in enumerate(shapes):
+        sp = _screen(20 + k, 12000, W, H, rmax, huge=1)
+        ref = _oracle_bin(sp, W, H, (16, 16), "reach")
+        sps.append(sp)
+        refs.append(ref)
+        frames.append(_frame(sp, W, H, (16, 16), "two_phase", len(ref[1]) + 99))
+    FrameBatch(frames, [None] * len(frames)).bin_sort()
+    torch.cuda.synchronize()
+    for fr, (keys_o, vals_o, ranges_o) in zip(frames, refs):
+        code, st = fr.status()
+        assert code == _abi.GS_OK
+        K = len(vals_o)
+        assert st.num_instances == K
+        assert np.array_equal(fr.view("vals_sorted", torch.int32, K).cpu().numpy().view(np.uint32), vals_o)
+        ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
+        assert np.array_equal(ranges, ranges_o)
+        tiles = fr.view("keys_sorted", torch.int32, K).cpu().numpy().view(np.uint32)
+        assert np.array_equal(tiles, (keys_o >> np.uint64(32)).astype(np.uint32))
