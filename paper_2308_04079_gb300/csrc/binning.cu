@@ -177,14 +177,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
             const uint32_t d = digit_of(key[i], a.shift, a.mask);
             // lanes holding the same digit: __match_any_sync costs more the more distinct
             // digits a warp holds, one ballot per digit bit costs the same for any keys; the
-            // host asks for ballots on passes whose digits are spread (the first tile pass)
+            // host asks for ballots (as many as the pass's digits have bits) on passes whose
+            // digits are spread (the first tile pass)
             uint32_t peers;
             if (a.ballot_rank) {
                 peers = 0xffffffffu;
 #pragma unroll
                 for (int b = 0; b < 8; ++b) {
-                    const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-                    peers &= ((d >> b) & 1u) ? bal : ~bal;
+                    if (b < a.ballot_rank) {
+                        const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                        peers &= ((d >> b) & 1u) ? bal : ~bal;
+                    }
                 }
             } else {
                 peers = __match_any_sync(0xffffffffu, d);

@@ -32,7 +32,7 @@ struct Layout {
     size_t tile_cnt, col_lb, col_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes, tile_passes, tile_digit_bits;
     bool row_sort;             // row-segmented tile sort (two-phase, tiles_x <= kRowSortMaxCols)
-    int row_passes, col_bits;
+    int row_passes;
 };
 
 bool valid_cfg(const gs_raster_config* c) {
@@ -74,7 +74,6 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->row_sort = cfg->sort_mode == GS_SORT_TWO_PHASE && L->tiles_x <= kRowSortMaxCols;
     if (L->row_sort) {
         L->row_passes = L->tiles_y > 256 ? 2 : 1;
-        L->col_bits = bits_for((uint32_t)L->tiles_x);
         L->key_passes = L->row_passes + 1;
     }
     const size_t nn = (size_t)(n > 0 ? n : 1);
@@ -309,7 +308,7 @@ gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
             const int tp = sizeof(KeyT) == 8 ? p - 4 : p;
             a.shift = depth_digit ? 8 * p : (sizeof(KeyT) == 8 ? 32 : 0) + tp * L.tile_digit_bits;
             a.mask = depth_digit ? 0xFFu : (1u << L.tile_digit_bits) - 1u;
-            a.ballot_rank = tp == 0;   // lowest tile-id byte: spread digits
+            a.ballot_rank = tp == 0 ? 8 : 0;   // lowest tile-id byte: spread digits
             a.hist = ctl->hist_keys[p < kMaxKeyPasses ? p : 0];
             a.lookback = at<uint32_t>(ws, L.sort_lb[p % 2]);
             a.lookback_next = (p + 1 < L.key_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
@@ -421,7 +420,6 @@ gs_status tiles_by_rows(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.capacity = fs.f[v]->capacity;
         a.tiles_x = L.tiles_x;
         a.tiles = L.tiles;
-        a.col_bits = L.col_bits;
         a.tile_cnt = at<uint32_t>(ws, L.tile_cnt);
         a.lookback = at<uint32_t>(ws, L.col_lb);
         a.ranges = at<uint32_t>(ws, L.ranges);

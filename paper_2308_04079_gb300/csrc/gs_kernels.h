@@ -160,7 +160,8 @@ struct SortPassArgs {
     uint32_t count_host;       // element count bound (capacity)
     int shift;                 // digit = (key >> shift) & mask
     uint32_t mask;
-    int ballot_rank;           // rank digits with ballots (spread digits) instead of match_any
+    int ballot_rank;           // > 0: rank digits with that many ballots (every digit below
+                               // 2^ballot_rank; spread digits), 0: with match_any
     const uint32_t* hist;      // [256] digit counts of this pass
     uint32_t* lookback;        // [chunks][256], zeroed
     uint32_t* lookback_next;   // rows to zero for the next pass, or null
@@ -250,7 +251,6 @@ struct ColArgs {
     const uint32_t* num_segments;  // S (device)
     unsigned long long capacity;
     int tiles_x, tiles;
-    int col_bits;                  // bits of tiles_x: column digits and the padding digit fit
     uint32_t* tile_cnt;            // [tiles] instances per tile (zeroed; the count pass adds)
     uint32_t* lookback;            // [chunks][256] per column: counts of a chunk's last row
                                    // (inclusive within the row), zeroed before the count pass

@@ -13,7 +13,7 @@
 //      look-back that runs inside a row (the chunk where the row starts ends it);
 //   3. k_tile_scan: exclusive scan of the tile counts = the [start, end) range of every tile;
 //   4. k_col_scatter, per chunk: the records' instances, expanded in rounds of kRound, ranked
-//      stably by column (ballots on the column bits, per-warp counters), staged in shared
+//      stably by column (one ballot per digit bit, per-warp counters), staged in shared
 //      memory in column order and written to start(tile) + (the row's instances of that column
 //      in earlier chunks and rounds) + rank: every instance goes straight to its final slot.
 // Within a tile, instances keep the record order, which is the depth order: the result is
@@ -28,7 +28,7 @@ namespace {
 constexpr int kColThreads = 256;
 constexpr int kColWarps = kColThreads / 32;
 constexpr int kColPer = kColChunk / kColThreads;    // records per thread
-constexpr int kColDiff = 4096;                      // tiles of one count window
+constexpr int kColDiff = 2048;                      // tiles of one count window
 constexpr int kRound = 4096;                        // instances ranked per round
 constexpr int kRoundPer = kRound / kColThreads;     // instances per thread and round
 
@@ -36,7 +36,7 @@ __device__ __forceinline__ uint32_t rk_row(uint32_t g) { return g >> kRowKeyRowS
 __device__ __forceinline__ uint32_t rk_len(uint32_t g) { return (g >> 8) & 0x1FFu; }
 __device__ __forceinline__ uint32_t rk_col(uint32_t g) { return g & 0xFFu; }
 
-// Shared-memory index with one word of padding per 32: a thread's run of 16 consecutive
+// Shared-memory index with one word of padding per 32: a thread's run of 8 or 16 consecutive
 // entries and a warp's 32 consecutive entries are both free of bank conflicts.
 __device__ __forceinline__ uint32_t pad32(uint32_t k) { return k + (k >> 5); }
 
@@ -84,7 +84,7 @@ __device__ __forceinline__ void with_args(const Multi<ColArgs, MAXF>& m, int f, 
 // a look-back inside that row.
 // ---------------------------------------------------------------------------------------
 template <int MAXF>
-__global__ void __launch_bounds__(kColThreads) k_col_count(const __grid_constant__ Multi<ColArgs, MAXF> m) {
+__global__ void __launch_bounds__(kColThreads, 6) k_col_count(const __grid_constant__ Multi<ColArgs, MAXF> m) {
     __shared__ uint32_t s_diff[kColDiff + 1 + (kColDiff + 1) / 32 + 1];   // padded difference array
     __shared__ uint32_t s_base[MAXF + 1];
     __shared__ uint32_t s_scan[33];
@@ -109,22 +109,27 @@ __global__ void __launch_bounds__(kColThreads) k_col_count(const __grid_constant
             const uint32_t j0 = chunk * kColChunk;
             const uint32_t mcnt = min((uint32_t)kColChunk, S - j0);
             const uint32_t tx = (uint32_t)a.tiles_x, tiles = (uint32_t)a.tiles;
-            if (tid == 0) {
-                s_skip = (a.status->flags & (kFlagCapacity | kFlagTimeout)) != 0;
-                s_ra = rk_row(a.geom[j0]);
-                s_rb = rk_row(a.geom[j0 + mcnt - 1]);
-                s_cont = chunk > 0 && rk_row(a.geom[j0 - 1]) == rk_row(a.geom[j0]);
-            }
             uint32_t gk[kColPer];
 #pragma unroll
             for (int i = 0; i < kColPer; ++i) {
                 const uint32_t j = (uint32_t)(i * kColThreads + tid);
                 gk[i] = j < mcnt ? a.geom[j0 + j] : 0xFFFFFFFFu;   // row 0x7FFF: in no window
             }
+            // rows of the first and last record, and whether the previous chunk ends in the
+            // first one, from the loaded records (thread 0 adds the one in front)
+            if (tid == 0) {
+                const uint32_t prev = chunk > 0 ? a.geom[j0 - 1] : 0xFFFFFFFFu;
+                s_skip = (a.status->flags & (kFlagCapacity | kFlagTimeout)) != 0;
+                s_ra = rk_row(gk[0]);
+                s_cont = chunk > 0 && rk_row(prev) == rk_row(gk[0]);
+            }
+#pragma unroll
+            for (int i = 0; i < kColPer; ++i)
+                if ((uint32_t)(i * kColThreads + tid) == mcnt - 1) s_rb = rk_row(gk[i]);
             __syncthreads();
             if (s_skip) return;   // block-uniform
             const uint32_t ra = s_ra, rb = s_rb;
-            const uint32_t rpw = kColDiff / tx;   // rows per window (>= 16)
+            const uint32_t rpw = kColDiff / tx;   // rows per window (>= 8)
             uint32_t last = 0;                    // thread c < tx: this chunk's count of (rb, c)
             for (uint32_t wr = ra; wr <= rb; wr += rpw) {   // block-uniform
                 const uint32_t nrows = min(rpw, rb - wr + 1);
@@ -141,7 +146,7 @@ __global__ void __launch_bounds__(kColThreads) k_col_count(const __grid_constant
                     }
                 }
                 __syncthreads();
-                // counts = inclusive prefix of the differences; thread t takes [16 t, 16 t + 16)
+                // counts = inclusive prefix of the differences; thread t takes [8 t, 8 t + 8)
                 constexpr int PER = kColDiff / kColThreads;
                 uint32_t v[PER];
                 uint32_t sum = 0;
@@ -289,8 +294,7 @@ __global__ void __launch_bounds__(kColThreads, 4) k_col_scatter(const __grid_con
             const uint32_t mcnt = min((uint32_t)kColChunk, S - j0);
             const uint32_t tx = (uint32_t)a.tiles_x, tiles = (uint32_t)a.tiles;
             const uint32_t K = (uint32_t)min((unsigned long long)a.status->num_instances, a.capacity);
-            const int nb = a.col_bits;
-            const uint32_t sent = (1u << nb) - 1u;   // digit of the padding items (> every column)
+            constexpr uint32_t sent = 255u;   // digit of the padding items (columns are <= 254)
             if (tid == 0) {
                 s_skip = (a.status->flags & (kFlagCapacity | kFlagTimeout)) != 0;
                 s_cont = chunk > 0 && rk_row(a.geom[j0 - 1]) == rk_row(a.geom[j0]);
@@ -387,11 +391,9 @@ __global__ void __launch_bounds__(kColThreads, 4) k_col_scatter(const __grid_con
                         const uint32_t d = it[i] & 0xFFu;
                         uint32_t peers = 0xffffffffu;
 #pragma unroll
-                        for (int b = 0; b < 8; ++b) {
-                            if (b < nb) {
-                                const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-                                peers &= ((d >> b) & 1u) ? bal : ~bal;
-                            }
+                        for (int b = 0; b < 8; ++b) {   // all 8 bits: no branch per bit
+                            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                            peers &= ((d >> b) & 1u) ? bal : ~bal;
                         }
                         const uint32_t below = peers & lt;
                         const uint32_t prev = wh[d];
