@@ -139,11 +139,19 @@ def job_rate(world: int, units_per_rank: int, ms: float) -> float:
     return world * units_per_rank / (ms / 1e3)
 
 
+def row_sort(layout) -> bool:
+    """Two-phase frames up to 255 tile columns take the row-segmented tile sort."""
+    return bool(layout.depth_passes) and layout.tiles_x <= 255
+
+
 def launches_per_step(layout) -> int:
     """Kernels one step launches: preprocess; binning = two-phase: depth histogram + depth
-    passes + one segment pass (count, scan and records) + emit + sort-prepare + instance passes
-    + ranges; KEY64: count + pair scan + segment write + emit + sort-prepare + instance passes +
-    ranges; forward; backward tiles; backward Gaussians."""
+    passes + one segment pass (count, scan and records), then either sort-prepare + row passes
+    over the records + column count + tile scan + column pass (key_passes = row passes + 1) or
+    emit + sort-prepare + instance passes + ranges; KEY64: count + pair scan + segment write +
+    emit + sort-prepare + instance passes + ranges; forward; backward tiles; backward
+    Gaussians.  Both two-phase forms launch 5 + key_passes binning kernels after the depth
+    sort."""
     if layout.depth_passes:
         binning = (1 + layout.depth_passes) + 1 + 3 + layout.key_passes
     else:
@@ -164,8 +172,15 @@ def byte_model(n, n_vis, K, segs, P, tiles, sh_floats, layout):
     # write 12 B per segment record; emit: read the records, write K (key, value); instance
     # sort passes: read+write K (key, value); ranges: 8 B per tile
     depth_sort = (8 * n + layout.depth_passes * 16 * n) if layout.depth_passes else 0
-    b["bin_sort"] = depth_sort + n_vis * 44 + segs * 12 * 2 + K * (key_bytes + 4) \
-        + layout.key_passes * 2 * K * (key_bytes + 4) + tiles * 8
+    if row_sort(layout):
+        # row sort: 8 B per (row key, Gaussian) record written, read + written by each row
+        # pass, read by the column count (4 B) and the column pass (8 B); tile counts and
+        # ranges 12 B per tile; the column pass writes K (tile id, Gaussian)
+        rp = layout.key_passes - 1
+        b["bin_sort"] = depth_sort + n_vis * 44 + segs * (8 + rp * 16 + 4 + 8) + tiles * 12 + K * 8
+    else:
+        b["bin_sort"] = depth_sort + n_vis * 44 + segs * 12 * 2 + K * (key_bytes + 4) \
+            + layout.key_passes * 2 * K * (key_bytes + 4) + tiles * 8
     # per instance one value read and one gathered splat (mean 16 + conic 16 + rgb 16 = 48 B;
     # the gather of a splat is counted once per instance, i.e. L2 reuse across tiles ignored);
     # per pixel write rgb, T, last (20 B)
