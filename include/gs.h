@@ -60,7 +60,10 @@ typedef struct gs_camera {
 
 /* Sort schedule of gs_bin_sort; both give bit-identical instance order and tile ranges. */
 enum {
-    GS_SORT_TWO_PHASE = 0,    /* depth sort of the N Gaussians, then a stable tile sort of the instances */
+    GS_SORT_TWO_PHASE = 0,    /* depth sort of the N Gaussians, then a stable tile sort of the instances:
+                                 up to 255 tile columns the per-row tile runs are sorted by row
+                                 and their instances placed by column, else byte passes over
+                                 the tile ids */
     GS_SORT_KEY64 = 1         /* one LSD sort of the 64-bit (tile << 32 | depth) keys, as in App. C      */
 };
 
@@ -152,7 +155,9 @@ typedef struct gs_layout {
     uint64_t status;          /* gs_device_status                                           */
     uint64_t total_bytes;
     int tiles_x, tiles_y;
-    int key_passes;           /* radix passes over the instance keys                         */
+    int key_passes;           /* passes of the tile sort: TWO_PHASE up to 255 tile columns,
+                                 the row passes over the segment records + the column pass;
+                                 otherwise the radix passes over the instance keys            */
     int depth_passes;         /* radix passes over the Gaussian depths (TWO_PHASE), else 0    */
 } gs_layout;
 
