@@ -84,7 +84,7 @@ def test_workspace_size_and_layout(lib):
     L = _abi.gs_workspace_layout(1000, 1920, 1080, 1 << 20, c)
     assert L.total_bytes == s1
     assert (L.tiles_x, L.tiles_y) == (120, 68)
-    assert L.key_passes == 2 and L.depth_passes == 4          # 8160 tiles -> 13 bits
+    assert L.key_passes == 2 and L.depth_passes == 4          # one row pass + the column pass
     offs = [L.xy, L.depth, L.conic_opacity, L.rgb, L.radius, L.vals_sorted, L.keys_sorted, L.ranges, L.grad2d,
             L.status]
     assert all(o % 16 == 0 for o in offs) and all(o < s1 for o in offs)
@@ -92,6 +92,27 @@ def test_workspace_size_and_layout(lib):
     L64 = _abi.gs_workspace_layout(1000, 1920, 1080, 1 << 20, c)
     assert L64.key_passes == 6 and L64.depth_passes == 0       # 32 + 13 bits
     assert _abi.gs_workspace_size(0, 64, 64, 0, c) > 0         # empty scenes are valid
+
+
+@pytest.mark.parametrize("W,H,tile,passes", [
+    (1920, 1080, 16, 2),    # 120 x 68 tiles: row-segmented sort, one row pass + column pass
+    (4080, 200, 16, 2),     # 255 tile columns: still the row sort
+    (640, 4200, 16, 3),     # 263 tile rows: two row passes + column pass
+    (4096, 200, 16, 2),     # 256 tile columns: instance radix sort, 3328 tiles -> 12 bits, 2 passes
+    (4400, 4400, 16, 3),    # 275 x 275 tiles: radix sort, 17 bits -> 3 passes
+    (2048, 2100, 8, 3),     # 256 x 263 tiles of 8 x 8: radix sort, 17 bits -> 3 passes
+])
+def test_tile_sort_schedule_passes(lib, W, H, tile, passes):
+    """Two-phase frames up to 255 tile columns take the row-segmented tile sort (row byte
+    passes over the segment records + one column pass), wider ones the byte passes over the
+    instance tile ids; the sorted instances sit in the buffer the pass count selects."""
+    from paper_2308_04079_gb300 import _abi
+    c = _abi.gs_default_config()
+    c.tile_w = c.tile_h = tile
+    c.batch_depth = min(c.batch_depth, tile * tile)
+    L = _abi.gs_workspace_layout(5000, W, H, 1 << 16, c)
+    assert L.key_passes == passes and L.depth_passes == 4
+    assert L.keys_sorted % 256 == 0 and L.vals_sorted % 256 == 0 and L.vals_sorted < L.total_bytes
 
 
 @pytest.mark.parametrize("bad", [dict(tile_w=12), dict(batch_depth=0), dict(batch_depth=257), dict(sort_mode=7),
