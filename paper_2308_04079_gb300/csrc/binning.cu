@@ -8,9 +8,11 @@
 //   the 32 + ceil(log2 tiles) significant bits (8-bit digits), ranges by neighbour compare.
 // GS_SORT_TWO_PHASE -- the same order with far fewer passes over the instances: first a stable
 //   LSD sort of the N Gaussians by fp32 depth bits (culled ones keyed 0xFFFFFFFF go last), then
-//   emit each visible Gaussian's tiles in that order and stable-sort the instances by tile id
-//   only.  Within a tile, instances then appear in (depth bits, Gaussian index) order, exactly
-//   the order the 64-bit sort produces.
+//   each visible Gaussian's tiles in that order, stable-sorted by tile id only: for frames up to
+//   255 tile columns by the row-segmented tile sort of tilesort.cu (the segment records sorted
+//   by row, the instances placed by column), otherwise by emitting the instances and sorting
+//   them with byte passes over the tile id.  Within a tile, instances then appear in (depth
+//   bits, Gaussian index) order, exactly the order the 64-bit sort produces.
 //
 // Radix sort: one kernel per digit pass in the onesweep style (Merrill & Grimshaw's radix
 // sorting, single-pass with decoupled look-back): every block claims a 4096-key chunk from an
