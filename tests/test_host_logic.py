@@ -54,3 +54,30 @@ def test_position_lr_is_log_linear():
     assert math.isclose(position_lr(30000, 1.6e-4, 1.6e-6, 30000), 1.6e-6)
     assert math.isclose(position_lr(15000, 1.6e-4, 1.6e-6, 30000), 1.6e-5)
     assert math.isclose(position_lr(90000, 1.6e-4, 1.6e-6, 30000), 1.6e-6)
+
+
+def test_bench_launch_count_and_byte_model_follow_the_schedule():
+    """bench.py's kernel count per step and algorithmic binning bytes for the row-segmented tile
+    sort (1080p, 16x16 tiles), the two-phase radix sort (over 255 tile columns) and KEY64,
+    from the workspace layout the library reports."""
+    import bench
+    from paper_2308_04079_gb300 import _abi
+    c = _abi.gs_default_config()
+    rows = _abi.gs_workspace_layout(3_000_000, 1920, 1080, 1 << 20, c)
+    wide = _abi.gs_workspace_layout(3_000_000, 4400, 1080, 1 << 20, c)
+    c.sort_mode = _abi.GS_SORT_KEY64
+    k64 = _abi.gs_workspace_layout(3_000_000, 1920, 1080, 1 << 20, c)
+    assert bench.row_sort(rows) and not bench.row_sort(wide) and not bench.row_sort(k64)
+    # preprocess, depth histogram + 4 depth passes, segment pass, sort-prepare, row pass,
+    # column count, tile scan, column pass, forward, backward tiles, backward Gaussians
+    assert bench.launches_per_step(rows) == 15
+    # the same with emit + 2 tile-id passes + ranges in place of the row sort's four kernels
+    assert bench.launches_per_step(wide) == 1 + 5 + 1 + 1 + 1 + wide.key_passes + 1 + 3
+    # KEY64: count + pair scan + segment write + emit + sort-prepare + 6 passes + ranges
+    assert bench.launches_per_step(k64) == 1 + 3 + 3 + 6 + 3
+    n, n_vis, K, segs, tiles = 3_000_000, 2_436_483, 28_516_288, 9_019_658, 8160
+    depth = 8 * n + 4 * 16 * n
+    b = bench.byte_model(n, n_vis, K, segs, 1920 * 1080, tiles, 48, rows)["bin_sort"]
+    assert b == depth + n_vis * 44 + segs * (8 + 16 + 4 + 8) + tiles * 12 + K * 8
+    b = bench.byte_model(n, n_vis, K, segs, 1920 * 1080, tiles, 48, wide)["bin_sort"]
+    assert b == depth + n_vis * 44 + segs * 24 + K * 8 + 2 * 2 * K * 8 + tiles * 8
