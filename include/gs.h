@@ -44,7 +44,11 @@ typedef enum gs_status {
     GS_ERR_CAPACITY = 2,      /* more (Gaussian, tile) instances than the workspace holds      */
     GS_ERR_TIMEOUT = 3,       /* a bounded device spin-wait gave up (results are invalid)      */
     GS_ERR_CUDA = 4,          /* a CUDA launch or memset failed                                */
-    GS_ERR_NUMERIC = 5        /* non-finite inputs were found and culled (results are valid)   */
+    GS_ERR_NUMERIC = 5,       /* non-finite inputs were found and culled (results are valid)   */
+    GS_ERR_INTERNAL = 6       /* a device-side consistency check failed: the per-tile instance
+                                 counts did not add up to the instance count, or (in a GS_DEBUG
+                                 build) an instance or range index was out of bounds; results
+                                 are invalid, nothing was written out of bounds               */
 } gs_status;
 
 /* Pinhole camera (the paper's view configuration V, Algorithm 2; viewing transformation W
@@ -91,7 +95,13 @@ typedef struct gs_raster_config {
     int isotropic;            /* 1: one scale per Gaussian for all three axes (the isotropic ablation
                                  of Sec. 7.3): scales and their gradients are [n], quaternions are
                                  neither read nor differentiated (may be NULL); 0: anisotropic      */
+    unsigned int spin_limit;  /* polls a thread block of the binning stage makes while waiting for
+                                 a predecessor's published prefix before it gives up, sets the
+                                 timeout flag (GS_ERR_TIMEOUT) and goes on without waiting;
+                                 GS_DEFAULT_SPIN_LIMIT by default, 0 gives up at the first wait   */
 } gs_raster_config;
+
+#define GS_DEFAULT_SPIN_LIMIT (1u << 22)
 
 /* Gaussian parameters (Sec. 4): device pointers, n rows each. */
 typedef struct gs_gaussians {
@@ -149,9 +159,12 @@ typedef struct gs_layout {
     uint64_t xy, depth, conic_opacity, rgb, radius;
     uint64_t tau;             /* float[n] alpha level 2 ln(o / alpha_min) of every splat       */
     uint64_t vals_sorted, keys_sorted, ranges;
-    uint64_t grad2d;          /* float[n, 12] per-Gaussian screen-space gradient accumulators:
-                                 dL/du, dL/dv, dL/dSigma'_00, dL/dSigma'_01, dL/dSigma'_11 (full-
-                                 matrix convention), dL/do, dL/d(r, g, b), 3 unused */
+    uint64_t grad2d;          /* float[n, 12] per-Gaussian screen-space gradient accumulators,
+                                 the mean and Sigma' terms in the whitened frame (p, q) = L^T d
+                                 of the conic's Cholesky factor L (conic_opacity): P, Q =
+                                 sum dL/dpower (p, q); K00, K01, K11 = (1/2) sum dL/dpower
+                                 (p, q)(p, q)^T; then dL/do, dL/d(r, g, b), 3 unused.  dL/du, dL/dv
+                                 = L (P, Q) and dL/dSigma' = L K L^T (full-matrix convention). */
     uint64_t status;          /* gs_device_status                                           */
     uint64_t total_bytes;
     int tiles_x, tiles_y;
@@ -163,7 +176,8 @@ typedef struct gs_layout {
 
 /* Device-side status block (in the workspace). */
 typedef struct gs_device_status {
-    uint32_t flags;           /* bit 0: capacity exceeded, bit 1: spin-wait timeout            */
+    uint32_t flags;           /* bit 0: capacity exceeded, bit 1: spin-wait timeout, bit 2: a
+                                 consistency check failed (GS_ERR_INTERNAL)                    */
     uint32_t num_instances;   /* (Gaussian, tile) pairs (may exceed capacity, see flags)       */
     uint32_t num_visible;     /* Gaussians that survived culling                               */
     uint32_t num_nonfinite;   /* Gaussians culled because an input was NaN or Inf              */
@@ -409,6 +423,9 @@ gs_status gs_opacity_reset(float* logit_opacities, float* adam_m, float* adam_v,
  * synchronise the device and stall other streams; a fixed memory budget leaves no room for a
  * workspace).  The scratch address is looked up once per device on the first call, which may
  * load the module on that device: make the first call on each device outside stream capture.
+ * The address stays cached for the life of the process: after cudaDeviceReset (or anything else
+ * that destroys the device's primary context and unloads the module) it is stale, so a process
+ * that resets a device must not call this entry point on that device again.
  * The scratch is shared by every call on a device, so calls that overlap in time (two streams
  * or two host threads) race and must be ordered by the caller.
  * Errors: GS_ERR_INVALID_ARG for n < 0, n > GS_STATIC_ORDER_MAX_N or a null pointer,
@@ -417,9 +434,36 @@ gs_status gs_opacity_reset(float* logit_opacities, float* adam_m, float* adam_v,
 gs_status gs_depth_order_static(int n, const float* depth, const int* radius, uint32_t* order,
                                 gs_device_status* status, cudaStream_t stream);
 
+/* gs_bin_sort with its launches timed (a measurement utility; the binning it performs is
+ * gs_bin_sort's, App. C DuplicateWithKeys / SortByKeys / IdentifyTileRanges).  An event is
+ * recorded on `stream` before the first launch and after each one; the call synchronises the
+ * stream and writes, for up to `cap` launches in order, the milliseconds between consecutive
+ * events to ms[i] and a static label of the launch ("depth radix pass", "segment pass", "row
+ * radix pass", "column count", "tile scan", "column pass", ...) to names[i]; *count receives
+ * how many were written.  Host arrays, caller-owned.  Creates and destroys its own events;
+ * allocates no device memory.  Errors: GS_ERR_INVALID_ARG (also for null ms, names or count, or
+ * cap <= 0), GS_ERR_CUDA. */
+gs_status gs_bin_sort_timed(const gs_frame* frame, float* ms, const char** names, int cap, int* count,
+                            cudaStream_t stream);
+
 /* Copy the workspace status block to the host (synchronises the stream) and return the first
- * device-side error as a status: GS_ERR_TIMEOUT, GS_ERR_CAPACITY, GS_ERR_NUMERIC or GS_OK. */
+ * device-side error as a status: GS_ERR_INTERNAL, GS_ERR_TIMEOUT, GS_ERR_CAPACITY,
+ * GS_ERR_NUMERIC or GS_OK. */
 gs_status gs_read_status(const gs_frame* frame, gs_device_status* out, cudaStream_t stream);
+
+/* Throughput microbenchmarks (no counterpart in the paper; measurement utilities).  The render
+ * kernels' work per (pixel, splat) pair is FP32 fused multiply-adds and one exp2f; these two
+ * kernels measure this GPU's rate of each, the denominator of the render kernels' roofline.
+ *   gs_peak_fma   `blocks` blocks of 1024 threads, each running independent chains of fmaf
+ *   gs_peak_ex2   the same with exp2f
+ *   gs_peak_ops   operations one launch of either performs (FMA instructions per lane, i.e.
+ *                 flops / 2, or exp2f evaluations), for (blocks, iters)
+ * sink: a device float[blocks] that is never written in practice (it keeps the chains live).
+ * Asynchronous on `stream`; time them with events.  Errors: GS_ERR_INVALID_ARG for blocks <= 0,
+ * iters <= 0 or a null sink, GS_ERR_CUDA. */
+gs_status gs_peak_fma(int blocks, int iters, float* sink, cudaStream_t stream);
+gs_status gs_peak_ex2(int blocks, int iters, float* sink, cudaStream_t stream);
+unsigned long long gs_peak_ops(int blocks, int iters);
 
 /* Human-readable name of a status code (static string). */
 const char* gs_status_string(gs_status s);

@@ -20,6 +20,7 @@ GS_ERR_CAPACITY = 2
 GS_ERR_TIMEOUT = 3
 GS_ERR_CUDA = 4
 GS_ERR_NUMERIC = 5
+GS_ERR_INTERNAL = 6
 
 GS_SORT_TWO_PHASE = 0
 GS_SORT_KEY64 = 1
@@ -30,6 +31,8 @@ GS_TILES_RECT = 1
 
 FLAG_CAPACITY = 1
 FLAG_TIMEOUT = 2
+FLAG_INTERNAL = 4
+GS_DEFAULT_SPIN_LIMIT = 1 << 22
 
 
 class gs_camera(ctypes.Structure):
@@ -41,7 +44,7 @@ class gs_raster_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int), ("tile_h", c_int), ("batch_depth", c_int), ("sort_mode", c_int),
                 ("alpha_min", c_float), ("alpha_max", c_float), ("T_min", c_float), ("dilation", c_float),
                 ("guard", c_float), ("extent", c_float), ("tile_rule", c_int), ("grad_limit", c_int),
-                ("isotropic", c_int)]
+                ("isotropic", c_int), ("spin_limit", ctypes.c_uint)]
 
 
 class gs_gaussians(ctypes.Structure):
@@ -129,23 +132,33 @@ SIGNATURES = [
     ("gs_opacity_reset", c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_float, c_void_p]),
     ("gs_depth_order_static", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("gs_status_string", ctypes.c_char_p, [c_int]),
+    ("gs_bin_sort_timed", c_int, [ctypes.POINTER(gs_frame), ctypes.POINTER(c_float), ctypes.POINTER(ctypes.c_char_p),
+                                  c_int, ctypes.POINTER(c_int), c_void_p]),
+    ("gs_peak_fma", c_int, [c_int, c_int, c_void_p, c_void_p]),
+    ("gs_peak_ex2", c_int, [c_int, c_int, c_void_p, c_void_p]),
+    ("gs_peak_ops", ctypes.c_ulonglong, [c_int, c_int]),
 ]
 
 _lib = None
 
 
+def debug_build() -> bool:
+    """GS_DEBUG=1 in the environment selects the bounds-checking build libgs_gb300_debug.so."""
+    return os.environ.get("GS_DEBUG", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_build() else _build.LIB
 
 
 def load(build_if_missing: bool = False) -> ctypes.CDLL:
-    """Load libgs_gb300.so.  Raises if it is missing (build it with __graft_entry__.build()
-    or ``python -m paper_2308_04079_gb300.build``)."""
+    """Load libgs_gb300.so (libgs_gb300_debug.so with GS_DEBUG=1).  Raises if it is missing
+    (build it with __graft_entry__.build() or ``python -m paper_2308_04079_gb300.build``)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if build_if_missing and _build.needs_build():
-            _build.build()
+        path = library_path()
+        if build_if_missing and _build.needs_build(debug_build()):
+            _build.build(debug=debug_build())
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA rasterizer library not built: {path} is missing")
         lib = ctypes.CDLL(path)
@@ -234,6 +247,28 @@ def gs_depth_order_static(n: int, depth: int, radius: int, order: int, status: i
     """Depth ordering with the library's static scratch (device pointers in, nothing
     allocated); see include/gs.h."""
     _check(load().gs_depth_order_static(n, depth, radius, order, status, stream), "gs_depth_order_static")
+
+
+def gs_bin_sort_timed(frame: gs_frame, stream: int, cap: int = 32) -> list:
+    """gs_bin_sort with every launch timed: [(label, ms), ...] in launch order (synchronises)."""
+    ms = (c_float * cap)()
+    names = (ctypes.c_char_p * cap)()
+    count = c_int(0)
+    _check(load().gs_bin_sort_timed(ctypes.byref(frame), ms, names, cap, ctypes.byref(count), stream),
+           "gs_bin_sort_timed")
+    return [(names[i].decode(), float(ms[i])) for i in range(count.value)]
+
+
+def gs_peak_fma(blocks: int, iters: int, sink: int, stream: int) -> None:
+    _check(load().gs_peak_fma(blocks, iters, sink, stream), "gs_peak_fma")
+
+
+def gs_peak_ex2(blocks: int, iters: int, sink: int, stream: int) -> None:
+    _check(load().gs_peak_ex2(blocks, iters, sink, stream), "gs_peak_ex2")
+
+
+def gs_peak_ops(blocks: int, iters: int) -> int:
+    return int(load().gs_peak_ops(blocks, iters))
 
 
 def _ptrs(values):

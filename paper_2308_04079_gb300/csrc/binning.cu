@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
                 if (stop) break;
                 j -= used;
                 if (wait) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > a.spin_limit) {
                         atomicOr(&a.status->flags, kFlagTimeout);
                         break;
                     }
@@ -278,6 +278,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const __grid_const
             if (dest < count) {
                 a.keys_out[dest] = kk;
                 a.vals_out[dest] = s_vals[s];
+            } else if (GS_DEBUG && chunk * (uint32_t)TILE + s < count) {   // a real key: padding sorts last
+                debug_fail(a.status);
             }
         }
         };
@@ -389,7 +391,10 @@ struct EntrySplat {
 __device__ __forceinline__ EntrySplat load_entry(const ScanArgs& a, uint32_t j, uint32_t count) {
     EntrySplat sp;
     uint32_t gid = j < count ? (a.order ? a.order[j] : j) : 0u;
-    if (gid >= (uint32_t)a.n) gid = 0;   // only reachable after a timed-out sort
+    if (gid >= (uint32_t)a.n) {   // only reachable after a timed-out sort
+        if (!(a.status->flags & kFlagTimeout)) debug_fail(a.status);
+        gid = 0;
+    }
     sp.gid = gid;
     const int rad = j < count ? a.radius[gid] : 0;
     sp.mean = a.xy[gid];
@@ -564,7 +569,7 @@ __global__ void __launch_bounds__(kDupThreads) k_scan_pairs(const __grid_constan
                     const int first_inc = inc ? __ffs(inc) - 1 : 32;
                     const uint32_t upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
                     if (zero & upto) {   // a predecessor in front of the first prefix is not ready
-                        if (++spins > kSpinLimit) {
+                        if (++spins > a.spin_limit) {
                             if (tid == 0) atomicOr(&a.status->flags, kFlagTimeout);
                             break;
                         }
@@ -843,7 +848,7 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
                         const int first_inc = inc ? __ffs(inc) - 1 : 32;
                         const uint32_t upto = first_inc >= 31 ? 0xffffffffu : ((2u << first_inc) - 1u);
                         if (zero & upto) {   // a predecessor in front of the first prefix is not ready
-                            if (++spins > kSpinLimit) {
+                            if (++spins > a.spin_limit) {
                                 if (tid == 0) atomicOr(&a.status->flags, kFlagTimeout);
                                 break;
                             }
@@ -962,7 +967,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const __grid_constant__ M
             const uint32_t S = *af.num_segments;
             if (blockIdx.x == 0) af.status->num_segments = S;
             // nothing is emitted for a frame after a capacity overflow or a timed-out scan
-            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout))) units = (S + UNIT - 1) / UNIT;
+            if (!(af.status->flags & kFlagAbort)) units = (S + UNIT - 1) / UNIT;
         }
         const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
         if (tid < m.frames) s_ubase[tid + 1] = inc;
@@ -1063,7 +1068,7 @@ __global__ void __launch_bounds__(256) k_ranges(const __grid_constant__ Multi<Ra
         uint32_t units = 0;
         if (tid < m.frames) {
             const RangesArgs& af = m.a[tid];
-            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout)))
+            if (!(af.status->flags & kFlagAbort))
                 units = (uint32_t)((min((unsigned long long)af.status->num_instances, af.capacity) + UNIT - 1) / UNIT);
         }
         const uint32_t inc = warp_inclusive_scan<uint32_t>(units);
@@ -1106,7 +1111,7 @@ __global__ void __launch_bounds__(256) k_ranges32(const __grid_constant__ Multi<
         uint32_t units = 0;
         if (tid < m.frames) {
             const RangesArgs& af = m.a[tid];
-            if (!(af.status->flags & (kFlagCapacity | kFlagTimeout)))
+            if (!(af.status->flags & kFlagAbort))
                 units = (uint32_t)((min((unsigned long long)af.status->num_instances, af.capacity) + UNIT - 1) / UNIT);
         }
         const uint32_t inc = warp_inclusive_scan<uint32_t>(units);

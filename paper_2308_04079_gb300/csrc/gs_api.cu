@@ -167,6 +167,23 @@ CfgK cfg_k(const gs_raster_config& c) {
 
 gs_status ok(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 
+// Optional per-launch timing of the binning stage (gs_bin_sort_timed): while a timer is active
+// on the calling host thread, an event is recorded on the stream after every launch.
+struct PhaseTimer {
+    static constexpr int kMax = 32;
+    cudaEvent_t ev[kMax + 1];   // ev[0]: before the first launch
+    const char* name[kMax];
+    int n = 0;
+};
+thread_local PhaseTimer* t_phase = nullptr;
+
+void phase(const char* name, cudaStream_t s) {
+    PhaseTimer* t = t_phase;
+    if (!t || t->n >= PhaseTimer::kMax) return;
+    t->name[t->n] = name;
+    cudaEventRecord(t->ev[++t->n], s);
+}
+
 size_t keys_sorted_off(const Layout& L) { return L.ikey[L.key_passes % 2]; }
 size_t vals_sorted_off(const Layout& L) { return L.ival[L.key_passes % 2]; }
 
@@ -285,6 +302,7 @@ gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
         max_passes = std::max(max_passes, fs.L[v].key_passes);
     }
     if (launch_sort_prepare(pm, s) != cudaSuccess) return GS_ERR_CUDA;
+    phase("sort prepare", s);
     Control* ctl0 = control_of(fs, 0);
     for (int p = 0; p < max_passes; ++p) {
         Multi<SortPassArgs<KeyT>, MAXF> m;
@@ -314,8 +332,10 @@ gs_status key_sort(const FrameSet<MAXF>& fs, cudaStream_t s) {
             a.lookback_next = (p + 1 < L.key_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
             a.chunk_counter = &ctl0->counters[8 + p];
             a.status = &ctl->status;
+            a.spin_limit = fs.f[v]->cfg.spin_limit;
         }
         if (launch_onesweep(m, 0, s) != cudaSuccess) return GS_ERR_CUDA;
+        phase("instance radix pass", s);
     }
     return GS_OK;
 }
@@ -355,9 +375,12 @@ gs_status tiles_by_radix(const FrameSet<MAXF>& fs, bool key64, cudaStream_t s) {
         a.status = &ctl->status;
     }
     if (launch_emit(e, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    phase("emit instances", s);
     const gs_status st = key64 ? key_sort<unsigned long long>(fs, s) : key_sort<uint32_t>(fs, s);
     if (st != GS_OK) return st;
-    return ok(launch_ranges(tr, key64, s));
+    const gs_status r = ok(launch_ranges(tr, key64, s));
+    phase("tile ranges", s);
+    return r;
 }
 
 // Row-segmented tile sort: the segment records sorted by row, then every instance placed by
@@ -377,6 +400,7 @@ gs_status tiles_by_rows(const FrameSet<MAXF>& fs, cudaStream_t s) {
         max_passes = std::max(max_passes, L.row_passes);
     }
     if (launch_sort_prepare(pm, s) != cudaSuccess) return GS_ERR_CUDA;
+    phase("sort prepare", s);
     Control* ctl0 = control_of(fs, 0);
     for (int p = 0; p < max_passes; ++p) {
         Multi<SortPassArgs<uint32_t>, MAXF> m;
@@ -403,8 +427,10 @@ gs_status tiles_by_rows(const FrameSet<MAXF>& fs, cudaStream_t s) {
             a.lookback_next = (p + 1 < L.row_passes) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
             a.chunk_counter = &ctl0->counters[8 + p];
             a.status = &ctl->status;
+            a.spin_limit = fs.f[v]->cfg.spin_limit;
         }
         if (launch_onesweep(m, 0, s) != cudaSuccess) return GS_ERR_CUDA;
+        phase("row radix pass", s);
     }
     Multi<ColArgs, MAXF> c;
     c.frames = fs.count;
@@ -427,11 +453,16 @@ gs_status tiles_by_rows(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.vals_out = at<uint32_t>(ws, L.ival[(rp + 1) % 2]);
         a.chunk_counter = &ctl0->counters[16];
         a.status = &ctl->status;
+        a.spin_limit = fs.f[v]->cfg.spin_limit;
     }
     if (launch_col_count(c, s) != cudaSuccess) return GS_ERR_CUDA;
+    phase("column count", s);
     if (launch_tile_scan(c, s) != cudaSuccess) return GS_ERR_CUDA;
+    phase("tile scan", s);
     for (int v = 0; v < fs.count; ++v) c.a[v].chunk_counter = &ctl0->counters[17];
-    return ok(launch_col_scatter(c, s));
+    const gs_status r = ok(launch_col_scatter(c, s));
+    phase("column pass", s);
+    return r;
 }
 
 template <int MAXF>
@@ -457,6 +488,7 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
     }
     gs_status st = clear_regions(fs, clr, s);
     if (st != GS_OK) return st;
+    phase("clear", s);
     Control* ctl0 = control_of(fs, 0);
 
     Multi<ScanArgs, MAXF> d;
@@ -475,6 +507,7 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
             chunks += (fs.f[v]->n + kSortTile - 1) / kSortTile;
         }
         if (launch_depth_hist(h, s) != cudaSuccess) return GS_ERR_CUDA;
+        phase("depth histogram", s);
         for (int p = 0; p < kDepthPasses; ++p) {
             Multi<SortPassArgs<uint32_t>, MAXF> m;
             m.frames = fs.count;
@@ -499,8 +532,10 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
                 a.lookback_next = (p + 1 < kDepthPasses) ? at<uint32_t>(ws, L.sort_lb[(p + 1) % 2]) : nullptr;
                 a.chunk_counter = &ctl0->counters[1 + p];
                 a.status = &ctl->status;
+                a.spin_limit = fs.f[v]->cfg.spin_limit;
             }
             if (chunks > 0 && launch_onesweep(m, chunks, s) != cudaSuccess) return GS_ERR_CUDA;
+            phase("depth radix pass", s);
         }
     }
     for (int v = 0; v < fs.count; ++v) {
@@ -537,8 +572,10 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         a.lookback = at<unsigned long long>(ws, L.scan_lb);
         a.chunk_counter = &ctl0->counters[0];
         a.status = &ctl->status;
+        a.spin_limit = fs.f[v]->cfg.spin_limit;
     }
     if (launch_scan_tiles(d, key64, s) != cudaSuccess) return GS_ERR_CUDA;
+    phase(key64 ? "tile count, scan and segment write" : "segment pass", s);
     FrameSet<MAXF> radix, rows;
     for (int v = 0; v < fs.count; ++v) {
         FrameSet<MAXF>& g = fs.L[v].row_sort ? rows : radix;
@@ -577,6 +614,8 @@ gs_status render_forward_impl(const FrameSet<MAXF>& fs, const float* bg, float* 
         a.out_T = out_T[v];
         a.out_last = out_last[v];
         a.out_count = f->cfg.grad_limit > 0 ? at<uint32_t>(ws, L.pix_count) : nullptr;
+        a.capacity = f->capacity;
+        a.status = &control_of(fs, v)->status;
     }
     return ok(launch_render_forward(m, s));
 }
@@ -614,6 +653,8 @@ gs_status render_backward_tiles_impl(const FrameSet<MAXF>& fs, const float* bg, 
         a.count = f->cfg.grad_limit > 0 ? at<uint32_t>(ws, L.pix_count) : nullptr;
         a.grad2d = at<float>(ws, L.grad2d);
         a.blended = reinterpret_cast<unsigned long long*>(&st->blended_pairs);
+        a.capacity = f->capacity;
+        a.status = st;
     }
     gs_status st = clear_regions(fs, clr, s);
     if (st != GS_OK) return st;
@@ -687,6 +728,7 @@ gs_status render_backward_gaussians_impl(const FrameSet<MAXF>& fs, const gs_gaus
                 b.cam = cam_k(f, L);
                 b.cfg = cfg_k(f->cfg);
                 b.grad2d = at<float>(ws, L.grad2d);
+                b.conic = at<float4>(ws, L.conic);
                 b.rgb = at<float4>(ws, L.rgb);
                 b.radius = at<int>(ws, L.radius);
                 b.g_means = rk.means; b.g_scales = rk.scales; b.g_quats = rk.quats; b.g_opacities = rk.opacities;
@@ -727,6 +769,7 @@ void gs_default_config(gs_raster_config* cfg) {
     cfg->tile_rule = GS_TILES_REACH;
     cfg->grad_limit = 0;
     cfg->isotropic = 0;
+    cfg->spin_limit = GS_DEFAULT_SPIN_LIMIT;
 }
 
 size_t gs_workspace_size(int n, int width, int height, uint64_t capacity, const gs_raster_config* cfg) {
@@ -852,6 +895,33 @@ gs_status gs_batch_render_backward(const gs_frame* frames, const gs_gaussians* g
     return render_backward_gaussians_impl(fs, g, grads, accumulate, s);
 }
 
+gs_status gs_bin_sort_timed(const gs_frame* f, float* ms, const char** names, int cap, int* count, cudaStream_t s) {
+    if (!ms || !names || !count || cap <= 0) return GS_ERR_INVALID_ARG;
+    *count = 0;
+    PhaseTimer t;
+    int made = 0;
+    gs_status st = GS_OK;
+    for (; made <= PhaseTimer::kMax; ++made)
+        if (cudaEventCreate(&t.ev[made]) != cudaSuccess) { st = GS_ERR_CUDA; break; }
+    if (st == GS_OK && cudaEventRecord(t.ev[0], s) != cudaSuccess) st = GS_ERR_CUDA;
+    if (st == GS_OK) {
+        t_phase = &t;
+        st = gs_bin_sort(f, s);
+        t_phase = nullptr;
+    }
+    if (st == GS_OK && cudaEventSynchronize(t.ev[t.n]) != cudaSuccess) st = GS_ERR_CUDA;
+    if (st == GS_OK) {
+        const int n = t.n < cap ? t.n : cap;
+        for (int i = 0; i < n; ++i) {
+            if (cudaEventElapsedTime(&ms[i], t.ev[i], t.ev[i + 1]) != cudaSuccess) st = GS_ERR_CUDA;
+            names[i] = t.name[i];
+        }
+        *count = n;
+    }
+    for (int i = 0; i < made; ++i) cudaEventDestroy(t.ev[i]);
+    return st;
+}
+
 gs_status gs_read_status(const gs_frame* f, gs_device_status* out, cudaStream_t s) {
     Layout L;
     if (!valid_frame(f, &L) || !out) return GS_ERR_INVALID_ARG;
@@ -859,6 +929,7 @@ gs_status gs_read_status(const gs_frame* f, gs_device_status* out, cudaStream_t 
     if (cudaMemcpyAsync(out, &ctl->status, sizeof(gs_device_status), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return GS_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
+    if (out->flags & kFlagInternal) return GS_ERR_INTERNAL;
     if (out->flags & kFlagTimeout) return GS_ERR_TIMEOUT;
     if (out->flags & kFlagCapacity) return GS_ERR_CAPACITY;
     if (out->num_nonfinite) return GS_ERR_NUMERIC;
@@ -873,6 +944,7 @@ const char* gs_status_string(gs_status s) {
         case GS_ERR_TIMEOUT: return "device spin-wait timed out";
         case GS_ERR_CUDA: return "CUDA error";
         case GS_ERR_NUMERIC: return "non-finite inputs culled";
+        case GS_ERR_INTERNAL: return "device-side consistency check failed";
     }
     return "unknown status";
 }

@@ -37,10 +37,25 @@ constexpr int kRadiusMax = 1 << 24;   // screen radius clamp (pixels)
 // Status-block flags (gs_device_status.flags).
 constexpr uint32_t kFlagCapacity = 1u;
 constexpr uint32_t kFlagTimeout = 2u;
+constexpr uint32_t kFlagInternal = 4u;   // a consistency check failed (see GS_ERR_INTERNAL)
+// Any of these: the later binning kernels write nothing.
+constexpr uint32_t kFlagAbort = kFlagCapacity | kFlagTimeout | kFlagInternal;
 
-// Upper bound on polling iterations of any device spin-wait; the waiting thread then sets
-// kFlagTimeout and gives up (results invalid, no hang).
-constexpr uint32_t kSpinLimit = 1u << 22;
+// Upper bound on polling iterations of a device spin-wait when the caller gives none (the
+// binning kernels take cfg.spin_limit); the waiting thread then sets kFlagTimeout and gives up
+// (results invalid, no hang).
+constexpr uint32_t kSpinLimit = GS_DEFAULT_SPIN_LIMIT;
+
+// GS_DEBUG builds (libgs_gb300_debug.so) add bounds checks on instance and range indices that a
+// correct run never fails; a failed check sets kFlagInternal (GS_ERR_INTERNAL) in the status
+// block and the access is skipped or clamped, so the kernel neither traps nor reads or writes
+// out of bounds.  Release builds keep the clamps without reporting.
+#ifndef GS_DEBUG
+#define GS_DEBUG 0
+#endif
+__device__ __forceinline__ void debug_fail(gs_device_status* st) {
+    if (GS_DEBUG && st) atomicOr(&st->flags, kFlagInternal);
+}
 
 __device__ __forceinline__ int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 

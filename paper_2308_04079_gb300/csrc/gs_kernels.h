@@ -110,6 +110,7 @@ struct PreprocessBwdArgs {
     CamK cam;
     CfgK cfg;
     const float* grad2d;     // [n, 12]
+    const float4* conic;     // (l11, l21, l22, o): the conic's Cholesky factor the tile kernels used
     const float4* rgb;
     const int* radius;
     float* g_means;
@@ -167,6 +168,7 @@ struct SortPassArgs {
     uint32_t* lookback_next;   // rows to zero for the next pass, or null
     uint32_t* chunk_counter;   // zeroed
     gs_device_status* status;
+    uint32_t spin_limit;       // look-back polls before giving up (kFlagTimeout)
 };
 
 struct ScanArgs {
@@ -192,6 +194,7 @@ struct ScanArgs {
     unsigned long long* lookback;  // [entries / kDupThreads], zeroed
     uint32_t* chunk_counter;
     gs_device_status* status;
+    uint32_t spin_limit;       // look-back polls before giving up (kFlagTimeout)
 };
 
 // Tile ranges from the sorted keys (uint32 tile ids, or 64-bit keys with the tile id high).
@@ -259,6 +262,7 @@ struct ColArgs {
     uint32_t* vals_out;            // [K] Gaussian per instance
     uint32_t* chunk_counter;       // zeroed
     gs_device_status* status;
+    uint32_t spin_limit;           // look-back polls before giving up (kFlagTimeout)
 };
 
 struct RenderFwdArgs {
@@ -276,6 +280,8 @@ struct RenderFwdArgs {
     float* out_T;
     uint32_t* out_last;
     uint32_t* out_count;       // nullable: blended splats per pixel (for cfg.grad_limit)
+    unsigned long long capacity;   // instance capacity (GS_DEBUG range checks)
+    gs_device_status* status;
 };
 
 struct RenderBwdArgs {
@@ -295,6 +301,8 @@ struct RenderBwdArgs {
     const uint32_t* count;     // blended splats per pixel when cfg.grad_limit > 0, else null
     float* grad2d;             // [n, 12] accumulators, zeroed
     unsigned long long* blended;   // count of back-propagated (pixel, splat) pairs, zeroed
+    unsigned long long capacity;   // instance capacity (GS_DEBUG range checks)
+    gs_device_status* status;
 };
 
 // Host-side launchers (defined next to their kernels).  Each returns the launch status.

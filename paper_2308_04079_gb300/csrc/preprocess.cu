@@ -9,9 +9,9 @@
 //   conic = Sigma'^-1 (stored as its Cholesky factor); radius = ceil(3 sqrt(lambda_max));
 //   mean2D = (fx x/z + cx, fy y/z + cy) in double-float;
 //   tile rectangle (culled when empty); rgb = max(0, sum_k c_k Y_k((mu - C)/|mu - C|)).
-// Backward: the same quantities recomputed, then dL/dSigma' (accumulated per pixel by the tile
-//   traversal) -> dL/dV = 2 H V -> dL/dM = (J W)^T dL/dV -> (s, R) -> q_hat -> q (normalisation
-//   Jacobian);
+// Backward: the same quantities recomputed, then dL/dSigma' = L K L^T (K accumulated per pixel by
+//   the tile traversal in the whitened frame of the conic's Cholesky factor L) -> dL/dV = 2 H V
+//   -> dL/dM = (J W)^T dL/dV -> (s, R) -> q_hat -> q (normalisation Jacobian);
 //   dL/d(J W) -> dL/dJ -> dL/dt; dL/dmean2D -> dL/dt; dL/dt -> dL/dmu = W^T dL/dt;
 //   dL/drgb (clamp mask) -> dL/dSH = Y dL/drgb and -> dL/d dir -> dL/dmu.
 #include "gs_device.cuh"
@@ -224,20 +224,27 @@ __device__ __forceinline__ void bwd_view(const PreprocessBwdArgs& a, int i, cons
                                          float4 q, const float* f, BwdAcc<DEG>& acc) {
     constexpr int D = BwdAcc<DEG>::D;
     const CamK& c = a.cam;
-    const float4 g0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i];       // du dv dS00 dS01
-    const float4 g1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];   // dS11 do dr dg
+    const float4 g0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i];       // P Q K00 K01
+    const float4 g1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];   // K11 do dr dg
     const float g2 = a.grad2d[12 * i + 8];                                    // db(rgb)
+    const float4 L = a.conic[i];                                              // (l11, l21, l22, o)
     Proj p;
     project_mean(mu, c, p);
     project_cov(s, q, c, a.cfg.dilation, p);
-    // dL/dSigma' (full-matrix convention, symmetric) accumulated by the tile traversal.
-    const float H00 = g0.z, H01 = g0.w, H11 = g1.x;
-    // Sigma'_raw = V V^T: dL/dV = 2 H V.
+    // The tile traversal summed dL/dpower (p, q) and K = (1/2) dL/dpower (p, q)(p, q)^T in the
+    // whitened frame (p, q) = L^T d of the conic's Cholesky factor L; with g = Sigma'^-1 d = L (p, q):
+    // dL/dmean2D = L (P, Q) and dL/dSigma' = L K L^T =: H.
+    const float du = L.x * g0.x, dv = fmaf(L.y, g0.x, L.z * g0.y);
+    const float K00 = g0.z, K01 = g0.w, K11 = g1.x;
+    // Sigma'_raw = V V^T: dL/dV = 2 H V = 2 L (K (L^T V)), never forming H (whose pixel-frame
+    // entries lose the long axis of an elongated splat to cancellation).
     float dV[6];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        dV[k] = 2.f * (H00 * p.V[k] + H01 * p.V[3 + k]);
-        dV[3 + k] = 2.f * (H01 * p.V[k] + H11 * p.V[3 + k]);
+        const float w0 = fmaf(L.x, p.V[k], L.y * p.V[3 + k]), w1 = L.z * p.V[3 + k];   // L^T V
+        const float z0 = fmaf(K00, w0, K01 * w1), z1 = fmaf(K01, w0, K11 * w1);         // K L^T V
+        dV[k] = 2.f * (L.x * z0);
+        dV[3 + k] = 2.f * fmaf(L.y, z0, L.z * z1);
     }
     // V = T2 M: dL/dM = T2^T dV, dL/dT2 = dV M^T.
     float dM[9], dT2[6];
@@ -282,7 +289,6 @@ __device__ __forceinline__ void bwd_view(const PreprocessBwdArgs& a, int i, cons
         dJ11 += dT2[3 + k] * c.R[3 + k];
         dJ12 += dT2[3 + k] * c.R[6 + k];
     }
-    const float du = g0.x, dv = g0.y;
     const float iz = 1.0f / p.tz, iz2 = iz * iz;
     const float fx = c.fx, fy = c.fy;
     const float dt0 = du * fx * iz - dJ02 * fx * iz2;

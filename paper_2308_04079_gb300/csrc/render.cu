@@ -20,8 +20,15 @@
 //   the colour behind the current Gaussian (normalised by the transmittance in front of it; R
 //   starts at bg) on the pixel's dL/dC, which is all the recurrence needs:
 //     dL/dc_i = a_i T_i dL/dC,  dL/da_i = T_i (c_i - R_{i+1}) . dL/dC,  R_i = a_i c_i + (1 - a_i) R_{i+1}.
-//   Through a = o G (zero when clamped), with g = Sigma'^-1 d: d(power)/d(mean) = g and
-//   d(power)/d(Sigma') = g g^T / 2.  A thread sums its pixels' dL/d(mean2D, Sigma', opacity,
+//   Through a = o G (zero when clamped), with g = Sigma'^-1 d = L (p, q) (L the Cholesky factor
+//   of the conic, (p, q) = L^T d): d(power)/d(mean) = g and d(power)/d(Sigma') = g g^T / 2.  The
+//   mean and Sigma' sums are kept in the whitened frame of L: sum dL/dpower (p, q) and
+//   (1/2) sum dL/dpower (p, q)(p, q)^T =: K; the per-Gaussian stage maps them back with the same
+//   stored L (dL/dmean2D = L (p, q) sums, dL/dSigma' = L K L^T contracted without forming it).
+//   In pixel coordinates the three entries of dL/dSigma' of an elongated splat are all dominated
+//   by its minor axis and their major-axis part, which the scale along the long axis needs, is
+//   lost to cancellation in fp32 sums over many pixels; in the whitened frame every direction of
+//   the splat has the same scale.  A thread sums its pixels' terms (mean, Sigma', opacity,
 //   colour); when more than twelve lanes of a warp contributed, the warp sums its lanes with a
 //   transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals with one atomic
 //   instruction, otherwise the contributing lanes add their own sums.
@@ -43,8 +50,10 @@ namespace {
 
 // sqrt(log2(e) / 2): scales the Cholesky factor so that p^2 + q^2 = -log2(e) power.
 constexpr float kScaleLog2 = 0.84932180028801907f;
-// 1 / kScaleLog2^2 = 2 ln 2: converts scaled (p, q) products back to natural units.
-constexpr float kTwoLn2 = 1.3862943611198906f;
+// 1 / kScaleLog2 = sqrt(2 ln 2): scaled p, q back to the whitened frame of the unscaled factor.
+constexpr float kUnscale = 1.1774100225154747f;
+// (1/2) / kScaleLog2^2 = ln 2: scaled (p, q)(p, q)^T sums to K = (1/2) sum dL/dpower (p, q)(p, q)^T.
+constexpr float kLn2 = 0.69314718055994531f;
 // At most this many contributing lanes add their own sums instead of a warp reduction.
 constexpr int kDirectLanes = 12;
 
@@ -171,7 +180,12 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     constexpr int WROWS = 32 / TPR;   // tile rows per warp
     const float wy0 = (float)((threadIdx.x >> 5) * WROWS), wy1 = wy0 + (float)(WROWS - 1);
     const float wx1 = (float)(c.tile_w - 1);
-    const uint32_t start = a.ranges[2 * tile], end = a.ranges[2 * tile + 1];
+    const uint32_t start = a.ranges[2 * tile];
+    uint32_t end = a.ranges[2 * tile + 1];
+    if (GS_DEBUG && (end < start || end > a.capacity)) {   // a range outside the instance lists
+        if (threadIdx.x == 0) debug_fail(a.status);
+        end = start;
+    }
     const float amax = a.cfg.alpha_max, tmin = a.cfg.T_min;
     const float log2_amin = __log2f(a.cfg.alpha_min);
 
@@ -193,7 +207,10 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
         const int nb = (int)min((uint32_t)a.batch, end - b);
         for (int k = threadIdx.x; k < nb; k += nthreads) {
             uint32_t g = a.vals[b + k];
-            if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
+            if (g >= (uint32_t)a.n) {   // only reachable after a timed-out sort
+                debug_fail(a.status);
+                g = 0;
+            }
             Staged st;
             float2 lim;
             stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st, lim);
@@ -278,7 +295,12 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     const int x0 = tx * c.tile_w, y0 = ty * c.tile_h;
     const int py = y0 + ly;
     const float lyf = (float)ly, c0f = (float)c0;
-    const uint32_t start = a.ranges[2 * tile], len = a.ranges[2 * tile + 1] - start;
+    const uint32_t start = a.ranges[2 * tile];
+    uint32_t len = a.ranges[2 * tile + 1] - start;
+    if (GS_DEBUG && (a.ranges[2 * tile + 1] < start || a.ranges[2 * tile + 1] > a.capacity)) {
+        if (threadIdx.x == 0) debug_fail(a.status);
+        len = 0;
+    }
     constexpr int WROWS = 32 / TPR;   // tile rows per warp
     const float wy0 = (float)((threadIdx.x >> 5) * WROWS), wy1 = wy0 + (float)(WROWS - 1);
     const float wx1 = (float)(c.tile_w - 1);
@@ -330,7 +352,10 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
         __syncthreads();
         for (int k = threadIdx.x; k < nb; k += nthreads) {
             uint32_t g = a.vals[start + (uint32_t)(bend - 1 - k)];
-            if (g >= (uint32_t)a.n) g = 0;   // only reachable after a timed-out sort
+            if (g >= (uint32_t)a.n) {   // only reachable after a timed-out sort
+                debug_fail(a.status);
+                g = 0;
+            }
             Staged st;
             float2 lim;
             stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st, lim);
@@ -352,7 +377,6 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
             splat_row(st, lyf, c0f, (float)TPR, p0, dp, q, qq);
             if (pos < tmax && qq <= st.a.z) {                      // s >= q^2: else the whole row skips
                 const float4 col = s_rgb[k];
-                const float qv = __fmul_rn(st.b.z, q);
 #pragma unroll
                 for (int j = 0; j < PX; ++j) {
                     float p;
@@ -376,18 +400,16 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                     g[7] += w * dLg[j];
                     g[8] += w * dLb[j];
                     if (oG <= amax) {
-                        // dpow = dL/d(power); g = Sigma'^-1 d = 2 ln 2 (u, v) with (u, v) = L' (p, q):
-                        // sums of dpow (u, v) and dpow (u, v)(u, v)^T here, the constant factors
-                        // 1/o, 2 ln 2 and (2 ln 2)^2 / 2 once per splat below
+                        // dpow = dL/d(power): sums of dpow (p, q) and dpow (p, q)(p, q)^T in the
+                        // whitened frame (scaled p, q), the constant factors 1/o, 1/kScaleLog2 and
+                        // ln 2 once per splat below
                         const float dpow = oG * dalpha;
-                        const float u = st.b.x * p;
-                        const float v = fmaf(st.b.y, p, qv);
-                        const float du = dpow * u, dv = dpow * v;
-                        g[0] += du;
-                        g[1] += dv;
-                        g[2] = fmaf(du, u, g[2]);
-                        g[3] = fmaf(du, v, g[3]);
-                        g[4] = fmaf(dv, v, g[4]);
+                        const float dpp = dpow * p, dpq = dpow * q;
+                        g[0] += dpp;
+                        g[1] += dpq;
+                        g[2] = fmaf(dpp, p, g[2]);
+                        g[3] = fmaf(dpp, q, g[3]);
+                        g[4] = fmaf(dpq, q, g[4]);
                         g[5] += dpow;
                     }
                 }
@@ -395,7 +417,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
             const uint32_t who = __ballot_sync(0xffffffffu, contrib);
             if (who == 0) continue;
             float* dst = a.grad2d + 12 * (size_t)s_idx[k];
-            const float k1 = kTwoLn2, k2 = 0.5f * kTwoLn2 * kTwoLn2, ko = st.b.w;
+            const float k1 = kUnscale, k2 = kLn2, ko = st.b.w;
             if (__popc(who) <= kDirectLanes) {
                 // few contributing lanes: each adds its own sums (cheaper than a butterfly)
                 if (contrib) {

@@ -49,7 +49,9 @@ StaticScratch* g_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up once per device.  The first
 // lookup may load the module on that device, so the first call on each device must not be
-// made while the stream is being captured.
+// made while the stream is being captured.  The cache is keyed by device ordinal only: a
+// cudaDeviceReset unloads the module and leaves the cached address stale (documented in gs.h:
+// no further calls on a device after resetting it).
 StaticScratch* scratch_address(int dev) {
     std::lock_guard<std::mutex> lock(g_addr_mutex);
     if (!g_addr[dev]) {
@@ -106,6 +108,7 @@ extern "C" gs_status gs_depth_order_static(int n, const float* depth, const int*
         a.lookback_next = last ? nullptr : sc->lookback[(p + 1) % 2];
         a.chunk_counter = &sc->counters[p];
         a.status = status;
+        a.spin_limit = kSpinLimit;
         if (launch_onesweep(m, chunks, s) != cudaSuccess) return GS_ERR_CUDA;
     }
     return GS_OK;

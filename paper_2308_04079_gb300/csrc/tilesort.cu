@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kColThreads, 6) k_col_count(const __grid_const
             // first one, from the loaded records (thread 0 adds the one in front)
             if (tid == 0) {
                 const uint32_t prev = chunk > 0 ? a.geom[j0 - 1] : 0xFFFFFFFFu;
-                s_skip = (a.status->flags & (kFlagCapacity | kFlagTimeout)) != 0;
+                s_skip = (a.status->flags & kFlagAbort) != 0;
                 s_ra = rk_row(gk[0]);
                 s_cont = chunk > 0 && rk_row(prev) == rk_row(gk[0]);
             }
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kColThreads, 6) k_col_count(const __grid_const
                         if (stop) break;
                         j -= used;
                         if (wait) {
-                            if (++spins > kSpinLimit) {
+                            if (++spins > a.spin_limit) {
                                 atomicOr(&a.status->flags, kFlagTimeout);
                                 break;
                             }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const __grid_constant__ Mult
     const int tid = threadIdx.x;
     const uint32_t tiles = (uint32_t)a.tiles;
     const uint32_t K = a.status->num_instances;
-    bool dead = (a.status->flags & (kFlagCapacity | kFlagTimeout)) != 0;
+    bool dead = (a.status->flags & kFlagAbort) != 0;
     uint32_t carry = 0;
     for (int pass = 0; pass < 2; ++pass) {   // the second pass clears the ranges if the total is wrong
         carry = 0;
@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const __grid_constant__ Mult
             carry += tot;
         }
         if (dead || carry == K) break;
-        dead = true;
-        if (tid == 0) atomicOr(&a.status->flags, kFlagTimeout);
+        dead = true;   // the tile counts do not add up to the instance count
+        if (tid == 0) atomicOr(&a.status->flags, kFlagInternal);
     }
     if (tid == 0) a.status->num_segments = *a.num_segments;
 }
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kColThreads, 4) k_col_scatter(const __grid_con
             const uint32_t K = (uint32_t)min((unsigned long long)a.status->num_instances, a.capacity);
             constexpr uint32_t sent = 255u;   // digit of the padding items (columns are <= 254)
             if (tid == 0) {
-                s_skip = (a.status->flags & (kFlagCapacity | kFlagTimeout)) != 0;
+                s_skip = (a.status->flags & kFlagAbort) != 0;
                 s_cont = chunk > 0 && rk_row(a.geom[j0 - 1]) == rk_row(a.geom[j0]);
             }
             // thread t: records [8 t, 8 t + 8) of the chunk; their first instances by a block scan
@@ -440,6 +440,8 @@ __global__ void __launch_bounds__(kColThreads, 4) k_col_scatter(const __grid_con
                         if (dest < K) {
                             a.keys_out[dest] = rbase + d;
                             a.vals_out[dest] = s_item[s];
+                        } else {
+                            debug_fail(a.status);
                         }
                     }
                     __syncthreads();

@@ -166,6 +166,10 @@ class Frame:
     def bin_sort(self) -> None:
         abi.gs_bin_sort(self.frame, _stream())
 
+    def bin_sort_timed(self) -> list:
+        """gs_bin_sort with each launch timed: [(label, ms), ...] (synchronises)."""
+        return abi.gs_bin_sort_timed(self.frame, _stream())
+
     def render_forward(self, bg, out_rgb: torch.Tensor, out_T: torch.Tensor, out_last: torch.Tensor) -> None:
         abi.gs_render_forward(self.frame, bg, out_rgb.data_ptr(), out_T.data_ptr(), out_last.data_ptr(), _stream())
 
@@ -215,7 +219,7 @@ class Frame:
             self.preprocess(g)
             self.bin_sort()
             code, st = self.status()
-        if code in (abi.GS_ERR_CAPACITY, abi.GS_ERR_TIMEOUT):
+        if code in (abi.GS_ERR_CAPACITY, abi.GS_ERR_TIMEOUT, abi.GS_ERR_INTERNAL):
             raise abi.GSError(code, "gs_bin_sort")
         self.last_status = st
 
@@ -259,7 +263,7 @@ class FrameBatch:
                 if code == abi.GS_ERR_CAPACITY:
                     f._alloc(int(st.num_instances * 1.25) + 1024)
                     grown = True
-                elif code == abi.GS_ERR_TIMEOUT:
+                elif code in (abi.GS_ERR_TIMEOUT, abi.GS_ERR_INTERNAL):
                     raise abi.GSError(code, "gs_batch_bin_sort")
                 f.last_status = st
             if not grown:
@@ -290,11 +294,26 @@ class FrameBatch:
         return [tuple(float(x) for x in b) for b in bg]
 
 
+def _cfg_bytes(cfg) -> bytes:
+    return bytes(cfg if cfg is not None else make_config())
+
+
+def _frame_for(frame: Frame | None, n: int, camera, cfg, device) -> Frame:
+    """``frame`` made ready for (n Gaussians, camera, cfg), or a new Frame when its Gaussian
+    count, image size or constants differ or its workspace still waits for a backward pass."""
+    cam = camera_struct(camera)
+    if (frame is None or frame.n != n or (frame.cam.width, frame.cam.height) != (cam.width, cam.height)
+            or bytes(frame.cfg) != _cfg_bytes(cfg) or getattr(frame, "pending_backward", False)):
+        return Frame(n, camera, cfg, device=device)
+    frame.set_camera(camera)
+    return frame
+
+
 def render(g: GaussianTensors, camera, bg=(0.0, 0.0, 0.0), cfg=None, frame: Frame | None = None):
-    """Forward render.  Returns (image [3,H,W], T_final [H,W], last [H,W] int32, frame)."""
+    """Forward render.  Returns (image [3,H,W], T_final [H,W], last [H,W] int32, frame); a
+    given ``frame`` is reused (with this camera) when its size and constants fit."""
     g = g.prepared()
-    if frame is None or frame.n != g.n:
-        frame = Frame(g.n, camera, cfg, device=g.means.device)
+    frame = _frame_for(frame, g.n, camera, cfg, g.means.device)
     frame.ensure_binned(g)
     img, T, last = frame.outputs()
     frame.render_forward(bg, img, T, last)
@@ -303,20 +322,23 @@ def render(g: GaussianTensors, camera, bg=(0.0, 0.0, 0.0), cfg=None, frame: Fram
 
 class RasterizeFunction(torch.autograd.Function):
     """image = Rasterize(means, scales, quats, opacities, sh) for one camera (Algorithm 2);
-    backward through the Sec. 6 traversal and the App. A chain rule."""
+    backward through the Sec. 6 traversal and the App. A chain rule.  The workspace of a
+    forward pass stays reserved for its backward pass (it holds the binned instances and the
+    screen-space splats that the backward reads); a second forward before that backward gets a
+    workspace of its own."""
 
     @staticmethod
     def forward(ctx, means, scales, quats, opacities, sh, settings):
         g = GaussianTensors(means, scales, quats, opacities, sh, settings["sh_degree"]).prepared()
-        frame = settings.get("frame")
-        if frame is None or frame.n != g.n:
-            frame = Frame(g.n, settings["camera"], settings.get("cfg"), device=g.means.device)
-            settings["frame"] = frame
+        frame = _frame_for(settings.get("frame"), g.n, settings["camera"], settings.get("cfg"), g.means.device)
+        settings["frame"] = frame
         frame.ensure_binned(g)
         img, T, last = frame.outputs()
         frame.render_forward(settings["bg"], img, T, last)
+        frame.pending_backward = True
         ctx.frame = frame
         ctx.g = g
+        ctx.bg = settings["bg"]
         ctx.settings = settings
         ctx.save_for_backward(T, last)
         return img
@@ -326,7 +348,8 @@ class RasterizeFunction(torch.autograd.Function):
         T, last = ctx.saved_tensors
         g = ctx.g
         grads = ctx.frame.new_grads(g)
-        ctx.frame.render_backward(g, ctx.settings["bg"], _prep(dimg), T, last, grads)
+        ctx.frame.render_backward(g, ctx.bg, _prep(dimg), T, last, grads)
+        ctx.frame.pending_backward = False
         ctx.settings["mean2d_grad"] = grads["mean2d"]
         return grads["means"], grads["scales"], grads["quats"], grads["opacities"], grads["sh"], None
 
@@ -334,8 +357,10 @@ class RasterizeFunction(torch.autograd.Function):
 def rasterize(means, scales, quats, opacities, sh, sh_degree: int, camera, bg=(0.0, 0.0, 0.0), cfg=None,
               settings: dict | None = None) -> torch.Tensor:
     """Differentiable render of one view; returns the image [3, H, W].  ``settings`` (a dict)
-    may be reused across calls to keep the workspace; after backward it holds the view-space
-    mean gradient under ``"mean2d_grad"``."""
+    may be reused across calls and views to keep the workspace: each call renders with its
+    own camera, background and constants, and a call made before the previous call's backward
+    pass gets a fresh workspace.  After backward it holds the view-space mean gradient under
+    ``"mean2d_grad"``."""
     s = settings if settings is not None else {}
     s.update(sh_degree=int(sh_degree), camera=camera, bg=tuple(float(x) for x in bg), cfg=cfg)
     return RasterizeFunction.apply(means, scales, quats, opacities, sh, s)

@@ -16,6 +16,7 @@ HEADER = os.path.join(ROOT, "include", "gs.h")
 def lib():
     from paper_2308_04079_gb300 import _abi, build
     build.build()
+    build.build(debug=True)
     return _abi.load()
 
 
@@ -39,6 +40,10 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
     from paper_2308_04079_gb300 import _abi
     assert sorted(n for n, _, _ in _abi.SIGNATURES) == _declared_functions()
+    # the GS_DEBUG build exports the same entry points
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB_DEBUG], capture_output=True, text=True,
+                         check=True).stdout
+    assert set(re.findall(r"\bT (gs_[a-z0-9_]+)$", out, flags=re.M)) >= set(_declared_functions())
 
 
 def test_struct_layouts_match_header(lib, tmp_path):
@@ -73,6 +78,15 @@ def test_default_config_is_the_papers(lib):
     assert c.alpha_min == pytest.approx(1 / 255) and c.alpha_max == pytest.approx(0.99)
     assert c.T_min == pytest.approx(1e-4) and c.dilation == pytest.approx(0.3)
     assert c.guard == pytest.approx(1.3) and c.extent == pytest.approx(3.0)
+    assert c.spin_limit == _abi.GS_DEFAULT_SPIN_LIMIT == 1 << 22
+
+
+def test_peak_microbenchmarks_validate_before_touching_the_device(lib):
+    from paper_2308_04079_gb300 import _abi
+    assert lib.gs_peak_fma(0, 10, 1, None) == _abi.GS_ERR_INVALID_ARG
+    assert lib.gs_peak_ex2(4, 0, 1, None) == _abi.GS_ERR_INVALID_ARG
+    assert lib.gs_peak_fma(4, 10, None, None) == _abi.GS_ERR_INVALID_ARG
+    assert _abi.gs_peak_ops(304, 1000) == 304 * 1024 * 1000 * 16 * 8
 
 
 def test_workspace_size_and_layout(lib):

@@ -1,0 +1,140 @@
+"""Failure paths, exercised without faulting or hanging the GPU.
+
+* A bounded spin-wait that runs out: with cfg.spin_limit = 0 every block of the binning stage
+  that finds a predecessor's prefix unpublished gives up at once, so the call returns promptly
+  with GS_ERR_TIMEOUT, writes nothing past its workspace, renders only the background from a
+  frame whose binning timed out, and the next call with the default limit on the same
+  workspace is exact.
+* The GS_DEBUG build (libgs_gb300_debug.so, selected by GS_DEBUG=1): the small parity cases run
+  clean under its bounds checks, and a corrupted tile range or instance index is reported as
+  GS_ERR_INTERNAL instead of being read out of bounds.
+"""
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _frame_with_guard(n, cam, cfg, capacity, guard=1 << 16):
+    """A Frame whose workspace is followed by `guard` bytes of a known pattern."""
+    import torch
+    from paper_2308_04079_gb300 import Frame
+    fr = Frame(n, cam, cfg, capacity=capacity)
+    size = fr.ws.numel()
+    big = torch.full((size + guard,), 0xA5, dtype=torch.uint8, device=fr.ws.device)
+    big[:size].copy_(fr.ws)
+    fr.ws = big[:size]
+    fr.frame.ws = big.data_ptr()
+    return fr, big, size
+
+
+def test_spin_limit_zero_times_out_promptly_and_the_next_call_is_exact():
+    import torch
+    from paper_2308_04079_gb300 import Frame, GaussianTensors, _abi, make_config
+    g, cam, bg, _ = S.config2()
+    gt = GaussianTensors.from_numpy(g).prepared()
+    ref = Frame(gt.n, cam, make_config())
+    ref.ensure_binned(gt)
+    img_ref, T_ref, last_ref = ref.outputs()
+    ref.render_forward(bg, img_ref, T_ref, last_ref)
+    cap = ref.capacity
+
+    fr, big, size = _frame_with_guard(gt.n, cam, make_config(spin_limit=0), cap)
+    assert fr.cfg.spin_limit == 0 and make_config().spin_limit == _abi.GS_DEFAULT_SPIN_LIMIT
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fr.preprocess(gt)
+    fr.bin_sort()
+    code, st = fr.status()
+    elapsed = time.perf_counter() - t0
+    assert code == _abi.GS_ERR_TIMEOUT and st.flags & _abi.FLAG_TIMEOUT, (code, st.flags)
+    assert elapsed < 5.0, elapsed
+    # the later binning kernels wrote nothing: every tile range is empty, so the frame renders
+    # the background only
+    img, T, last = fr.outputs()
+    fr.render_forward(bg, img, T, last)
+    torch.cuda.synchronize()
+    assert torch.all(fr.view("ranges", torch.int32, 2 * fr.tiles) == 0)
+    assert torch.all(last == 0) and torch.all(T == 1.0)
+    for ch in range(3):
+        assert torch.all(img[ch] == float(np.float32(bg[ch])))
+    assert torch.all(big[size:] == 0xA5), "write past the workspace"
+
+    # the same workspace with the default limit: exact
+    fr.cfg.spin_limit = _abi.GS_DEFAULT_SPIN_LIMIT
+    fr.frame.cfg = fr.cfg
+    fr.preprocess(gt)
+    fr.bin_sort()
+    code, st = fr.status()
+    assert code == _abi.GS_OK
+    fr.render_forward(bg, img, T, last)
+    torch.cuda.synchronize()
+    assert torch.equal(img, img_ref) and torch.equal(T, T_ref) and torch.equal(last, last_ref)
+    assert torch.all(big[size:] == 0xA5)
+
+
+def test_loaded_library_follows_the_debug_flag():
+    from paper_2308_04079_gb300 import _abi
+    lib = _abi.load()
+    want = "libgs_gb300_debug.so" if os.environ.get("GS_DEBUG") == "1" else "libgs_gb300.so"
+    assert os.path.basename(lib._name) == want
+    with open("/proc/self/maps") as f:
+        assert any(line.rstrip().endswith(want) for line in f)
+
+
+@pytest.mark.skipif(os.environ.get("GS_DEBUG") != "1", reason="needs the GS_DEBUG build (GS_DEBUG=1)")
+def test_debug_checks_report_a_corrupted_range_and_index():
+    """Run only under the GS_DEBUG build, whose range check empties a range that reaches past
+    the instance capacity before any instance is read (the release build trusts the ranges it
+    computed itself)."""
+    import torch
+    from paper_2308_04079_gb300 import GaussianTensors, _abi
+    from gpu_util import gpu_frame
+    g, cam = S.tiny_scene(71, n=300, width=80, height=48)
+    fr, gt = gpu_frame(g, cam)
+    fr.ensure_binned(gt)
+    img, T, last = fr.outputs()
+    fr.render_forward((0, 0, 0), img, T, last)
+    assert fr.status()[0] == _abi.GS_OK
+    ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).view(-1, 2)
+    busy = int(torch.argmax(ranges[:, 1] - ranges[:, 0]))
+    saved = ranges[busy].clone()
+    ranges[busy, 1] = fr.capacity + 1000            # a range past the instance lists
+    fr.render_forward((0, 0, 0), img, T, last)
+    code, st = fr.status()
+    assert code == _abi.GS_ERR_INTERNAL and st.flags & _abi.FLAG_INTERNAL
+    # an instance naming a Gaussian that does not exist
+    ranges[busy] = saved
+    fr.ensure_binned(gt)
+    vals = fr.view("vals_sorted", torch.int32, fr.capacity)
+    vals[int(ranges[busy, 0])] = gt.n + 5
+    fr.render_forward((0, 0, 0), img, T, last)
+    assert fr.status()[0] == _abi.GS_ERR_INTERNAL
+
+
+def test_small_parity_cases_run_clean_under_the_debug_build():
+    """The tiny scenes and config 1 (forward, backward, binning of both schedules) with the
+    GS_DEBUG library: every bounds check passes and the results still match the oracle."""
+    if os.environ.get("GS_DEBUG") == "1":
+        pytest.skip("this test starts the GS_DEBUG run itself")
+    sel = ["tests/test_gpu_failure.py::test_loaded_library_follows_the_debug_flag",
+           "tests/test_gpu_failure.py::test_debug_checks_report_a_corrupted_range_and_index",
+           "tests/test_gpu_render.py::test_tiny_scenes", "tests/test_gpu_render.py::test_config1",
+           "tests/test_gpu_backward.py::test_tiny_scene_gradients",
+           "tests/test_gpu_binning.py::test_bin_sort_bit_exact",
+           "tests/test_gpu_binning.py::test_bin_sort_empty_and_all_culled",
+           "tests/test_gpu_variants.py::test_limited_bw_gradients_match_the_oracle"]
+    env = dict(os.environ, GS_DEBUG="1")
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider", *sel],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stdout[-3000:] + res.stderr[-2000:]
+    summary = [ln for ln in res.stdout.splitlines() if " passed" in ln]
+    assert summary and "skipped" not in summary[-1] and "failed" not in summary[-1], res.stdout[-800:]
