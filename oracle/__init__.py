@@ -22,27 +22,35 @@ Functions (each a thin ctypes marshaller around ``gs_oracle.c``):
 The Limited-BW ablation of Sec. 7.3 is ``cfg_array(grad_limit=N)``: gradients reach only the
 N front-most blended Gaussians of each pixel.
 
-Every pixel/Gaussian decision that lies within a relative margin of its threshold is
-reported as ambiguous (``pix_amb``, ``gauss_amb``), see the bit constants below.
+Every discrete decision (cull, radius, tile rectangle, skip, clamp, stop, depth order) that
+lies within the error margin of an FP32 evaluation of its threshold is reported, and each is
+evaluated the other way too: :func:`render_forward` returns the flipped alternatives of every
+such pixel (``alt``), :func:`render_backward` the per-Gaussian sum of the magnitudes of the
+changes they make to the gradients (``allow``).  Tests check every pixel and every Gaussian
+against them instead of excluding any.
 """
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
 from . import build as _build
 
-# per-Gaussian ambiguity bits
+# per-Gaussian bits of the per-Gaussian stage (preprocess)
 AMB_CULL = 1
 AMB_RECT = 2
 AMB_RGB = 4
-AMB_PIXEL = 8
-AMB_CLAMP = 16
-# per-pixel ambiguity bits
-PIX_DECISION = 1
-PIX_CLAMP = 2
-PIX_ANY = 4
+# kinds of pixel decision near a threshold; pix_dec has bit (kind - 1) set for each kind present
+DEC_SKIP = 1    # alpha < 1/255 (App. C)
+DEC_CLAMP = 2   # alpha clamped at 0.99 (App. C)
+DEC_STOP = 3    # stop before T (1 - alpha) < 1e-4 (App. C)
+DEC_SWAP = 4    # equal or adjacent fp32 depth keys
+DEC_DROP = 5    # tile membership near its threshold: the Gaussian may be absent
+DEC_ADD = 6     # a Gaussian outside the tile's list may be in it
+
+U = 2.0 ** -24  # unit roundoff of IEEE fp32
 
 DEFAULT_CFG = dict(
     tile_w=16, tile_h=16,          # Sec. 6 / App. C: 16x16 tiles
@@ -53,13 +61,11 @@ DEFAULT_CFG = dict(
     guard=1.3,                     # guard band on the frustum tangents (Sec. 6)
     extent=3.0,                    # 3-sigma screen extent (Sec. 6, 99% interval)
     radius_max=1 << 24,            # radius clamp (pixels)
-    eps_geom=2e-6,                 # ambiguity margin, geometric decisions (relative)
-    eps_alpha=3e-5,                # ambiguity margin, alpha skip / clamp decisions (relative)
-    eps_T=1e-3,                    # ambiguity margin, transmittance stop decision (relative)
-    T_impact=1e-4 / (2.0 / 255.0), # skip flips behind less light cannot move a pixel by 1e-4
-    T_grad=1e-3,                   # flips behind less light are negligible for gradients
+    eps_geom=2e-6,                 # margin, geometric decisions (relative): ~32 u
+    eps_alpha=3e-5,                # margin, o G at the skip / clamp thresholds (relative), besides the power's
+    eps_T=1e-3,                    # margin, transmittance at the stop threshold (relative)
     grad_limit=0,                  # > 0: gradients for the N front-most blended Gaussians only
-    eps_conic=5e-7,                # fp32 Cholesky factor of the conic: relative error, ~4 ulp
+    eps_power=20 * U,              # margin of the power relative to its terms' magnitude sum (gs_oracle.c)
 )
 
 _lib = None
@@ -68,7 +74,9 @@ _lib = None
 def _load():
     global _lib
     if _lib is None:
-        path = _build.build()
+        # GS_ORACLE_LIB: a differently built oracle library (the mutant tests plant errors in a
+        # copy of gs_oracle.c and check that the pins catch them)
+        path = os.environ.get("GS_ORACLE_LIB") or _build.build()
         lib = ctypes.CDLL(path)
         D = ctypes.POINTER(ctypes.c_double)
         I32 = ctypes.POINTER(ctypes.c_int32)
@@ -81,14 +89,19 @@ def _load():
         lib.orc_sh_eval.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D]
         lib.orc_preprocess.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
                                        I32, D, D, D, D, I32, I32, D, D, U32, I32, I32]
+        I64 = ctypes.POINTER(ctypes.c_int64)
+        LP = ctypes.POINTER(ctypes.c_long)
         lib.orc_render_forward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
-                                           D, U8, D, D, I32, I32, U8, U32]
+                                           D, U8, D, D, I32, I32, U8, U32, L, I64, I32, D, D, I32, LP]
         lib.orc_render_backward.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D,
-                                            D, U8, D, D, D, D, D, D, D, D, D, D, U8, U32]
+                                            D, U8, D, D, D, D, D, D, D, D, D, D, U8, U32,
+                                            D, D, D, D, D, D, D, D, D, D, LP]
         lib.orc_bin.argtypes = [L, F, F, I32, F, F, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 L, U64, U32, U32]
         lib.orc_bin.restype = L
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_reach_needed.argtypes = [L, D, D, D, D, D, ctypes.c_int, ctypes.c_int, D, D, L, I64]
+        lib.orc_reach_needed.restype = L
         _lib = lib
     return _lib
 
@@ -126,7 +139,7 @@ def cfg_array(**overrides) -> np.ndarray:
         c[k] = v
     return np.array([c["tile_w"], c["tile_h"], c["alpha_min"], c["alpha_max"], c["T_min"],
                      c["dilation"], c["guard"], c["extent"], c["radius_max"], c["eps_geom"],
-                     c["eps_alpha"], c["eps_T"], c["T_impact"], c["T_grad"], c["grad_limit"], c["eps_conic"]],
+                     c["eps_alpha"], c["eps_T"], c["grad_limit"], c["eps_power"]],
                     dtype=np.float64)
 
 
@@ -192,32 +205,59 @@ def _mask_arg(cam, cfg, tile_mask):
 
 def render_forward(g, cam, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
     """Planar image [3, H, W], final transmittance [H, W], last contributor (1-based
-    position in the tile list, 0 = none) [H, W] and its Gaussian index (-1 = none) [H, W],
-    per-pixel and per-Gaussian ambiguity."""
+    position in the tile list, 0 = none) [H, W] and its Gaussian index (-1 = none) [H, W];
+    ``pix_dec`` [H, W]: bit (kind - 1) set for each kind of decision near its threshold at the
+    pixel; ``alt``: one entry per such decision, with the pixel's colour, T and last Gaussian
+    when that decision is taken the other way (``pix`` flat pixel index, ``kind``, ``g0``,
+    ``g1`` the Gaussians involved); ``gauss_amb`` the per-Gaussian stage's bits."""
     cfg = cfg_array() if cfg is None else cfg
     n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
     ca = cam_array(cam)
     W, H = cam.width, cam.height
     bg = _f64(bg).reshape(3)
     m = _mask_arg(cam, cfg, tile_mask)
-    img = np.zeros((3, H, W))
-    T = np.ones((H, W))
-    last = np.zeros((H, W), np.int32)
-    last_id = np.full((H, W), -1, np.int32)
-    pix = np.zeros((H, W), np.uint8)
-    gamb = np.zeros(n, np.uint32)
     D = ctypes.c_double
-    _load().orc_render_forward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
-                               _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(img, D), _p(T, D),
-                               _p(last, ctypes.c_int32), _p(last_id, ctypes.c_int32), _p(pix, ctypes.c_uint8),
-                               _p(gamb, ctypes.c_uint32))
-    return dict(img=img, T=T, last=last, last_id=last_id, pix_amb=pix, gauss_amb=gamb)
+    cap = 4096
+    while True:
+        img = np.zeros((3, H, W))
+        T = np.ones((H, W))
+        last = np.zeros((H, W), np.int32)
+        last_id = np.full((H, W), -1, np.int32)
+        pix = np.zeros((H, W), np.uint8)
+        gamb = np.zeros(n, np.uint32)
+        a_pix = np.zeros(cap, np.int64)
+        a_dec = np.zeros((cap, 3), np.int32)
+        a_img = np.zeros((cap, 3))
+        a_T = np.zeros(cap)
+        a_last = np.zeros(cap, np.int32)
+        counts = np.zeros(2, np.int64)
+        _load().orc_render_forward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
+                                   _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(img, D), _p(T, D),
+                                   _p(last, ctypes.c_int32), _p(last_id, ctypes.c_int32), _p(pix, ctypes.c_uint8),
+                                   _p(gamb, ctypes.c_uint32), cap, _p(a_pix, ctypes.c_int64),
+                                   _p(a_dec, ctypes.c_int32), _p(a_img, D), _p(a_T, D),
+                                   _p(a_last, ctypes.c_int32), _p(counts, ctypes.c_long))
+        k = int(counts[0])
+        if k <= cap:
+            break
+        cap = k + 1024
+    order = np.argsort(a_pix[:k], kind="stable")
+    alt = dict(pix=a_pix[:k][order], kind=a_dec[:k, 0][order], g0=a_dec[:k, 1][order], g1=a_dec[:k, 2][order],
+               img=a_img[:k][order], T=a_T[:k][order], last_id=a_last[:k][order])
+    return dict(img=img, T=T, last=last, last_id=last_id, pix_dec=pix, gauss_amb=gamb, alt=alt,
+                dec_overflow=int(counts[1]))
 
 
-def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None) -> dict:
+def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None = None, tile_mask=None,
+                    allowance: bool = True) -> dict:
     """Analytic FP64 gradients of L = <dL_dimg, image> w.r.t. every input, plus the
     screen-space gradients that the backward walk accumulates: mean2D (uv), conic, opacity,
-    colour, and dL/dSigma' (cov2d: entries 00, 01, 11, full-matrix convention)."""
+    colour, and dL/dSigma' (cov2d: entries 00, 01, 11, full-matrix convention).  With
+    ``allowance``, ``allow`` holds per Gaussian and per entry the summed magnitude of the changes
+    that flipping each decision near its threshold makes to these gradients (keys as the
+    gradients, plus ``opac2d`` for the screen-space opacity term); ``flips`` counts them; and
+    ``cond`` the fp32 conditioning allowance of the chain rule (first-order effect of rounding
+    R, J W, the camera-space mean and the view direction; zero for the screen-space terms)."""
     cfg = cfg_array() if cfg is None else cfg
     n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
     ca = cam_array(cam)
@@ -227,15 +267,35 @@ def render_backward(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarray | None 
     m = _mask_arg(cam, cfg, tile_mask)
     out = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacities=np.zeros(n), sh=np.zeros_like(sh), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
-               rgb=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), pix_amb=np.zeros((H, W), np.uint8),
+               rgb=np.zeros((n, 3)), cov2d=np.zeros((n, 3)), pix_dec=np.zeros((H, W), np.uint8),
                gauss_amb=np.zeros(n, np.uint32))
+    al = cond = None
+    if allowance:
+        al = dict(screen=np.zeros((n, 9)), means=np.zeros((n, 3)), scales=np.zeros((n, 3)),
+                  quats=np.zeros((n, 4)), opacities=np.zeros(n), sh=np.zeros_like(sh))
+        cond = dict(means=np.zeros((n, 3)), scales=np.zeros((n, 3)), quats=np.zeros((n, 4)), sh=np.zeros_like(sh))
+    counts = np.zeros(2, np.int64)
     D = ctypes.c_double
+    A = (lambda k: _p(al[k], D)) if al is not None else (lambda k: None)
+    Cd = (lambda k: _p(cond[k], D)) if cond is not None else (lambda k: None)
     _load().orc_render_backward(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg, st,
                                 _p(ca, D), _p(cfg, D), _p(bg, D), _p(m, ctypes.c_uint8), _p(dimg, D),
                                 _p(out["means"], D), _p(out["scales"], D), _p(out["quats"], D),
                                 _p(out["opacities"], D), _p(out["sh"], D), _p(out["uv"], D), _p(out["conic"], D),
-                                _p(out["rgb"], D), _p(out["cov2d"], D), _p(out["pix_amb"], ctypes.c_uint8),
-                                _p(out["gauss_amb"], ctypes.c_uint32))
+                                _p(out["rgb"], D), _p(out["cov2d"], D), _p(out["pix_dec"], ctypes.c_uint8),
+                                _p(out["gauss_amb"], ctypes.c_uint32), A("screen"), A("means"), A("scales"),
+                                A("quats"), A("opacities"), A("sh"), Cd("means"), Cd("scales"), Cd("quats"),
+                                Cd("sh"), _p(counts, ctypes.c_long))
+    if al is not None:
+        scr = al.pop("screen")
+        al.update(uv=scr[:, 0:2], cov2d=scr[:, 2:5], opac2d=scr[:, 5], rgb=scr[:, 6:9])
+        out["allow"] = al
+        cond["opacities"] = np.zeros(n)
+        for k in ("uv", "cov2d", "opac2d", "rgb"):
+            cond[k] = np.zeros_like(al[k])
+        out["cond"] = cond
+    out["flips"] = int(counts[0])
+    out["dec_overflow"] = int(counts[1])
     return out
 
 
@@ -264,7 +324,29 @@ def render_backward_isotropic(g, cam, dL_dimg, bg=(0.0, 0.0, 0.0), cfg: np.ndarr
     out = render_backward(_Anisotropic(g), cam, dL_dimg, bg, cfg, tile_mask)
     out["scales"] = out["scales"].sum(axis=1)
     del out["quats"]
+    for key in ("allow", "cond"):
+        if key in out:
+            out[key]["scales"] = out[key]["scales"].sum(axis=1)
+            del out[key]["quats"]
     return out
+
+
+def reach_needed(g, cam, cfg: np.ndarray | None = None) -> np.ndarray:
+    """Sorted keys i * tiles + t of the (Gaussian, tile) pairs any binning must keep: tiles of
+    the Sec. 6 rectangle (under every rounding of it) in which some pixel centre certainly
+    reaches alpha_min in FP64 (brute force over the tile's pixels)."""
+    cfg = cfg_array() if cfg is None else cfg
+    n, means, scales, quats, opac, sh, deg, st = _gauss_args(g)
+    ca = cam_array(cam)
+    D = ctypes.c_double
+    cap = 1 << 20
+    while True:
+        out = np.zeros(cap, np.int64)
+        k = _load().orc_reach_needed(n, _p(means, D), _p(scales, D), _p(quats, D), _p(opac, D), _p(sh, D), deg,
+                                     st, _p(ca, D), _p(cfg, D), cap, _p(out, ctypes.c_int64))
+        if k <= cap:
+            return np.sort(out[:k])
+        cap = k
 
 
 def _bin_args(uv, depth, radius, chol, tau):

@@ -27,10 +27,13 @@
  * no early tile termination, no transmittance recovery by division: the backward pass
  * re-runs the pixel's forward walk and keeps every T_i.
  *
- * Decisions (cull, radius, tile rectangle, skip, clamp, stop, depth order) are also
- * reported as "ambiguous" when the FP64 value lies within a stated relative margin of its
- * threshold, so that tests can exclude pixels where an FP32 implementation may
- * legitimately decide the other way.
+ * Decisions (cull, radius, tile rectangle, skip, clamp, stop, depth order) whose FP64 value
+ * lies within the error margin of an FP32 evaluation of the same definition are reported, and
+ * each one is also evaluated the other way: the forward pass returns the pixel's colour, T and
+ * last Gaussian with that decision flipped, and the backward pass adds up, per Gaussian, the
+ * magnitude of the change the flip makes to its gradients.  A test can then check every pixel
+ * and every Gaussian: against the definition, against one of the flipped alternatives, or
+ * within the definition plus the summed effect of the flips, instead of excluding them.
  *
  * Build: gcc -O2 -std=c11 -fopenmp -ffp-contract=off -fPIC -shared (see build.py).
  */
@@ -65,12 +68,10 @@ typedef struct {
     double eps_geom;    /* relative margin for geometric decisions (cull, floor, ceil) */
     double eps_alpha;   /* relative margin for the alpha skip / clamp decisions */
     double eps_T;       /* relative margin for the transmittance stop decision */
-    double T_impact;    /* skip flips in front of which less light than this remains cannot move
-                           the pixel by the image tolerance: alpha_min * T * 2 < tolerance */
-    double T_grad;      /* a flipped decision behind less light than this is negligible for gradients */
     int grad_limit;     /* > 0: only the grad_limit front-most blended Gaussians of a pixel receive
                            gradients (Limited-BW ablation, Sec. 7.3); 0: all of them */
-    double eps_conic;   /* relative error of the fp32 Cholesky factor of the conic: see power_margin */
+    double eps_power;   /* margin of the splat power, relative to the magnitude sum of the terms of
+                           the quadratic form: see power_margin */
 } ocfg;
 
 static void read_cam(const double* c, ocam* o) {
@@ -86,26 +87,15 @@ static void read_cfg(const double* c, ocfg* o) {
     o->alpha_min = c[2]; o->alpha_max = c[3]; o->T_min = c[4];
     o->dilation = c[5]; o->guard = c[6]; o->extent = c[7];
     o->radius_max = (int)c[8]; o->eps_geom = c[9]; o->eps_alpha = c[10];
-    o->eps_T = c[11]; o->T_impact = c[12]; o->T_grad = c[13];
-    o->grad_limit = (int)c[14];
-    o->eps_conic = c[15];
+    o->eps_T = c[11];
+    o->grad_limit = (int)c[12];
+    o->eps_power = c[13];
 }
 
-/* Ambiguity bits (per Gaussian). */
+/* Per-Gaussian bits: decisions of the per-Gaussian stage near their threshold. */
 #define AMB_CULL   1u   /* a cull decision lies within eps_geom of its threshold                */
 #define AMB_RECT   2u   /* floor(u), floor(v) or the radius ceiling may round the other way     */
 #define AMB_RGB    4u   /* an SH colour channel lies within eps_geom (relative) of the 0 clamp  */
-#define AMB_PIXEL  8u   /* its own skip / order / membership decision is near a threshold at a  */
-                        /* pixel with transmittance >= T_grad                                   */
-#define AMB_CLAMP 16u   /* o*G within eps_alpha of the 0.99 clamp at a pixel with T >= T_grad   */
-
-/* Ambiguity bits (per pixel). */
-#define PIX_DECISION 1u /* a decision near its threshold that can move the pixel by more than   */
-                        /* the tolerance: skip (with T >= T_impact), stop, depth order, tile    */
-                        /* membership                                                           */
-#define PIX_CLAMP    2u /* clamp decision near threshold: value is continuous, gradient is not  */
-#define PIX_ANY      4u /* any skip / stop / order / membership decision near its threshold     */
-                        /* (the last-contributor index may differ)                              */
 
 /* ------------------------------------------------------------------------- */
 /* Small linear algebra.                                                       */
@@ -260,6 +250,7 @@ typedef struct {
     double rgb_raw[3];
     double rgb[3];
     unsigned amb;
+    unsigned rgb_amb;   /* bit ch: channel ch near the 0 clamp */
 } ogauss;
 
 static int rect_of(double u, double v, int r, const ocam* cam, const ocfg* cfg, int fu_off, int fv_off, int out[4]) {
@@ -365,8 +356,9 @@ static void gauss_forward(size_t i, const double* means, const double* scales, c
     if (!rclamped) {
         double rfrac = rr - floor(rr);
         double sr = rr > 1.0 ? rr : 1.0;
-        if (rfrac <= cfg->eps_geom * sr && rr >= 1.0) r_alt[0] = (int)floor(rr);       /* ceil may drop */
-        if (1.0 - rfrac <= cfg->eps_geom * sr || rfrac == 0.0) r_alt[1] = (int)floor(rr) + 1;
+        /* an fp32 value of rr on the other side of the integer below (above) changes ceil by one */
+        if (rfrac <= cfg->eps_geom * sr && rfrac > 0.0 && rr >= 1.0) r_alt[0] = g->radius - 1;
+        if (1.0 - rfrac <= cfg->eps_geom * sr || rfrac == 0.0) r_alt[1] = g->radius + 1;
     } else if (near_threshold(rr, cfg->radius_max, cfg->eps_geom)) {
         r_alt[0] = cfg->radius_max - 1;
     }
@@ -412,7 +404,7 @@ static void gauss_forward(size_t i, const double* means, const double* scales, c
         }
         g->rgb_raw[ch] = acc;
         g->rgb[ch] = acc > 0.0 ? acc : 0.0;
-        if (fabs(acc) <= cfg->eps_geom * mag) g->amb |= AMB_RGB;   /* clamp at 0 may flip */
+        if (fabs(acc) <= cfg->eps_geom * mag) { g->amb |= AMB_RGB; g->rgb_amb |= 1u << ch; }   /* clamp at 0 may flip */
     }
     g->visible = keep;
     (void)opac;
@@ -541,6 +533,13 @@ typedef struct {
     int clamped;
 } contrib_t;
 
+/* Screen-space gradient terms that one pixel gives one Gaussian: dL/d(u, v), dL/d(conic a, b,
+   c) with b the off-diagonal entry as it enters the power once, dL/do, dL/d(r, g, b). */
+typedef struct {
+    int32_t idx;
+    double uv[2], conic[3], op, rgb[3];
+} pgrad_t;
+
 /* Evaluate the 2D Gaussian of g at pixel centre (px + 0.5, py + 0.5). */
 static double eval_power(const ogauss* g, double pxc, double pyc, double* dx, double* dy) {
     *dx = pxc - g->uv[0];
@@ -548,92 +547,155 @@ static double eval_power(const ogauss* g, double pxc, double pyc, double* dx, do
     return -0.5 * (g->conic[0] * (*dx) * (*dx) + g->conic[2] * (*dy) * (*dy)) - g->conic[1] * (*dx) * (*dy);
 }
 
-/* Bound on the error of the power that fp32 conic entries can cause (see ocfg.eps_conic): with
-   the conic's Cholesky factor L (conic = L L^T, l11 = sqrt(a), l21 = b / l11, l22^2 = c - l21^2)
-   the power is -(p^2 + q^2) / 2, p = l11 dx + l21 dy, q = l22 dy; relative errors eps in the
-   factor's entries move it by at most eps (|p| (|l11 dx| + |l21 dy|) + q^2), which exceeds
-   eps |power| when the two terms of p cancel (an elongated splat, far from its centre). */
+/* Margin of the power for an fp32 evaluation (ocfg.eps_power).  The plain definition's form
+   P = (a dx^2 + c dy^2)/2 + b dx dy (power = -P) is evaluated from fp32 values; with unit
+   roundoff u = 2^-24 and Q = (|a| dx^2 + |c| dy^2)/2 + |b dx dy| (the magnitude sum of its
+   terms), first-order error analysis gives |P_fp32 - P| <= eps Q with
+     conic entries a, c within 6u relative and b within 6u sqrt(a c)        12u Q
+       (|db dx dy| <= 6u sqrt(a) |dx| sqrt(c) |dy| <= 6u (a dx^2 + c dy^2)/2)
+     pixel offsets dx, dy within 2u relative, entering squared               4u Q
+     the evaluation: at most two products and two sums on any term's path   4u Q
+   eps = 20u = 1.19e-6.  Q equals |P| when the terms share a sign and exceeds it by the
+   conditioning of the form when they cancel (an elongated splat, far along its major axis),
+   which is where an fp32 evaluation may decide a threshold differently. */
 static double power_margin(const ogauss* g, double dx, double dy, const ocfg* cfg) {
-    if (!(g->conic[0] > 0.0)) return 0.0;
-    double l11 = sqrt(g->conic[0]);
-    double l21 = g->conic[1] / l11;
-    double l22s = g->conic[2] - l21 * l21;
-    double l22 = l22s > 0.0 ? sqrt(l22s) : 0.0;
-    double p = l11 * dx + l21 * dy, q = l22 * dy;
-    return cfg->eps_conic * (fabs(p) * (fabs(l11 * dx) + fabs(l21 * dy)) + q * q);
+    double Q = 0.5 * (fabs(g->conic[0]) * dx * dx + fabs(g->conic[2]) * dy * dy) + fabs(g->conic[1] * dx * dy);
+    return cfg->eps_power * Q;
 }
 
-static void mark(unsigned* gamb, int32_t i, unsigned bit) {
-    if (!gamb) return;
-#pragma omp atomic
-    gamb[i] |= bit;
+/* ------------------------------------------------------------------------- */
+/* Discrete decisions of a pixel's walk, and the walk with one of them taken   */
+/* the other way.  A decision is "near its threshold" when the FP64 quantity   */
+/* lies within the margin that an FP32 evaluation of the same definition may   */
+/* err by (ocfg eps_*); for each such decision the walk is also run with the   */
+/* decision flipped, so that a test can accept either outcome (and bound the   */
+/* effect of several flips by the sum of their effects) instead of skipping    */
+/* the pixel or the Gaussians it touches.                                      */
+/* ------------------------------------------------------------------------- */
+#define DEC_SKIP  1   /* alpha < 1/255 (App. C)                                                */
+#define DEC_CLAMP 2   /* alpha clamped at 0.99 (App. C): continuous value, not its derivative  */
+#define DEC_STOP  3   /* T (1 - alpha) < 1e-4: stop before this Gaussian (App. C)              */
+#define DEC_SWAP  4   /* equal or adjacent fp32 depth keys: the two Gaussians may swap places  */
+#define DEC_DROP  5   /* tile membership near its threshold (cull, rectangle): may be absent   */
+#define DEC_ADD   6   /* a Gaussian outside the tile's list whose membership is near threshold */
+
+typedef struct { int kind; int32_t g0, g1; } odec_t;
+
+/* Per-thread scratch of the pixel walks. */
+typedef struct {
+    int32_t* cand;   /* walk order */
+    contrib_t* rec;  /* blended Gaussians, main walk */
+    contrib_t* rec2; /* blended Gaussians, alternative walk */
+    pgrad_t* pg;     /* gradient terms, main walk */
+    pgrad_t* pg2;    /* gradient terms, alternative walk */
+    odec_t* dec;     /* decisions near their threshold */
+    int dec_cap;
+} oscratch;
+
+#define DEC_CAP 512
+
+static void scratch_alloc(oscratch* W, int64_t maxlen) {
+    size_t m = (size_t)maxlen + 2;
+    W->cand = (int32_t*)malloc(sizeof(int32_t) * m);
+    W->rec = (contrib_t*)malloc(sizeof(contrib_t) * m);
+    W->rec2 = (contrib_t*)malloc(sizeof(contrib_t) * m);
+    W->pg = (pgrad_t*)malloc(sizeof(pgrad_t) * m);
+    W->pg2 = (pgrad_t*)malloc(sizeof(pgrad_t) * m);
+    W->dec = (odec_t*)malloc(sizeof(odec_t) * DEC_CAP);
+    W->dec_cap = DEC_CAP;
 }
+
+static void scratch_free(oscratch* W) {
+    free(W->cand); free(W->rec); free(W->rec2); free(W->pg); free(W->pg2); free(W->dec);
+}
+
+/* Walk order of the definition: (fp32 depth bits, index) ascending. */
+static int walk_before(const oscene* S, int32_t x, int32_t y) {
+    uint32_t kx = depth_key(S->g[x].tcam[2]), ky = depth_key(S->g[y].tcam[2]);
+    return kx != ky ? kx < ky : x < y;
+}
+
+static int flips(const odec_t* f, int kind, int32_t gi) { return f && f->kind == kind && f->g0 == gi; }
 
 /*
- * Forward walk of one pixel over its tile's list (eq. front-to-back, App. C rules).
- * Returns the number of contributors written to rec (rec may be NULL).  Sets the pixel's
- * ambiguity flags and, if gamb is given, marks the Gaussians whose own decision is near a
- * threshold (see the AMB_* / PIX_* bits).
+ * One pixel's walk over its tile's list: eq. front-to-back with the App. C rules (skip
+ * alpha < 1/255 after the 0.99 clamp, stop before T (1 - alpha) < 1e-4), in (fp32 depth,
+ * index) order.  flip == NULL: the definition, and (if ndec is given) the decisions that lie
+ * near their threshold are listed in W->dec.  flip != NULL: the same walk with that one decision
+ * taken the other way.  Writes C (before the background), T, the 1-based list position and the
+ * index of the last blended Gaussian; returns the number of blended Gaussians (recorded in rec
+ * when given).
  */
-static int pixel_forward(const oscene* S, int t, int px, int py, const double* bg, double* out_rgb, double* out_T,
-                         int* out_last, int* out_last_id, unsigned* out_flags, contrib_t* rec, unsigned* gamb,
-                         int* out_first_amb) {
+static int pixel_walk(const oscene* S, int t, int px, int py, const odec_t* flip, oscratch* W, contrib_t* rec,
+                      double* C_out, double* T_out, int* last_pos, int32_t* last_id, int* ndec) {
     const ocfg* cfg = &S->cfg;
-    double pxc = px + 0.5, pyc = py + 0.5;
-    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
-    int last = 0, last_id = -1, nrec = 0;
-    int first_amb = -1;   /* blended Gaussians in front of the first decision near its threshold */
-    unsigned flags = 0;
-    int64_t a = S->tile_start[t], b = S->tile_start[t + 1];
-    uint32_t prev_key = 0;
-    int32_t prev_idx = -1;
+    const double pxc = px + 0.5, pyc = py + 0.5;
     const int tx = t % S->TX, ty = t / S->TX;
+    const int main_walk = flip == NULL;
+    const int want_dec = main_walk && ndec != NULL;
+    int nd = 0;
+#define ADD_DEC(k, a, b)                                                                           \
+    do {                                                                                           \
+        if (nd < W->dec_cap) { W->dec[nd].kind = (k); W->dec[nd].g0 = (a); W->dec[nd].g1 = (b); } \
+        ++nd;                                                                                      \
+    } while (0)
+
+    /* walk order: the tile's list, with the flipped membership or order applied */
+    int64_t a = S->tile_start[t], b = S->tile_start[t + 1];
+    int m = 0, added = 0;
     for (int64_t k = a; k < b; ++k) {
-        const int32_t gi = S->tile_list[k];
+        int32_t gi = S->tile_list[k];
+        if (flips(flip, DEC_DROP, gi)) continue;
+        if (flip && flip->kind == DEC_ADD && !added && walk_before(S, flip->g0, gi)) { W->cand[m++] = flip->g0; added = 1; }
+        W->cand[m++] = gi;
+    }
+    if (flip && flip->kind == DEC_ADD && !added) W->cand[m++] = flip->g0;
+    if (flip && flip->kind == DEC_SWAP) {
+        int p0 = -1, p1 = -1;
+        for (int w = 0; w < m; ++w) {
+            if (W->cand[w] == flip->g0) p0 = w;
+            if (W->cand[w] == flip->g1) p1 = w;
+        }
+        if (p0 >= 0 && p1 >= 0) { W->cand[p0] = flip->g1; W->cand[p1] = flip->g0; }
+    }
+
+    double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+    int nrec = 0, lp = 0;
+    int32_t lid = -1;
+    uint32_t prev_key = 0;
+    int32_t prev = -1;
+    for (int w = 0; w < m; ++w) {
+        const int32_t gi = W->cand[w];
         const ogauss* g = &S->g[gi];
         double dx, dy;
-        double power = eval_power(g, pxc, pyc, &dx, &dy);
-        double G = exp(power);
-        double oG = S->opac[gi] * G;
+        const double power = eval_power(g, pxc, pyc, &dx, &dy);
+        const double G = exp(power);
+        const double oG = S->opac[gi] * G;
         const double eps_a = cfg->eps_alpha + power_margin(g, dx, dy, cfg);   /* relative, on o G */
-        if (oG >= cfg->alpha_min * (1.0 - eps_a)) {
-            /* tile membership that an fp32 binning may decide differently */
-            if ((g->amb & (AMB_CULL | AMB_RECT)) && !in_rect(g->rect_in, tx, ty)) {
-                flags |= PIX_ANY;
-                if (T >= cfg->T_impact) flags |= PIX_DECISION;
-                if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);
+        if (want_dec) {
+            if (oG >= cfg->alpha_min * (1.0 - eps_a)) {
+                if ((g->amb & (AMB_CULL | AMB_RECT)) && !in_rect(g->rect_in, tx, ty)) ADD_DEC(DEC_DROP, gi, -1);
+                const uint32_t key = depth_key(g->tcam[2]);
+                if (prev >= 0 && key - prev_key <= 1u) ADD_DEC(DEC_SWAP, prev, gi);
+                prev_key = key;
+                prev = gi;
             }
-            /* equal or adjacent fp32 depth keys: the two may swap */
-            uint32_t key = depth_key(g->tcam[2]);
-            if (prev_idx >= 0 && key - prev_key <= 1u) {
-                flags |= PIX_ANY;
-                if (T >= cfg->T_impact) flags |= PIX_DECISION;
-                if (T >= cfg->T_grad) { mark(gamb, gi, AMB_PIXEL); mark(gamb, prev_idx, AMB_PIXEL); }
-            }
-            prev_key = key;
-            prev_idx = gi;
-        }
-        if (near_threshold(oG, cfg->alpha_min, eps_a)) {
-            flags |= PIX_ANY;
-            if (T >= cfg->T_impact) flags |= PIX_DECISION;
-            if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);
-        }
-        if (near_threshold(oG, cfg->alpha_max, eps_a)) {
-            flags |= PIX_CLAMP;
-            if (T >= cfg->T_grad) mark(gamb, gi, AMB_CLAMP);
+            if (near_threshold(oG, cfg->alpha_min, eps_a)) ADD_DEC(DEC_SKIP, gi, -1);
+            if (near_threshold(oG, cfg->alpha_max, eps_a)) ADD_DEC(DEC_CLAMP, gi, -1);
         }
         int clamped = oG > cfg->alpha_max;
-        double alpha = clamped ? cfg->alpha_max : oG;
-        if (first_amb < 0 && (flags & PIX_ANY)) first_amb = nrec;
-        if (alpha < cfg->alpha_min) continue;                   /* skip (App. C) */
-        double test_T = T * (1.0 - alpha);
+        if (flips(flip, DEC_CLAMP, gi)) clamped = !clamped;
+        const double alpha = clamped ? cfg->alpha_max : oG;
+        int skip = alpha < cfg->alpha_min;                      /* skip (App. C) */
+        if (flips(flip, DEC_SKIP, gi)) skip = !skip;
+        if (skip) continue;
+        const double test_T = T * (1.0 - alpha);
         /* (1 - alpha) is uncertain by alpha (eps_a - eps_alpha) relative to alpha */
-        if (near_threshold(test_T, cfg->T_min, cfg->eps_T + alpha / (1.0 - alpha) * (eps_a - cfg->eps_alpha))) {
-            flags |= PIX_DECISION | PIX_ANY;
-            if (T >= cfg->T_grad) mark(gamb, gi, AMB_PIXEL);   /* its inclusion may flip */
-            if (first_amb < 0) first_amb = nrec;
-        }
-        if (test_T < cfg->T_min) break;                         /* stop before exceeding 0.9999 */
+        if (want_dec && near_threshold(test_T, cfg->T_min, cfg->eps_T + alpha / (1.0 - alpha) * (eps_a - cfg->eps_alpha)))
+            ADD_DEC(DEC_STOP, gi, -1);
+        int stop = test_T < cfg->T_min;                         /* stop before exceeding 0.9999 */
+        if (flips(flip, DEC_STOP, gi)) stop = !stop;
+        if (stop) break;
         for (int ch = 0; ch < 3; ++ch) C[ch] += g->rgb[ch] * alpha * T;
         if (rec) {
             rec[nrec].idx = gi; rec[nrec].alpha = alpha; rec[nrec].G = G; rec[nrec].T = T;
@@ -641,28 +703,217 @@ static int pixel_forward(const oscene* S, int t, int px, int py, const double* b
         }
         nrec++;
         T = test_T;
-        last = (int)(k - a) + 1;
-        last_id = gi;
+        lp = w + 1;
+        lid = gi;
     }
-    /* Gaussians outside this tile's list that an fp32 binning may add to it. */
-    for (int64_t k = S->shadow_start[t]; k < S->shadow_start[t + 1]; ++k) {
-        const int32_t gi = S->shadow_list[k];
-        const ogauss* g = &S->g[gi];
-        double dx, dy;
-        double oG = S->opac[gi] * exp(eval_power(g, pxc, pyc, &dx, &dy));
-        if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha - power_margin(g, dx, dy, cfg))) {
-            flags |= PIX_DECISION | PIX_ANY;
-            mark(gamb, gi, AMB_PIXEL);
-            first_amb = 0;   /* its place in the order is unknown */
+    if (want_dec) {
+        /* Gaussians outside this tile's list whose membership is near its threshold */
+        for (int64_t k = S->shadow_start[t]; k < S->shadow_start[t + 1]; ++k) {
+            const int32_t gi = S->shadow_list[k];
+            const ogauss* g = &S->g[gi];
+            double dx, dy;
+            const double oG = S->opac[gi] * exp(eval_power(g, pxc, pyc, &dx, &dy));
+            if (oG >= cfg->alpha_min * (1.0 - cfg->eps_alpha - power_margin(g, dx, dy, cfg))) ADD_DEC(DEC_ADD, gi, -1);
         }
+        *ndec = nd;
     }
-    for (int ch = 0; ch < 3; ++ch) out_rgb[ch] = C[ch] + T * bg[ch];
-    *out_T = T;
-    *out_last = last;
-    if (out_last_id) *out_last_id = last_id;
-    *out_flags = flags;
-    if (out_first_amb) *out_first_amb = first_amb;
+#undef ADD_DEC
+    for (int ch = 0; ch < 3; ++ch) C_out[ch] = C[ch];
+    *T_out = T;
+    if (last_pos) *last_pos = main_walk ? lp : 0;
+    if (last_id) *last_id = lid;
     return nrec;
+}
+
+/*
+ * Backward walk of one pixel (Sec. 6): back to front over the blended Gaussians, with the
+ * colour behind each one (normalised by the transmittance in front of it) carried from the
+ * background.  pg[k] receives the screen-space gradient terms of rec[k].  With a gradient limit
+ * N (Limited-BW, Sec. 7.3) only the N front-most blended Gaussians get terms; the colour behind
+ * still takes in every one.
+ */
+static void pixel_backward(const oscene* S, const contrib_t* rec, int nrec, const double* dC, const double* bg,
+                           pgrad_t* pg) {
+    double Rb[3] = {bg[0], bg[1], bg[2]};
+    for (int k = nrec - 1; k >= 0; --k) {
+        const contrib_t* c = &rec[k];
+        const ogauss* g = &S->g[c->idx];
+        pgrad_t* p = &pg[k];
+        memset(p, 0, sizeof(*p));
+        p->idx = c->idx;
+        const int grad = S->cfg.grad_limit <= 0 || k < S->cfg.grad_limit;
+        double dL_dalpha = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            if (grad) p->rgb[ch] = c->T * c->alpha * dC[ch];
+            dL_dalpha += c->T * (g->rgb[ch] - Rb[ch]) * dC[ch];
+            Rb[ch] = c->alpha * g->rgb[ch] + (1.0 - c->alpha) * Rb[ch];
+        }
+        if (!grad || c->clamped) continue;   /* derivative of min(o G, 0.99) is 0 when clamped */
+        const double o = S->opac[c->idx];
+        p->op = c->G * dL_dalpha;
+        const double dL_dpower = o * c->G * dL_dalpha;
+        p->conic[0] = -0.5 * c->dx * c->dx * dL_dpower;
+        p->conic[1] = -c->dx * c->dy * dL_dpower;
+        p->conic[2] = -0.5 * c->dy * c->dy * dL_dpower;
+        /* d = p - mean: d(power)/du = a dx + b dy, d(power)/dv = b dx + c dy */
+        p->uv[0] = (g->conic[0] * c->dx + g->conic[1] * c->dy) * dL_dpower;
+        p->uv[1] = (g->conic[1] * c->dx + g->conic[2] * c->dy) * dL_dpower;
+    }
+}
+
+/* dL/dSigma' from dL/dconic, conic = Sigma'^-1: dL/dSigma' = -Q G_Q Q with G_Q the symmetric
+   gradient of Q (the off-diagonal b enters the power once, as the symmetric entry); returns the
+   full-matrix entries (00, 01, 11). */
+static void conic_to_cov_grad(const ogauss* g, const double* dconic, double* H4) {
+    double Q[4] = {g->conic[0], g->conic[1], g->conic[1], g->conic[2]};
+    double GQ[4] = {dconic[0], 0.5 * dconic[1], 0.5 * dconic[1], dconic[2]};
+    double QG[4];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) QG[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) H4[2 * r + c] = -(QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);
+}
+
+/*
+ * Chain rule of App. A for Gaussian i, linear in the screen-space gradients: dL/d(u, v),
+ * dL/dconic and dL/drgb (the latter already masked by the colour clamp) to dL/d(mu, s, q, SH).
+ * dsh receives the first D x 3 coefficients.
+ */
+static void gauss_chain_g(const oscene* S, size_t i, const ogauss* g, const double* d_uv, const double* d_conic,
+                          const double* drgb, double* dmu, double* ds, double* dq, double* dsh) {
+    const double* s = S->scales + 3 * i;
+    const int D = (S->deg + 1) * (S->deg + 1);
+    double H[4];
+    conic_to_cov_grad(g, d_conic, H);
+
+    /* App. A: dSigma'/dSigma_ij = [[U1i U1j, U1i U2j], [U1j U2i, U2i U2j]] with U = J W. */
+    double GS[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double* U = g->U;
+            GS[3 * a + b] = H[0] * U[a] * U[b] + H[1] * U[a] * U[3 + b] + H[2] * U[b] * U[3 + a] + H[3] * U[3 + a] * U[3 + b];
+        }
+    /* Sigma = M M^T: dL/dM = (G + G^T) M. */
+    double GSs[9], dM[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) GSs[3 * a + b] = GS[3 * a + b] + GS[3 * b + a];
+    matmul33(GSs, g->M, dM);
+    /* dM_ij/ds_k = R_ik if j == k. */
+    for (int k = 0; k < 3; ++k) ds[k] = dM[k] * g->R[k] + dM[3 + k] * g->R[3 + k] + dM[6 + k] * g->R[6 + k];
+    /* dM/dq from App. A (q normalised). */
+    double qr = g->qn[0], qi = g->qn[1], qj = g->qn[2], qk = g->qn[3];
+    double sx = s[0], sy = s[1], sz = s[2];
+    double dMr[9] = {0, -sy * qk, sz * qj, sx * qk, 0, -sz * qi, -sx * qj, sy * qi, 0};
+    double dMi[9] = {0, sy * qj, sz * qk, sx * qj, -2 * sy * qi, -sz * qr, sx * qk, sy * qr, -2 * sz * qi};
+    double dMj[9] = {-2 * sx * qj, sy * qi, sz * qr, sx * qi, 0, sz * qk, -sx * qr, sy * qk, -2 * sz * qj};
+    double dMk[9] = {-2 * sx * qk, -sy * qr, sz * qi, sx * qr, -2 * sy * qk, sz * qj, sx * qi, sy * qj, 0};
+    double dqn[4] = {0, 0, 0, 0};
+    for (int e = 0; e < 9; ++e) {
+        dqn[0] += 2.0 * dMr[e] * dM[e];
+        dqn[1] += 2.0 * dMi[e] * dM[e];
+        dqn[2] += 2.0 * dMj[e] * dM[e];
+        dqn[3] += 2.0 * dMk[e] * dM[e];
+    }
+    /* q_hat = q / |q|: dL/dq = (dL/dq_hat - q_hat (q_hat . dL/dq_hat)) / |q|. */
+    double proj = dqn[0] * qr + dqn[1] * qi + dqn[2] * qj + dqn[3] * qk;
+    for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - g->qn[k] * proj) / g->qnorm;
+
+    /* Jacobian and screen position depend on the camera-space mean t. */
+    /* Sigma'_raw = U Sigma U^T: dL/dU = (H + H^T) U Sigma; U = J W: dL/dJ = dL/dU W^T. */
+    double Hs[4] = {2 * H[0], H[1] + H[2], H[1] + H[2], 2 * H[3]};
+    double USg[6];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c)
+            USg[3 * r + c] = g->U[3 * r] * g->Sigma[c] + g->U[3 * r + 1] * g->Sigma[3 + c] + g->U[3 * r + 2] * g->Sigma[6 + c];
+    double dU[6], dJ[6];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) dU[3 * r + c] = Hs[2 * r] * USg[c] + Hs[2 * r + 1] * USg[3 + c];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c)
+            dJ[3 * r + c] = dU[3 * r] * S->cam.W[3 * c] + dU[3 * r + 1] * S->cam.W[3 * c + 1] + dU[3 * r + 2] * S->cam.W[3 * c + 2];
+    double tx = g->tcam[0], ty = g->tcam[1], tz = g->tcam[2];
+    double fx = S->cam.fx, fy = S->cam.fy;
+    double du = d_uv[0], dv = d_uv[1];
+    double dt[3];
+    dt[0] = du * fx / tz + dJ[2] * (-fx / (tz * tz));
+    dt[1] = dv * fy / tz + dJ[5] * (-fy / (tz * tz));
+    dt[2] = du * (-fx * tx / (tz * tz)) + dv * (-fy * ty / (tz * tz)) + dJ[0] * (-fx / (tz * tz)) +
+            dJ[2] * (2.0 * fx * tx / (tz * tz * tz)) + dJ[4] * (-fy / (tz * tz)) + dJ[5] * (2.0 * fy * ty / (tz * tz * tz));
+    for (int k = 0; k < 3; ++k) dmu[k] = S->cam.W[k] * dt[0] + S->cam.W[3 + k] * dt[1] + S->cam.W[6 + k] * dt[2];
+
+    /* Colour: rgb = max(0, sum_k sh_k Y_k(d_hat)); drgb is already zero on clamped channels. */
+    double dd[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) {
+        double w = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            dsh[3 * k + ch] = g->Y[k] * drgb[ch];
+            w += S->sh[((size_t)i * S->sh_stride + k) * 3 + ch] * drgb[ch];
+        }
+        for (int r = 0; r < 3; ++r) dd[r] += w * g->dY[3 * k + r];
+    }
+    double dproj = dd[0] * g->dhat[0] + dd[1] * g->dhat[1] + dd[2] * g->dhat[2];
+    for (int r = 0; r < 3; ++r) dmu[r] += (dd[r] - g->dhat[r] * dproj) / g->dnorm;
+}
+
+static void gauss_chain(const oscene* S, size_t i, const double* d_uv, const double* d_conic, const double* drgb,
+                        double* dmu, double* ds, double* dq, double* dsh) {
+    gauss_chain_g(S, i, &S->g[i], d_uv, d_conic, drgb, dmu, ds, dq, dsh);
+}
+
+/*
+ * Conditioning of the chain rule in fp32 (test allowance; see orc_render_backward): the
+ * first-order change of dL/d(mu, s, q, SH) when the quantities every fp32 implementation of
+ * App. A must form from the fp32 inputs -- the rotation R(q_hat) (with M = R S), the projection
+ * U = J W, the camera-space mean t and the view direction d_hat (with its SH basis) -- carry
+ * relative rounding errors of COND_ROUNDINGS units in the last place.  Per quantity, two
+ * perturbations of all its entries with pseudo-random signs (relative step COND_STEP) give a
+ * finite-difference sensitivity; the larger of the two, summed over the quantities and times
+ * COND_ROUNDINGS u, is added to out[] entry by entry.  The screen-space sums are held fixed:
+ * their own conditioning depends on the frame an implementation accumulates them in.
+ */
+#define COND_ROUNDINGS 4.0
+#define COND_STEP 9.5367431640625e-07   /* 2^-20 */
+#define COND_U 5.9604644775390625e-08   /* 2^-24, unit roundoff of IEEE fp32 */
+
+static double sign_hash(size_t i, int a, int t, int j) {
+    uint64_t x = (uint64_t)i * 0x9E3779B97F4A7C15ull ^ (uint64_t)(a * 131 + t * 17 + j + 1) * 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 31; x *= 0x94D049BB133111EBull; x ^= x >> 29;
+    return (x & 1) ? 1.0 : -1.0;
+}
+
+static void chain_conditioning(const oscene* S, size_t i, const double* d_uv, const double* d_conic,
+                               const double* drgb, double* out /* [3 + 3 + 4 + 3D] */) {
+    const ogauss* g = &S->g[i];
+    const int D = (S->deg + 1) * (S->deg + 1), NY = 10 + 3 * D;
+    double y0[58], y[58], sens[58], tot[58];
+    gauss_chain_g(S, i, g, d_uv, d_conic, drgb, y0, y0 + 3, y0 + 6, y0 + 10);
+    for (int e = 0; e < NY; ++e) tot[e] = 0.0;
+    const double* s = S->scales + 3 * i;
+    for (int a = 0; a < 4; ++a) {
+        for (int e = 0; e < NY; ++e) sens[e] = 0.0;
+        for (int t = 0; t < 2; ++t) {
+            ogauss gp = *g;
+            if (a == 0) {          /* R, and M = R S formed from it */
+                for (int j = 0; j < 9; ++j) gp.R[j] *= 1.0 + COND_STEP * sign_hash(i, a, t, j);
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) gp.M[3 * r + c] = gp.R[3 * r + c] * s[c];
+            } else if (a == 1) {   /* U = J W */
+                for (int j = 0; j < 6; ++j) gp.U[j] *= 1.0 + COND_STEP * sign_hash(i, a, t, j);
+            } else if (a == 2) {   /* camera-space mean */
+                for (int j = 0; j < 3; ++j) gp.tcam[j] *= 1.0 + COND_STEP * sign_hash(i, a, t, j);
+            } else {               /* view direction and its SH basis */
+                for (int j = 0; j < 3; ++j) gp.dhat[j] *= 1.0 + COND_STEP * sign_hash(i, a, t, j);
+                sh_basis(S->deg, gp.dhat, gp.Y, gp.dY);
+            }
+            gauss_chain_g(S, i, &gp, d_uv, d_conic, drgb, y, y + 3, y + 6, y + 10);
+            for (int e = 0; e < NY; ++e) {
+                const double d = fabs(y[e] - y0[e]) / COND_STEP;
+                if (d > sens[e]) sens[e] = d;
+            }
+        }
+        for (int e = 0; e < NY; ++e) tot[e] += sens[e];
+    }
+    for (int e = 0; e < NY; ++e) out[e] = COND_ROUNDINGS * COND_U * tot[e];
 }
 
 static void scene_init(oscene* S, long n, const double* means, const double* scales, const double* quats,
@@ -672,6 +923,15 @@ static void scene_init(oscene* S, long n, const double* means, const double* sca
     S->means = means; S->scales = scales; S->quats = quats; S->opac = opac; S->sh = sh;
     read_cam(cam, &S->cam);
     read_cfg(cfg, &S->cfg);
+}
+
+static int64_t max_list(const oscene* S) {
+    int64_t m = 1;
+    for (int t = 0; t < S->TX * S->TY; ++t) {
+        int64_t l = S->tile_start[t + 1] - S->tile_start[t];
+        if (l > m) m = l;
+    }
+    return m;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -700,12 +960,19 @@ void orc_preprocess(long n, const double* means, const double* scales, const dou
 /* ------------------------------------------------------------------------- */
 /* Exported: forward render (Algorithm 2, eq. front-to-back).                  */
 /* tile_mask (may be NULL) selects the tiles to render; other pixels are left   */
-/* untouched.  Images are planar [3, H, W].                                     */
+/* untouched.  Images are planar [3, H, W].  out_pix_dec[p] has bit (kind - 1)  */
+/* set for every kind of decision near its threshold at pixel p.  For each such */
+/* decision one alternative is written (up to alt_cap): the pixel, the decision */
+/* (kind, g0, g1), and the pixel's colour, T and last Gaussian with that        */
+/* decision flipped.  counts[0] = alternatives found, counts[1] = decisions     */
+/* beyond the per-pixel list capacity (not flipped; a test must see 0).         */
 /* ------------------------------------------------------------------------- */
 void orc_render_forward(long n, const double* means, const double* scales, const double* quats, const double* opac,
                         const double* sh, int deg, int sh_stride, const double* cam, const double* cfg,
                         const double* bg, const uint8_t* tile_mask, double* out_img, double* out_T, int32_t* out_last,
-                        int32_t* out_last_id, uint8_t* out_pix_amb, uint32_t* out_gauss_amb) {
+                        int32_t* out_last_id, uint8_t* out_pix_dec, uint32_t* out_gauss_amb, long alt_cap,
+                        int64_t* alt_pix, int32_t* alt_dec, double* alt_img, double* alt_T, int32_t* alt_last_id,
+                        long* counts) {
     oscene S;
     scene_init(&S, n, means, scales, quats, opac, sh, deg, sh_stride, cam, cfg);
     scene_build(&S, tile_mask);
@@ -713,35 +980,125 @@ void orc_render_forward(long n, const double* means, const double* scales, const
     size_t P = (size_t)W * H;
     if (out_gauss_amb)
         for (size_t i = 0; i < S.n; ++i) out_gauss_amb[i] = S.g[i].amb;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int t = 0; t < T; ++t) {
-        if (tile_mask && !tile_mask[t]) continue;
-        int tx = t % S.TX, ty = t / S.TX;
-        for (int ly = 0; ly < S.cfg.tile_h; ++ly)
-            for (int lx = 0; lx < S.cfg.tile_w; ++lx) {
-                int px = tx * S.cfg.tile_w + lx, py = ty * S.cfg.tile_h + ly;
-                if (px >= W || py >= H) continue;
-                double rgb[3], Tf; int last, last_id; unsigned flags;
-                pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, &last_id, &flags, NULL, out_gauss_amb, NULL);
-                size_t p = (size_t)py * W + px;
-                if (out_last_id) out_last_id[p] = last_id;
-                for (int ch = 0; ch < 3; ++ch) out_img[ch * P + p] = rgb[ch];
-                out_T[p] = Tf;
-                out_last[p] = last;
-                if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
-            }
+    const int64_t maxlen = max_list(&S);
+    long nalt = 0, overflow = 0;
+#pragma omp parallel
+    {
+        oscratch Wk;
+        scratch_alloc(&Wk, maxlen);
+#pragma omp for schedule(dynamic, 1) reduction(+ : overflow)
+        for (int t = 0; t < T; ++t) {
+            if (tile_mask && !tile_mask[t]) continue;
+            int tx = t % S.TX, ty = t / S.TX;
+            for (int ly = 0; ly < S.cfg.tile_h; ++ly)
+                for (int lx = 0; lx < S.cfg.tile_w; ++lx) {
+                    int px = tx * S.cfg.tile_w + lx, py = ty * S.cfg.tile_h + ly;
+                    if (px >= W || py >= H) continue;
+                    double C[3], Tf;
+                    int last, ndec;
+                    int32_t last_id;
+                    pixel_walk(&S, t, px, py, NULL, &Wk, NULL, C, &Tf, &last, &last_id, &ndec);
+                    size_t p = (size_t)py * W + px;
+                    if (out_last_id) out_last_id[p] = last_id;
+                    for (int ch = 0; ch < 3; ++ch) out_img[ch * P + p] = C[ch] + Tf * bg[ch];
+                    out_T[p] = Tf;
+                    out_last[p] = last;
+                    if (ndec > Wk.dec_cap) { overflow += ndec - Wk.dec_cap; ndec = Wk.dec_cap; }
+                    uint8_t bits = 0;
+                    for (int d = 0; d < ndec; ++d) {
+                        const odec_t dec = Wk.dec[d];
+                        bits |= (uint8_t)(1u << (dec.kind - 1));
+                        double C2[3], T2;
+                        int32_t lid2;
+                        pixel_walk(&S, t, px, py, &dec, &Wk, NULL, C2, &T2, NULL, &lid2, NULL);
+                        long slot;
+#pragma omp atomic capture
+                        slot = nalt++;
+                        if (slot < alt_cap) {
+                            alt_pix[slot] = (int64_t)p;
+                            alt_dec[3 * slot] = dec.kind; alt_dec[3 * slot + 1] = dec.g0; alt_dec[3 * slot + 2] = dec.g1;
+                            for (int ch = 0; ch < 3; ++ch) alt_img[3 * slot + ch] = C2[ch] + T2 * bg[ch];
+                            alt_T[slot] = T2;
+                            alt_last_id[slot] = lid2;
+                        }
+                    }
+                    if (out_pix_dec) out_pix_dec[p] = bits;
+                }
+        }
+        scratch_free(&Wk);
     }
+    counts[0] = nalt;
+    counts[1] = overflow;
     scene_free(&S);
 }
 
 /* ------------------------------------------------------------------------- */
-/* Exported: backward pass.  Per pixel: forward walk keeping every T_i, then the  */
-/* reverse walk (Sec. 6) accumulates dL/d(mean2D, conic, opacity, colour); per   */
-/* Gaussian: chain rule of App. A down to (mu, s, q, o, SH).                      */
+/* Exported: backward pass.  Per pixel: the forward walk keeping every T_i,   */
+/* then the reverse walk (Sec. 6) gives dL/d(mean2D, conic, opacity, colour)   */
+/* of each blended Gaussian; per Gaussian: chain rule of App. A down to        */
+/* (mu, s, q, o, SH).                                                          */
+/* allow_screen [n, 9] (dL/du, dL/dv, dL/dSigma' 00, 01, 11, dL/do, dL/drgb)   */
+/* and allow_* (may all be NULL): for every decision near its threshold, the   */
+/* pixel's gradient terms are recomputed with the decision flipped, and the    */
+/* magnitude of the change they make to each Gaussian's gradients (screen      */
+/* space, and through the chain rule the inputs) is added up; a colour channel */
+/* near the 0 clamp adds the magnitude of its own chain-rule terms.  A test    */
+/* can accept |g - g*| <= tolerance + allowance for every Gaussian.            */
+/* cond_* (may be NULL): per gradient entry, the fp32 conditioning allowance  */
+/* of the chain rule (chain_conditioning).                                     */
+/* counts[0] = decisions flipped, counts[1] = decisions beyond the per-pixel   */
+/* list capacity.                                                              */
 /* ------------------------------------------------------------------------- */
 static void atomic_add(double* p, double v) {
 #pragma omp atomic
     *p += v;
+}
+
+typedef struct {
+    double *screen, *means, *scales, *quats, *opac, *sh;
+} oallow;
+
+/* |change| of one Gaussian's gradients between two pixel walks: screen space and chained. */
+static void allow_add(const oscene* S, const oallow* A, const pgrad_t* d) {
+    const size_t i = (size_t)d->idx;
+    const ogauss* g = &S->g[i];
+    double H[4];
+    conic_to_cov_grad(g, d->conic, H);
+    double sc[9] = {d->uv[0], d->uv[1], H[0], H[1], H[3], d->op, d->rgb[0], d->rgb[1], d->rgb[2]};
+    for (int k = 0; k < 9; ++k) if (sc[k] != 0.0) atomic_add(&A->screen[9 * i + k], fabs(sc[k]));
+    if (d->op != 0.0) atomic_add(&A->opac[i], fabs(d->op));
+    if (!g->valid) return;
+    double drgb[3], dmu[3], ds[3], dq[4], dsh[48];
+    for (int ch = 0; ch < 3; ++ch) drgb[ch] = g->rgb_raw[ch] > 0.0 ? d->rgb[ch] : 0.0;
+    gauss_chain(S, i, d->uv, d->conic, drgb, dmu, ds, dq, dsh);
+    for (int k = 0; k < 3; ++k) { atomic_add(&A->means[3 * i + k], fabs(dmu[k])); atomic_add(&A->scales[3 * i + k], fabs(ds[k])); }
+    for (int k = 0; k < 4; ++k) atomic_add(&A->quats[4 * i + k], fabs(dq[k]));
+    const int D = (S->deg + 1) * (S->deg + 1);
+    for (int k = 0; k < 3 * D; ++k) if (dsh[k] != 0.0) atomic_add(&A->sh[(size_t)i * S->sh_stride * 3 + k], fabs(dsh[k]));
+}
+
+static int cmp_pg(const void* a, const void* b) {
+    int32_t x = ((const pgrad_t*)a)->idx, y = ((const pgrad_t*)b)->idx;
+    return (x > y) - (x < y);
+}
+
+/* Add |alt - main| per Gaussian (both lists sorted by index). */
+static void allow_delta(const oscene* S, const oallow* A, const pgrad_t* p1, int n1, const pgrad_t* p2, int n2) {
+    int a = 0, b = 0;
+    while (a < n1 || b < n2) {
+        pgrad_t d;
+        memset(&d, 0, sizeof(d));
+        int take1 = b >= n2 || (a < n1 && p1[a].idx <= p2[b].idx);
+        int take2 = a >= n1 || (b < n2 && p2[b].idx <= p1[a].idx);
+        d.idx = take1 ? p1[a].idx : p2[b].idx;
+        for (int k = 0; k < 2; ++k) d.uv[k] = (take2 ? p2[b].uv[k] : 0.0) - (take1 ? p1[a].uv[k] : 0.0);
+        for (int k = 0; k < 3; ++k) d.conic[k] = (take2 ? p2[b].conic[k] : 0.0) - (take1 ? p1[a].conic[k] : 0.0);
+        for (int k = 0; k < 3; ++k) d.rgb[k] = (take2 ? p2[b].rgb[k] : 0.0) - (take1 ? p1[a].rgb[k] : 0.0);
+        d.op = (take2 ? p2[b].op : 0.0) - (take1 ? p1[a].op : 0.0);
+        allow_add(S, A, &d);
+        if (take1) ++a;
+        if (take2) ++b;
+    }
 }
 
 void orc_render_backward(long n, const double* means, const double* scales, const double* quats, const double* opac,
@@ -749,7 +1106,10 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                          const double* bg, const uint8_t* tile_mask, const double* dL_dimg,
                          double* d_means, double* d_scales, double* d_quats, double* d_opac, double* d_sh,
                          double* d_uv, double* d_conic, double* d_rgb, double* d_cov2d,
-                         uint8_t* out_pix_amb, uint32_t* out_gauss_amb) {
+                         uint8_t* out_pix_dec, uint32_t* out_gauss_amb,
+                         double* allow_screen, double* allow_means, double* allow_scales, double* allow_quats,
+                         double* allow_opac, double* allow_sh, double* cond_means, double* cond_scales,
+                         double* cond_quats, double* cond_sh, long* counts) {
     oscene S;
     scene_init(&S, n, means, scales, quats, opac, sh, deg, sh_stride, cam, cfg);
     scene_build(&S, tile_mask);
@@ -760,15 +1120,32 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
     memset(d_conic, 0, sizeof(double) * 3 * S.n);
     memset(d_rgb, 0, sizeof(double) * 3 * S.n);
     memset(d_opac, 0, sizeof(double) * S.n);
+    oallow A = {allow_screen, allow_means, allow_scales, allow_quats, allow_opac, allow_sh};
+    const int want_allow = allow_screen != NULL;
+    if (want_allow) {
+        memset(allow_screen, 0, sizeof(double) * 9 * S.n);
+        memset(allow_means, 0, sizeof(double) * 3 * S.n);
+        memset(allow_scales, 0, sizeof(double) * 3 * S.n);
+        memset(allow_quats, 0, sizeof(double) * 4 * S.n);
+        memset(allow_opac, 0, sizeof(double) * S.n);
+        memset(allow_sh, 0, sizeof(double) * 3 * (size_t)sh_stride * S.n);
+    }
+    if (cond_means) {
+        memset(cond_means, 0, sizeof(double) * 3 * S.n);
+        memset(cond_scales, 0, sizeof(double) * 3 * S.n);
+        memset(cond_quats, 0, sizeof(double) * 4 * S.n);
+        memset(cond_sh, 0, sizeof(double) * 3 * (size_t)sh_stride * S.n);
+    }
     if (out_gauss_amb)
         for (size_t i = 0; i < S.n; ++i) out_gauss_amb[i] = S.g[i].amb;
-    int64_t maxlen = 1;
-    for (int t = 0; t < T; ++t) if (S.tile_start[t + 1] - S.tile_start[t] > maxlen) maxlen = S.tile_start[t + 1] - S.tile_start[t];
+    const int64_t maxlen = max_list(&S);
+    long nflip = 0, overflow = 0;
 
 #pragma omp parallel
     {
-        contrib_t* rec = (contrib_t*)malloc(sizeof(contrib_t) * (size_t)maxlen);
-#pragma omp for schedule(dynamic, 1)
+        oscratch Wk;
+        scratch_alloc(&Wk, maxlen);
+#pragma omp for schedule(dynamic, 1) reduction(+ : nflip, overflow)
         for (int t = 0; t < T; ++t) {
             if (tile_mask && !tile_mask[t]) continue;
             int tx = t % S.TX, ty = t / S.TX;
@@ -777,49 +1154,42 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
                     int px = tx * S.cfg.tile_w + lx, py = ty * S.cfg.tile_h + ly;
                     if (px >= W || py >= H) continue;
                     size_t p = (size_t)py * W + px;
-                    double rgb[3], Tf; int last; unsigned flags;
-                    int first_amb;
-                    int nrec = pixel_forward(&S, t, px, py, bg, rgb, &Tf, &last, NULL, &flags, rec, out_gauss_amb,
-                                             &first_amb);
-                    if (out_pix_amb) out_pix_amb[p] = (uint8_t)flags;
-                    /* with a gradient limit N, a decision near its threshold among the first N
-                       blended Gaussians (order, skip, stop or membership) can move the limit by one
-                       place: the Gaussians at front ranks N-1 and N may swap roles */
-                    if (S.cfg.grad_limit > 0 && first_amb >= 0 && first_amb < S.cfg.grad_limit && out_gauss_amb)
-                        for (int k = S.cfg.grad_limit - 1; k <= S.cfg.grad_limit && k < nrec; ++k)
-                            if (k >= 0) mark(out_gauss_amb, rec[k].idx, AMB_PIXEL);
-                    double dC[3] = {dL_dimg[p], dL_dimg[P + p], dL_dimg[2 * P + p]};
-                    /* R = colour accumulated behind the current Gaussian, normalised by the
-                       transmittance in front of it; starts with the background. */
-                    double Rb[3] = {bg[0], bg[1], bg[2]};
-                    for (int k = nrec - 1; k >= 0; --k) {
-                        const contrib_t* c = &rec[k];
-                        const ogauss* g = &S.g[c->idx];
-                        /* rec[k] is the k-th blended Gaussian from the front; with a gradient limit
-                           N only k < N receive gradients, while R still takes in every one */
-                        const int grad = S.cfg.grad_limit <= 0 || k < S.cfg.grad_limit;
-                        double dL_dalpha = 0.0;
-                        for (int ch = 0; ch < 3; ++ch) {
-                            if (grad) atomic_add(&d_rgb[3 * c->idx + ch], c->T * c->alpha * dC[ch]);
-                            dL_dalpha += c->T * (g->rgb[ch] - Rb[ch]) * dC[ch];
-                            Rb[ch] = c->alpha * g->rgb[ch] + (1.0 - c->alpha) * Rb[ch];
+                    double C[3], Tf;
+                    int last, ndec;
+                    int32_t last_id;
+                    int nrec = pixel_walk(&S, t, px, py, NULL, &Wk, Wk.rec, C, &Tf, &last, &last_id, &ndec);
+                    if (ndec > Wk.dec_cap) { overflow += ndec - Wk.dec_cap; ndec = Wk.dec_cap; }
+                    const double dC[3] = {dL_dimg[p], dL_dimg[P + p], dL_dimg[2 * P + p]};
+                    pixel_backward(&S, Wk.rec, nrec, dC, bg, Wk.pg);
+                    for (int k = 0; k < nrec; ++k) {
+                        const pgrad_t* q = &Wk.pg[k];
+                        const int32_t i = q->idx;
+                        for (int c = 0; c < 3; ++c) if (q->rgb[c] != 0.0) atomic_add(&d_rgb[3 * i + c], q->rgb[c]);
+                        if (q->op != 0.0) {
+                            atomic_add(&d_opac[i], q->op);
+                            for (int c = 0; c < 3; ++c) atomic_add(&d_conic[3 * i + c], q->conic[c]);
+                            for (int c = 0; c < 2; ++c) atomic_add(&d_uv[2 * i + c], q->uv[c]);
                         }
-                        if (!grad) continue;
-                        if (c->clamped) continue;   /* derivative of min(o G, 0.99) is 0 there */
-                        double o = S.opac[c->idx];
-                        atomic_add(&d_opac[c->idx], c->G * dL_dalpha);
-                        double dL_dpower = o * c->G * dL_dalpha;
-                        atomic_add(&d_conic[3 * c->idx + 0], -0.5 * c->dx * c->dx * dL_dpower);
-                        atomic_add(&d_conic[3 * c->idx + 1], -c->dx * c->dy * dL_dpower);
-                        atomic_add(&d_conic[3 * c->idx + 2], -0.5 * c->dy * c->dy * dL_dpower);
-                        /* d = p - mean: d(power)/du = a dx + b dy, d(power)/dv = b dx + c dy */
-                        atomic_add(&d_uv[2 * c->idx + 0], (g->conic[0] * c->dx + g->conic[1] * c->dy) * dL_dpower);
-                        atomic_add(&d_uv[2 * c->idx + 1], (g->conic[1] * c->dx + g->conic[2] * c->dy) * dL_dpower);
+                    }
+                    uint8_t bits = 0;
+                    for (int d = 0; d < ndec; ++d) bits |= (uint8_t)(1u << (Wk.dec[d].kind - 1));
+                    if (out_pix_dec) out_pix_dec[p] = bits;
+                    if (!want_allow || ndec == 0) continue;
+                    qsort(Wk.pg, (size_t)nrec, sizeof(pgrad_t), cmp_pg);
+                    for (int d = 0; d < ndec; ++d) {
+                        double C2[3], T2;
+                        const odec_t dec = Wk.dec[d];
+                        int n2 = pixel_walk(&S, t, px, py, &dec, &Wk, Wk.rec2, C2, &T2, NULL, NULL, NULL);
+                        pixel_backward(&S, Wk.rec2, n2, dC, bg, Wk.pg2);
+                        qsort(Wk.pg2, (size_t)n2, sizeof(pgrad_t), cmp_pg);
+                        allow_delta(&S, &A, Wk.pg, nrec, Wk.pg2, n2);
+                        ++nflip;
                     }
                 }
         }
-        free(rec);
+        scratch_free(&Wk);
     }
+    if (counts) { counts[0] = nflip; counts[1] = overflow; }
 
     /* Per Gaussian: chain rule of App. A. */
 #pragma omp parallel for schedule(static)
@@ -834,90 +1204,32 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
         for (int k = 0; k < sh_stride * 3; ++k) dsh[k] = 0.0;
         d_cov2d[3 * i] = d_cov2d[3 * i + 1] = d_cov2d[3 * i + 2] = 0.0;
         if (!g->visible) { d_opac[i] = 0.0; continue; }
-        const double* s = scales + 3 * i;
-
-        /* conic = Sigma'^{-1}: dL/dSigma' = -Q G_Q Q with G_Q the symmetric gradient of Q
-           (the off-diagonal b enters the power once, as the symmetric entry). */
-        double Q[4] = {g->conic[0], g->conic[1], g->conic[1], g->conic[2]};
-        double GQ[4] = {d_conic[3 * i], 0.5 * d_conic[3 * i + 1], 0.5 * d_conic[3 * i + 1], d_conic[3 * i + 2]};
-        double QG[4], H[4];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 2; ++c) QG[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 2; ++c) H[2 * r + c] = -(QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);
-        d_cov2d[3 * i + 0] = H[0];
-        d_cov2d[3 * i + 1] = H[1];
-        d_cov2d[3 * i + 2] = H[3];
-
-        /* App. A: dSigma'/dSigma_ij = [[U1i U1j, U1i U2j], [U1j U2i, U2i U2j]] with U = J W. */
-        double GS[9];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                const double* U = g->U;
-                GS[3 * a + b] = H[0] * U[a] * U[b] + H[1] * U[a] * U[3 + b] + H[2] * U[b] * U[3 + a] + H[3] * U[3 + a] * U[3 + b];
-            }
-        /* Sigma = M M^T: dL/dM = (G + G^T) M. */
-        double GSs[9], dM[9];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) GSs[3 * a + b] = GS[3 * a + b] + GS[3 * b + a];
-        matmul33(GSs, g->M, dM);
-        /* dM_ij/ds_k = R_ik if j == k. */
-        for (int k = 0; k < 3; ++k) ds[k] = dM[k] * g->R[k] + dM[3 + k] * g->R[3 + k] + dM[6 + k] * g->R[6 + k];
-        /* dM/dq from App. A (q normalised). */
-        double qr = g->qn[0], qi = g->qn[1], qj = g->qn[2], qk = g->qn[3];
-        double sx = s[0], sy = s[1], sz = s[2];
-        double dMr[9] = {0, -sy * qk, sz * qj, sx * qk, 0, -sz * qi, -sx * qj, sy * qi, 0};
-        double dMi[9] = {0, sy * qj, sz * qk, sx * qj, -2 * sy * qi, -sz * qr, sx * qk, sy * qr, -2 * sz * qi};
-        double dMj[9] = {-2 * sx * qj, sy * qi, sz * qr, sx * qi, 0, sz * qk, -sx * qr, sy * qk, -2 * sz * qj};
-        double dMk[9] = {-2 * sx * qk, -sy * qr, sz * qi, sx * qr, -2 * sy * qk, sz * qj, sx * qi, sy * qj, 0};
-        double dqn[4] = {0, 0, 0, 0};
-        for (int e = 0; e < 9; ++e) {
-            dqn[0] += 2.0 * dMr[e] * dM[e];
-            dqn[1] += 2.0 * dMi[e] * dM[e];
-            dqn[2] += 2.0 * dMj[e] * dM[e];
-            dqn[3] += 2.0 * dMk[e] * dM[e];
-        }
-        /* q_hat = q / |q|: dL/dq = (dL/dq_hat - q_hat (q_hat . dL/dq_hat)) / |q|. */
-        double proj = dqn[0] * qr + dqn[1] * qi + dqn[2] * qj + dqn[3] * qk;
-        for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - g->qn[k] * proj) / g->qnorm;
-
-        /* Jacobian and screen position depend on the camera-space mean t. */
-        /* Sigma'_raw = U Sigma U^T: dL/dU = (H + H^T) U Sigma; U = J W: dL/dJ = dL/dU W^T. */
-        double Hs[4] = {2 * H[0], H[1] + H[2], H[1] + H[2], 2 * H[3]};
-        double USg[6];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 3; ++c)
-                USg[3 * r + c] = g->U[3 * r] * g->Sigma[c] + g->U[3 * r + 1] * g->Sigma[3 + c] + g->U[3 * r + 2] * g->Sigma[6 + c];
-        double dU[6], dJ[6];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 3; ++c) dU[3 * r + c] = Hs[2 * r] * USg[c] + Hs[2 * r + 1] * USg[3 + c];
-        for (int r = 0; r < 2; ++r)
-            for (int c = 0; c < 3; ++c)
-                dJ[3 * r + c] = dU[3 * r] * S.cam.W[3 * c] + dU[3 * r + 1] * S.cam.W[3 * c + 1] + dU[3 * r + 2] * S.cam.W[3 * c + 2];
-        double tx = g->tcam[0], ty = g->tcam[1], tz = g->tcam[2];
-        double fx = S.cam.fx, fy = S.cam.fy;
-        double du = d_uv[2 * i], dv = d_uv[2 * i + 1];
-        double dt[3];
-        dt[0] = du * fx / tz + dJ[2] * (-fx / (tz * tz));
-        dt[1] = dv * fy / tz + dJ[5] * (-fy / (tz * tz));
-        dt[2] = du * (-fx * tx / (tz * tz)) + dv * (-fy * ty / (tz * tz)) + dJ[0] * (-fx / (tz * tz)) +
-                dJ[2] * (2.0 * fx * tx / (tz * tz * tz)) + dJ[4] * (-fy / (tz * tz)) + dJ[5] * (2.0 * fy * ty / (tz * tz * tz));
-        for (int k = 0; k < 3; ++k) dmu[k] = S.cam.W[k] * dt[0] + S.cam.W[3 + k] * dt[1] + S.cam.W[6 + k] * dt[2];
-
-        /* Colour: rgb = max(0, sum_k sh_k Y_k(d_hat)). */
+        double Hc[4];
+        conic_to_cov_grad(g, d_conic + 3 * i, Hc);
+        d_cov2d[3 * i + 0] = Hc[0];
+        d_cov2d[3 * i + 1] = Hc[1];
+        d_cov2d[3 * i + 2] = Hc[3];
         double drgb[3];
         for (int ch = 0; ch < 3; ++ch) drgb[ch] = g->rgb_raw[ch] > 0.0 ? d_rgb[3 * i + ch] : 0.0;
-        double dd[3] = {0, 0, 0};
-        for (int k = 0; k < D; ++k) {
-            double w = 0.0;
-            for (int ch = 0; ch < 3; ++ch) {
-                dsh[3 * k + ch] = g->Y[k] * drgb[ch];
-                w += sh[((size_t)i * sh_stride + k) * 3 + ch] * drgb[ch];
-            }
-            for (int r = 0; r < 3; ++r) dd[r] += w * g->dY[3 * k + r];
+        gauss_chain(&S, (size_t)i, d_uv + 2 * i, d_conic + 3 * i, drgb, dmu, ds, dq, dsh);
+        if (cond_means) {
+            double c[58];
+            chain_conditioning(&S, (size_t)i, d_uv + 2 * i, d_conic + 3 * i, drgb, c);
+            for (int k = 0; k < 3; ++k) { cond_means[3 * i + k] = c[k]; cond_scales[3 * i + k] = c[3 + k]; }
+            for (int k = 0; k < 4; ++k) cond_quats[4 * i + k] = c[6 + k];
+            for (int k = 0; k < 3 * D; ++k) cond_sh[(size_t)i * sh_stride * 3 + k] = c[10 + k];
         }
-        double dproj = dd[0] * g->dhat[0] + dd[1] * g->dhat[1] + dd[2] * g->dhat[2];
-        for (int r = 0; r < 3; ++r) dmu[r] += (dd[r] - g->dhat[r] * dproj) / g->dnorm;
+        if (!want_allow) continue;
+        /* a colour channel near the 0 clamp: its gradient terms may be absent or present */
+        for (int ch = 0; ch < 3; ++ch) {
+            if (!(g->rgb_amb & (1u << ch)) || d_rgb[3 * i + ch] == 0.0) continue;
+            const double zero2[2] = {0.0, 0.0}, zero3[3] = {0.0, 0.0, 0.0};
+            double one[3] = {0.0, 0.0, 0.0}, amu[3], as[3], aq[4], ash[48];
+            one[ch] = d_rgb[3 * i + ch];
+            gauss_chain(&S, (size_t)i, zero2, zero3, one, amu, as, aq, ash);
+            for (int k = 0; k < 3; ++k) allow_means[3 * i + k] += fabs(amu[k]);
+            for (int k = 0; k < 3 * D; ++k) allow_sh[(size_t)i * sh_stride * 3 + k] += fabs(ash[k]);
+        }
     }
     scene_free(&S);
 }
@@ -1055,6 +1367,47 @@ long orc_bin(long n, const float* uv, const float* depth, const int32_t* radius,
     }
     free(inst);
     return K;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported: (Gaussian, tile) pairs of the Sec. 6 rectangle that any binning   */
+/* must keep: tiles that every rounding of the rectangle contains (rect_in) in */
+/* which some pixel centre certainly reaches alpha_min in FP64, i.e.           */
+/* o G >= alpha_min (1 + eps_alpha + power margin); found by brute force over  */
+/* the tile's pixels.  Writes keys i * tiles + t (up to cap); returns the      */
+/* number of pairs.                                                            */
+/* ------------------------------------------------------------------------- */
+long orc_reach_needed(long n, const double* means, const double* scales, const double* quats, const double* opac,
+                      const double* sh, int deg, int sh_stride, const double* cam, const double* cfg, long cap,
+                      int64_t* out) {
+    ocam c; ocfg f;
+    read_cam(cam, &c); read_cfg(cfg, &f);
+    const int TX = (c.width + f.tile_w - 1) / f.tile_w, TY = (c.height + f.tile_h - 1) / f.tile_h;
+    long count = 0;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long i = 0; i < n; ++i) {
+        ogauss g;
+        gauss_forward((size_t)i, means, scales, quats, opac, sh, deg, sh_stride, &c, &f, &g);
+        if (!g.visible || (g.amb & AMB_CULL)) continue;
+        for (int ty = g.rect_in[2]; ty < g.rect_in[3]; ++ty)
+            for (int tx = g.rect_in[0]; tx < g.rect_in[1]; ++tx) {
+                int hit = 0;
+                for (int ly = 0; ly < f.tile_h && !hit; ++ly)
+                    for (int lx = 0; lx < f.tile_w && !hit; ++lx) {
+                        const int px = tx * f.tile_w + lx, py = ty * f.tile_h + ly;
+                        if (px >= c.width || py >= c.height) continue;
+                        double dx, dy;
+                        const double oG = opac[i] * exp(eval_power(&g, px + 0.5, py + 0.5, &dx, &dy));
+                        hit = oG >= f.alpha_min * (1.0 + f.eps_alpha + power_margin(&g, dx, dy, &f));
+                    }
+                if (!hit) continue;
+                long slot;
+#pragma omp atomic capture
+                slot = count++;
+                if (slot < cap) out[slot] = (int64_t)i * TX * TY + (int64_t)(ty * TX + tx);
+            }
+    }
+    return count;
 }
 
 int orc_num_threads(void) {

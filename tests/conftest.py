@@ -26,3 +26,15 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    # parity statistics of every oracle comparison that ran (flagged pixels, allowances)
+    try:
+        import gpu_util
+    except Exception:  # pragma: no cover
+        return
+    if gpu_util.REPORT:
+        terminalreporter.section("parity against the oracle")
+        for line in gpu_util.REPORT:
+            terminalreporter.write_line(line)

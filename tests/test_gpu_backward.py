@@ -1,7 +1,8 @@
 """gs_render_backward (Sec. 6 traversal, App. A chain rule) vs the oracle's analytic FP64
 gradients, for the screen-space accumulators and for every input tensor; the oracle's
-analytic gradients are themselves pinned to finite differences on the CPU.  Gaussians that
-are relevant to a pixel with an ambiguous decision are excluded and counted."""
+analytic gradients are themselves pinned to finite differences on the CPU.  Every Gaussian is
+checked: the per-element bound holds exactly, plus, for a Gaussian that a decision near its
+threshold touches, the oracle's allowance for that decision being flipped."""
 import numpy as np
 import pytest
 
@@ -12,23 +13,18 @@ from gpu_util import compare_grads, gpu_backward, gpu_forward
 pytestmark = pytest.mark.gpu
 
 
-def _check(g, cam, bg, dimg, tile_mask=None, max_excluded=0.05, cfg=None):
+def _check(g, cam, bg, dimg, tile_mask=None, cfg=None, label=""):
     run = gpu_forward(g, cam, bg, cfg)
     gg = gpu_backward(run, bg, dimg)
     ob = oracle.render_backward(g, cam, dimg, bg, tile_mask=tile_mask)
+    assert ob["dec_overflow"] == 0
     touched = np.abs(ob["opacities"]) > 0
-    keep = touched & (ob["gauss_amb"] == 0)
-    excluded = float((touched & ~keep).sum()) / max(1, touched.sum())
     assert touched.sum() > 10
-    assert excluded <= max_excluded, excluded
     ob2 = dict(ob)
     ob2["opac2d"] = ob["opacities"]
-    s2 = compare_grads(gg, ob2, keep, names=("uv", "cov2d", "opac2d", "rgb"))
-    s3 = compare_grads(gg, ob, keep)
-    # Gaussians that received no gradient in FP64 receive none on the GPU either
-    untouched = ~touched & (ob["gauss_amb"] == 0)
-    assert np.all(gg["opacities"][untouched] == 0)
-    return s2, s3, excluded
+    s2 = compare_grads(gg, ob2, names=("uv", "cov2d", "opac2d", "rgb"), label=label + " screen space")
+    s3 = compare_grads(gg, ob, label=label)
+    return s2, s3
 
 
 @pytest.mark.parametrize("seed,kw", [(301, dict(n=200, width=100, height=37)),
@@ -38,32 +34,25 @@ def _check(g, cam, bg, dimg, tile_mask=None, max_excluded=0.05, cfg=None):
 def test_tiny_scene_gradients(seed, kw):
     g, cam = S.tiny_scene(seed, **kw)
     dimg = S.upstream_grad(seed + 1, cam.height, cam.width)
-    _check(g, cam, (0.1, 0.3, 0.2), dimg, max_excluded=0.1)
+    _check(g, cam, (0.1, 0.3, 0.2), dimg, label=f"tiny{seed}")
 
 
 def test_config2_crop_gradients():
     """The config-2 gradient-check case: 5k Gaussians, 64x64 window of the 1080p camera."""
     g, cam, bg, dimg = S.config2_crop()
-    _check(g, cam, bg, dimg)
+    _check(g, cam, bg, dimg, label="config2 64x64 crop")
 
 
 def test_config2_full_frame_gradients():
     g, cam, bg, dimg = S.config2()
-    _check(g, cam, bg, dimg)
+    _check(g, cam, bg, dimg, label="config2 1080p full frame")
 
 
-def test_config3_sampled_tiles_gradients():
-    """3M Gaussians at 1080p: dL/dpixel is non-zero on 32 sampled tiles only, so the oracle
-    restricted to those tiles computes the same gradients."""
+def test_config3_full_frame_gradients():
+    """3M Gaussians at 1080p (config 3, the benchmarked frame): dL/dpixel ~ N(0, 1) on every
+    pixel, all gradients of all 3M Gaussians against the oracle."""
     g, cam, bg, dimg = S.config3()
-    TX, TY = 120, 68
-    rng = np.random.default_rng(4444)
-    tiles = rng.choice(TX * TY, 32, replace=False)
-    mask = np.zeros(TX * TY, np.uint8)
-    mask[tiles] = 1
-    pix = np.repeat(np.repeat(mask.reshape(TY, TX), 16, 0), 16, 1)[:1080, :1920].astype(bool)
-    dimg = np.where(pix[None], dimg, 0.0).astype(np.float32)
-    _check(g, cam, bg, dimg, tile_mask=mask)
+    _check(g, cam, bg, dimg, label="config3 1080p full frame")
 
 
 def test_accumulate_over_views_sums_gradients():
@@ -99,3 +88,48 @@ def test_autograd_function_matches_direct_calls():
     np.testing.assert_array_equal(img.detach().cpu().numpy(), run["img"].astype(np.float32))
     for k in t:
         np.testing.assert_allclose(t[k].grad.cpu().numpy(), direct[k], rtol=1e-5, atol=1e-7)
+
+
+def test_autograd_settings_reused_across_views_match_fresh_calls():
+    """One settings dict reused for two cameras (one of another image size), and two forward
+    passes before their backward passes: every image and gradient equals a fresh call's."""
+    import torch
+    from paper_2308_04079_gb300 import rasterize
+    g, cam1 = S.tiny_scene(307, n=250, width=64, height=48)
+    cam2 = S.orbit_camera(3.0, 0.6, -0.2, 64, 48)
+    cam3 = S.orbit_camera(3.0, -0.4, 0.3, 80, 40)
+    bg = (0.2, 0.1, 0.3)
+
+    def params():
+        return {k: torch.tensor(getattr(g, k), device="cuda", requires_grad=True)
+                for k in ("means", "scales", "quats", "opacities", "sh")}
+
+    def run(cam, settings=None):
+        t = params()
+        img = rasterize(t["means"], t["scales"], t["quats"], t["opacities"], t["sh"], g.sh_degree, cam, bg,
+                        settings=settings)
+        return t, img
+
+    fresh = {}
+    for name, cam in (("1", cam1), ("2", cam2), ("3", cam3)):
+        t, img = run(cam)
+        d = torch.from_numpy(S.upstream_grad(int(name), cam.height, cam.width)).cuda()
+        (img * d).sum().backward()
+        fresh[name] = (img.detach().clone(), {k: v.grad.clone() for k, v in t.items()}, d)
+    shared = {}
+    # sequential reuse across cameras and image sizes
+    for name, cam in (("1", cam1), ("2", cam2), ("3", cam3)):
+        t, img = run(cam, shared)
+        (img * fresh[name][2]).sum().backward()
+        assert torch.equal(img.detach(), fresh[name][0]), name
+        for k in t:
+            torch.testing.assert_close(t[k].grad, fresh[name][1][k], rtol=1e-5, atol=1e-7)
+    # two forward passes on one settings dict before either backward pass
+    ta, ia = run(cam1, shared)
+    tb, ib = run(cam2, shared)
+    (ib * fresh["2"][2]).sum().backward()
+    (ia * fresh["1"][2]).sum().backward()
+    for (t, img), name in (((ta, ia), "1"), ((tb, ib), "2")):
+        assert torch.equal(img.detach(), fresh[name][0]), name
+        for k in t:
+            torch.testing.assert_close(t[k].grad, fresh[name][1][k], rtol=1e-5, atol=1e-7)

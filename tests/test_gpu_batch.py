@@ -1,14 +1,16 @@
 """Batched stages (gs_batch_*): several frames -- views of uneven size of one scene, or views
 of several scenes -- in one launch per kernel.  Every frame's binning, image, transmittance and
 last contributor equal the single-frame calls bit for bit; each scene's gradients equal the
-per-view calls accumulated over its views (summation order differs: fp32 tolerance); and a
-batched scene is checked against the FP64 oracle on sampled tiles of every view."""
+per-view calls accumulated over its views (summation order differs: fp32 tolerance); the
+config-4 batch (1M Gaussians, 16 uneven views) is checked against the FP64 oracle on every
+pixel of every view and every Gaussian of the summed gradient, and the full-size config-5
+multi-scene graph against the plain calls and, on sampled tiles, against the oracle."""
 import numpy as np
 import pytest
 
 import oracle
 import synthetic as S
-from gpu_util import compare_grads, compare_images, last_contributor_ids
+from gpu_util import compare_grads, compare_images, last_contributor_ids, oracle_view_sum
 
 pytestmark = pytest.mark.gpu
 
@@ -128,49 +130,24 @@ def test_batched_scenes_keep_their_gradients_apart():
             _assert_close_grads(gs[key].cpu().numpy(), gb[s][key].cpu().numpy(), f"scene {s} {key}")
 
 
-def test_batched_views_match_the_oracle_on_sampled_tiles():
-    """Config-4 form (one scene, uneven views) at 300k Gaussians: every view's image on 12
-    sampled tiles, and the gradient summed over all views with dL/dpixel kept on those tiles,
-    against the FP64 oracle."""
+def test_config4_batch_matches_the_oracle():
+    """Config 4 in full: one 1M-Gaussian scene (config-3 distribution), 16 views of uneven size
+    (640x480 to 1920x1080) in one batch, forward and backward with the gradients summed over the
+    views; every pixel of every view and every Gaussian's summed gradient against the oracle."""
     import torch
-    from paper_2308_04079_gb300 import make_config
-    g, gt, cams, _ = _views(3, 300_000, 5)
-    rng = np.random.default_rng(99)
-    bg = (0.0, 0.0, 0.0)
-    masks, dimgs, pixsel = [], [], []
-    for v, cam in enumerate(cams):
-        TX, TY = (cam.width + 15) // 16, (cam.height + 15) // 16
-        m = np.zeros(TX * TY, np.uint8)
-        m[rng.choice(TX * TY, 12, replace=False)] = 1
-        pix = np.repeat(np.repeat(m.reshape(TY, TX), 16, 0), 16, 1)[:cam.height, :cam.width].astype(bool)
-        d = np.where(pix[None], S.upstream_grad(700 + v, cam.height, cam.width), 0.0).astype(np.float32)
-        masks.append(m)
-        dimgs.append(d)
-        pixsel.append(pix)
+    from paper_2308_04079_gb300 import GaussianTensors, make_config
+    g, cams, bg, dimgs = S.config4()
+    gt = GaussianTensors.from_numpy(g).prepared()
     fb, ob, gb = _batched([(gt, cams, [torch.from_numpy(d).cuda() for d in dimgs])], bg, make_config())
-    total = None
     for v, cam in enumerate(cams):
-        orc = oracle.render_forward(g, cam, bg, tile_mask=masks[v])
+        orc = oracle.render_forward(g, cam, bg)
         last = ob[v][2].cpu().numpy()
         run = dict(img=ob[v][0].cpu().numpy().astype(np.float64), T=ob[v][1].cpu().numpy().astype(np.float64),
                    last_id=last_contributor_ids(fb[v], last))
-        pix = pixsel[v]
-        compare_images(dict(img=run["img"][:, pix], T=run["T"][pix], last_id=run["last_id"][pix]),
-                       dict(img=orc["img"][:, pix], T=orc["T"][pix], last_id=orc["last_id"][pix],
-                            pix_amb=orc["pix_amb"][pix]), max_amb_frac=0.05)
-        ob_v = oracle.render_backward(g, cam, dimgs[v], bg, tile_mask=masks[v])
-        if total is None:
-            total = {k: ob_v[k].copy() for k in ("means", "scales", "quats", "opacities", "sh")}
-            amb = ob_v["gauss_amb"].copy()
-        else:
-            for k in total:
-                total[k] += ob_v[k]
-            amb |= ob_v["gauss_amb"]
-    touched = np.abs(total["opacities"]) > 0
-    keep = touched & (amb == 0)
-    assert keep.sum() > 100 and (touched & ~keep).sum() <= 0.05 * touched.sum()
+        compare_images(run, orc, label=f"config4 view {v} {cam.width}x{cam.height}")
+    total = oracle_view_sum(g, cams, dimgs, bg)
     got = {k: gb[0][k].cpu().numpy().astype(np.float64) for k in ("means", "scales", "quats", "opacities", "sh")}
-    compare_grads(got, total, keep)
+    compare_grads(got, total, label="config4 16 views summed")
 
 
 def test_multiscene_graph_with_autotuned_config_matches_plain_calls():
@@ -208,3 +185,63 @@ def test_multiscene_graph_with_autotuned_config_matches_plain_calls():
             v += 1
         for key in GRAD_KEYS:
             _assert_close_grads(gs[key].cpu().numpy(), sb.scene_grads(sc)[key].cpu().numpy(), key)
+
+
+def test_config5_full_size_graph_matches_plain_calls_and_the_oracle():
+    """Config 5 at full size: 8 cluster-mixture scenes of 50k-2M Gaussians, 4 views each at
+    mixed resolutions, forward+backward captured in one CUDA graph at the autotuned tile shape
+    and batch depth.  The graph's images equal the plain per-view calls bit for bit and each
+    scene's gradients their sum over views; on 8 sampled tiles per view (dL/dpixel zero
+    elsewhere), images and every scene's gradients against the oracle at that tile shape."""
+    import torch
+    from paper_2308_04079_gb300 import GaussianTensors
+    from paper_2308_04079_gb300.batching import Scene, SceneBatch, autotune
+    raw, bg = S.config5()
+    bg = tuple(float(x) for x in bg)
+    rng = np.random.default_rng(5555)
+    # the tile shape is chosen first (on full dL/dpixel); the sampled tiles follow it
+    scenes = [Scene(GaussianTensors.from_numpy(g).prepared(), cams, [torch.from_numpy(d).cuda() for d in dl])
+              for g, cams, dl in raw]
+    cfg, table = autotune(scenes, bg, cands=[((16, 16), 128), ((16, 8), 128), ((8, 8), 64)], steps=2)
+    tw, th = cfg.tile_w, cfg.tile_h
+    masks, pixs = [], []
+    for si, (g, cams, dl) in enumerate(raw):
+        mm, pp = [], []
+        for v, cam in enumerate(cams):
+            TX, TY = (cam.width + tw - 1) // tw, (cam.height + th - 1) // th
+            m = np.zeros(TX * TY, np.uint8)
+            m[rng.choice(TX * TY, 8, replace=False)] = 1
+            pix = np.repeat(np.repeat(m.reshape(TY, TX), th, 0), tw, 1)[:cam.height, :cam.width].astype(bool)
+            dl[v] = np.where(pix[None], dl[v], 0.0).astype(np.float32)
+            mm.append(m)
+            pp.append(pix)
+        masks.append(mm)
+        pixs.append(pp)
+    scenes = [Scene(GaussianTensors.from_numpy(g).prepared(), cams, [torch.from_numpy(d).cuda() for d in dl])
+              for g, cams, dl in raw]
+    sb = SceneBatch(scenes, bg, cfg)
+    sb.capture()
+    sb.replay()
+    torch.cuda.synchronize()
+    sb.check()
+    ocfg = oracle.cfg_array(tile_w=tw, tile_h=th)
+    v = 0
+    for si, ((g, cams, dl), sc) in enumerate(zip(raw, scenes)):
+        fs, os_, gs = _single(sc.gaussians, sc.cameras, bg, sc.dL_dimages, cfg)
+        for k, cam in enumerate(cams):
+            for x, y in zip(os_[k], sb.outs[v]):
+                assert torch.equal(x, y)
+            orc = oracle.render_forward(g, cam, bg, ocfg, tile_mask=masks[si][k])
+            last = sb.outs[v][2].cpu().numpy()
+            run = dict(img=sb.outs[v][0].cpu().numpy().astype(np.float64),
+                       T=sb.outs[v][1].cpu().numpy().astype(np.float64),
+                       last_id=last_contributor_ids(sb.frames[v], last))
+            compare_images(run, orc, mask=pixs[si][k], label=f"config5 scene {si} view {k} {tw}x{th}")
+            v += 1
+        got = sb.scene_grads(sc)
+        for key in GRAD_KEYS:
+            _assert_close_grads(gs[key].cpu().numpy(), got[key].cpu().numpy(), key)
+        total = oracle_view_sum(g, cams, dl, bg, ocfg, masks[si])
+        compare_grads({k: got[k].cpu().numpy().astype(np.float64) for k in ("means", "scales", "quats",
+                                                                           "opacities", "sh")},
+                      total, label=f"config5 scene {si} ({g.n} Gaussians, 4 views)")

@@ -198,3 +198,41 @@ def test_config3_full_frame_binning_bit_exact():
     assert np.array_equal(tiles, (keys_o >> np.uint64(32)).astype(np.uint32))
     ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
     assert np.array_equal(ranges, ranges_o)
+
+
+def test_config3_kept_tiles_cover_every_reaching_tile_and_stay_in_the_rectangle():
+    """The benchmark frame (3M Gaussians, 1080p, reachable-tile rule, two-phase schedule) as
+    bench.py bins it: every (Gaussian, tile) pair the GPU keeps lies in the Sec. 6 rectangle
+    (under any rounding of it), and every pair of the FP64 brute-force set -- rectangle tiles in
+    which some pixel centre certainly reaches alpha_min -- is kept.  This does not rely on the
+    oracle's fp32 restatement of the reachable-tile rule."""
+    import torch
+    from gpu_util import REPORT
+    from paper_2308_04079_gb300 import Frame, GaussianTensors, _abi, make_config
+    g, cam, _, _ = S.config3()
+    gt = GaussianTensors.from_numpy(g, device="cuda").prepared()
+    fr = Frame(gt.n, cam, make_config())
+    fr.ensure_binned(gt)
+    code, st = fr.status()
+    assert code == _abi.GS_OK
+    K, T = int(st.num_instances), fr.tiles
+    vals = fr.view("vals_sorted", torch.int32, K).cpu().numpy().astype(np.int64)
+    ranges = fr.view("ranges", torch.int32, 2 * T).cpu().numpy().astype(np.int64).reshape(-1, 2)
+    counts = ranges[:, 1] - ranges[:, 0]
+    assert counts.sum() == K
+    # the instances are sorted by tile id: tile t holds positions [start, end) in order
+    nz = counts > 0
+    assert np.all(np.diff(ranges[nz, 0]) > 0) and np.array_equal(ranges[nz, 0][1:], ranges[nz, 1][:-1])
+    tile = np.repeat(np.arange(T, dtype=np.int64), counts)
+    kept = np.sort(vals * T + tile)
+    pp = oracle.preprocess(g, cam)
+    TX = (cam.width + 15) // 16
+    ro = pp["rect_out"][vals]
+    tx, ty = tile % TX, tile // TX
+    inside = (tx >= ro[:, 0]) & (tx < ro[:, 1]) & (ty >= ro[:, 2]) & (ty < ro[:, 3])
+    assert inside.all(), int((~inside).sum())
+    need = oracle.reach_needed(g, cam)
+    missing = ~np.isin(need, kept, assume_unique=True)
+    REPORT.append(f"binning config3: GPU keeps {K} (Gaussian, tile) pairs, all inside the rectangle; "
+                  f"the FP64 brute-force set has {len(need)}, missing {int(missing.sum())}")
+    assert len(need) > 0.9 * K and not missing.any(), need[missing][:10]

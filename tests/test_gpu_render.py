@@ -1,6 +1,7 @@
 """gs_render_forward (eq. front-to-back, App. C rules) vs the FP64 oracle's per-pixel
 definition: image, final transmittance and last contributor, element by element on every
-pixel whose decisions are not within the ambiguity margin of a threshold."""
+pixel; where a decision lies within its margin of a threshold, the oracle's alternative with
+that decision flipped is accepted too (gpu_util.compare_images)."""
 import numpy as np
 import pytest
 
@@ -32,7 +33,7 @@ def test_tiny_scenes(seed, kw, tile):
     gcfg, ocfg = _cfg_pair(tile)
     run = gpu_forward(g, cam, bg, gcfg)
     orc = oracle.render_forward(g, cam, bg, ocfg)
-    compare_images(run, orc, max_amb_frac=0.05)
+    compare_images(run, orc, label=f"tiny{seed} {tile[0]}x{tile[1]}")
 
 
 @pytest.mark.parametrize("mode,batch", [("two_phase", None), ("key64", None), ("two_phase", 32), ("key64", 100)])
@@ -42,7 +43,7 @@ def test_config1(mode, batch):
     gcfg, ocfg = _cfg_pair((16, 16), mode, batch)
     run = gpu_forward(g, cam, bg, gcfg)
     orc = oracle.render_forward(g, cam, bg, ocfg)
-    st = compare_images(run, orc, max_amb_frac=0.03)
+    compare_images(run, orc, label=f"config1 {mode} batch {batch}")
     assert (run["last"] > 0).mean() > 0.3
 
 
@@ -52,31 +53,20 @@ def test_config2_full_frame():
     gcfg, ocfg = _cfg_pair((16, 16))
     run = gpu_forward(g, cam, bg, gcfg)
     orc = oracle.render_forward(g, cam, bg, ocfg)
-    st = compare_images(run, orc, max_amb_frac=0.03)
-    assert st["pixels"] > 0.97 * 1920 * 1080
+    st = compare_images(run, orc, label="config2 1080p full frame")
+    assert st["flagged_frac"] < 0.05
 
 
-def test_config3_sampled_tiles():
-    """3M Gaussians, 1920x1080 (config 3): every pixel of 48 sampled tiles (plus the image
-    centre and the ragged bottom row of tiles) against the oracle restricted to those tiles."""
+def test_config3_full_frame():
+    """3M Gaussians, 1920x1080 (config 3, the benchmarked frame): every pixel of the frame,
+    including the ragged bottom row of tiles, against the oracle."""
     g, cam, bg, _ = S.config3()
     gcfg, ocfg = _cfg_pair((16, 16))
     run = gpu_forward(g, cam, bg, gcfg)
-    TX, TY = 120, 68
-    rng = np.random.default_rng(3333)
-    tiles = set(rng.choice(TX * TY, 48, replace=False).tolist())
-    tiles |= {34 * TX + 60, 67 * TX + 5, 67 * TX + 119}
-    mask = np.zeros(TX * TY, np.uint8)
-    mask[list(tiles)] = 1
-    orc = oracle.render_forward(g, cam, bg, ocfg, tile_mask=mask)
-    pix = np.zeros((1080, 1920), bool)
-    for t in tiles:
-        ty, tx = divmod(t, TX)
-        pix[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
-    gsub = dict(img=run["img"][:, pix], T=run["T"][pix], last_id=run["last_id"][pix])
-    osub = dict(img=orc["img"][:, pix], T=orc["T"][pix], last_id=orc["last_id"][pix], pix_amb=orc["pix_amb"][pix])
-    compare_images(gsub, osub, max_amb_frac=0.04)
-    assert (run["last"][pix] > 0).mean() > 0.2
+    orc = oracle.render_forward(g, cam, bg, ocfg)
+    st = compare_images(run, orc, label="config3 1080p full frame")
+    assert st["flagged_frac"] < 0.05
+    assert (run["last"] > 0).mean() > 0.2
 
 
 def test_forward_is_deterministic():

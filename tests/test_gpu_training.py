@@ -99,9 +99,11 @@ def test_training_iteration_matches_the_oracle():
     L, _, _, dimg = OT.loss(orc["img"], target, 0.2)
     assert abs(float(out[0].item()) - L) <= 1e-4 * max(1.0, L)
     ob = oracle.render_backward(g, cam, dimg, (0, 0, 0))
+    # The comparison is of Adam steps, whose sign follows the gradient's: an element whose
+    # gradient the oracle's allowance (decisions near their threshold, flipped) could move by
+    # a tenth of its size or more is left out of the sign check, every other one is in it.
     touched = np.abs(ob["opacities"]) > 0
-    keep = touched & (ob["gauss_amb"] == 0)
-    assert keep.sum() > 50
+    grad_of = {"means": "means", "log_scales": "scales", "quats": "quats", "logit_opacities": "opacities"}
     lr = tr.lr
     ref = {
         "means": OT.adam_step(before["means"], ob["means"], 0, 0, lr["means"], 1)[0],
@@ -112,13 +114,17 @@ def test_training_iteration_matches_the_oracle():
     }
     for k, r in ref.items():
         got = getattr(model, k).cpu().numpy().astype(np.float64)
-        dg, dr = (got - before[k])[keep].reshape(-1), (r - before[k])[keep].reshape(-1)
+        gstar = np.abs(ob[grad_of[k]])
+        sure = (np.asarray(ob["allow"][grad_of[k]]) < 0.1 * gstar)
+        sure = (sure & touched.reshape((-1,) + (1,) * (gstar.ndim - 1))).reshape(-1)
+        assert sure.mean() > 0.5
+        dg, dr = (got - before[k]).reshape(-1), (r - before[k]).reshape(-1)
         # a first Adam step is +-lr wherever |g| >> eps: the signs must agree where the oracle's
         # gradient is clearly non-zero, and the sizes everywhere
-        big = np.abs(dr) > 0.5 * lr[k if k != "means" else "means"]
+        big = (np.abs(dr) > 0.5 * lr[k]) & sure
         agree = np.mean(np.sign(dg[big]) == np.sign(dr[big]))
         assert agree >= 0.995, (k, agree)
-        assert np.all(np.abs(dg) <= lr[k if k != "means" else "means"] * (1 + 1e-4) + 1e-7), k
+        assert np.all(np.abs(dg) <= lr[k] * (1 + 1e-4) + 1e-7), k
 
 
 def test_sh_band_schedule_moves_only_the_active_bands():
