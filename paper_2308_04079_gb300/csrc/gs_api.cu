@@ -27,13 +27,16 @@ struct Layout {
     size_t gkey[2], gval[2];
     size_t pairs, scan_lb, sort_lb[2];
     size_t ikey[2], ival[2];
-    size_t ranges, grad2d, pix_count, total;
+    size_t ranges, grad2d, pix_count, contrib, contrib_words, total;
     size_t sort_lb_rows, scan_lb_rows;
     size_t tile_cnt, col_lb, col_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes, tile_passes, tile_digit_bits;
     bool row_sort;             // row-segmented tile sort (two-phase, tiles_x <= kRowSortMaxCols)
     int row_passes;
 };
+
+// Warps of a render block: 4 threads per tile row.
+int render_warps(int tile_h) { return (4 * tile_h + 31) / 32; }
 
 bool valid_cfg(const gs_raster_config* c) {
     if (!c) return false;
@@ -107,6 +110,10 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     L->grad2d = take(nn * 12 * sizeof(float));
     // blended splats per pixel, written by the forward pass when gradients are limited
     L->pix_count = cfg->grad_limit > 0 ? take((size_t)W * H * sizeof(uint32_t)) : 0;
+    // contribution bits: per warp of a tile block, one bit per instance, set by the forward pass
+    // when some pixel of the warp blended that instance (the backward pass visits only those)
+    L->contrib_words = (cc + 31) / 32 + 2;
+    L->contrib = take((size_t)render_warps(cfg->tile_h) * L->contrib_words * sizeof(uint32_t));
     L->total = off;
     return true;
 }
@@ -593,6 +600,7 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
 template <int MAXF>
 gs_status render_forward_impl(const FrameSet<MAXF>& fs, const float* bg, float* const* out_rgb,
                               float* const* out_T, uint32_t* const* out_last, cudaStream_t s) {
+    ClearArgs clr[MAXF];
     Multi<RenderFwdArgs, MAXF> m;
     m.frames = fs.count;
     for (int v = 0; v < fs.count; ++v) {
@@ -616,7 +624,14 @@ gs_status render_forward_impl(const FrameSet<MAXF>& fs, const float* bg, float* 
         a.out_count = f->cfg.grad_limit > 0 ? at<uint32_t>(ws, L.pix_count) : nullptr;
         a.capacity = f->capacity;
         a.status = &control_of(fs, v)->status;
+        a.contrib = at<uint32_t>(ws, L.contrib);
+        a.contrib_words = (uint32_t)L.contrib_words;
+        clr[v] = ClearArgs{};
+        clr[v].ptr[0] = a.contrib;
+        clr[v].words[0] = (unsigned long long)render_warps(f->cfg.tile_h) * L.contrib_words;
     }
+    gs_status st = clear_regions(fs, clr, s);
+    if (st != GS_OK) return st;
     return ok(launch_render_forward(m, s));
 }
 
@@ -655,6 +670,8 @@ gs_status render_backward_tiles_impl(const FrameSet<MAXF>& fs, const float* bg, 
         a.blended = reinterpret_cast<unsigned long long*>(&st->blended_pairs);
         a.capacity = f->capacity;
         a.status = st;
+        a.contrib = at<uint32_t>(ws, L.contrib);
+        a.contrib_words = (uint32_t)L.contrib_words;
     }
     gs_status st = clear_regions(fs, clr, s);
     if (st != GS_OK) return st;

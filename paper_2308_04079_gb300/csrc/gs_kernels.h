@@ -282,6 +282,8 @@ struct RenderFwdArgs {
     uint32_t* out_count;       // nullable: blended splats per pixel (for cfg.grad_limit)
     unsigned long long capacity;   // instance capacity (GS_DEBUG range checks)
     gs_device_status* status;
+    uint32_t* contrib;         // per warp of a tile block: bit i set when the warp blended instance i (zeroed)
+    uint32_t contrib_words;    // words per warp
 };
 
 struct RenderBwdArgs {
@@ -303,6 +305,8 @@ struct RenderBwdArgs {
     unsigned long long* blended;   // count of back-propagated (pixel, splat) pairs, zeroed
     unsigned long long capacity;   // instance capacity (GS_DEBUG range checks)
     gs_device_status* status;
+    const uint32_t* contrib;   // the forward pass's contribution bits (see RenderFwdArgs)
+    uint32_t contrib_words;
 };
 
 // Host-side launchers (defined next to their kernels).  Each returns the launch status.

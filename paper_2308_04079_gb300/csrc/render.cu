@@ -62,8 +62,7 @@ struct Staged {
     float4 b;   // (l11', l21', l22', 1/o)
 };
 
-__device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s,
-                                            float2& lim) {
+__device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s) {
     const float ox = tile_offset(x0, m.x, m.z);
     const float oy = tile_offset(y0, m.y, m.w);
     const float lo = __log2f(L.w);
@@ -71,17 +70,27 @@ __device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, 
     s.a = make_float4(ox, oy, thr, lo);
     s.b = make_float4(__fmul_rn(L.x, kScaleLog2), __fmul_rn(L.y, kScaleLog2), __fmul_rn(L.z, kScaleLog2),
                       __frcp_rn(L.w));
-    // Half-widths of the bounding box of the ellipse s = d^T Q' d <= thr (Q' = L' L'^T):
-    // sqrt(thr (Q'^-1)_00) and sqrt(thr (Q'^-1)_11), widened by a small margin so that the
-    // box test below never drops a pixel that the per-pixel test would keep.
-    if (thr > 0.f) {
-        const float l11 = s.b.x, l21 = s.b.y, l22 = s.b.z;
-        const float xl = sqrtf(thr * (l21 * l21 + l22 * l22)) / (l11 * l22);
-        const float yl = sqrtf(thr) / l22;
-        lim = make_float2(xl * 1.001f + 0.01f, yl * 1.001f + 0.01f);
-    } else {
-        lim = make_float2(-1e30f, -1e30f);   // never reaches alpha >= alpha_min
-    }
+}
+
+// Half-widths of the bounding box of the ellipse s = d^T Q' d <= thr (Q' = L' L'^T) of a staged
+// splat: sqrt(thr (Q'^-1)_00) and sqrt(thr (Q'^-1)_11), widened by a small margin so that the
+// box test (warp_misses) never drops a pixel that the per-pixel test would keep.
+__device__ __forceinline__ float2 splat_lim(const Staged& s) {
+    const float thr = s.a.z;
+    if (!(thr > 0.f)) return make_float2(-1e30f, -1e30f);   // never reaches alpha >= alpha_min
+    const float l11 = s.b.x, l21 = s.b.y, l22 = s.b.z;
+    const float xl = sqrtf(thr * (l21 * l21 + l22 * l22)) / (l11 * l22);
+    const float yl = sqrtf(thr) / l22;
+    return make_float2(xl * 1.001f + 0.01f, yl * 1.001f + 0.01f);
+}
+
+// 32 bits of a contribution bit array ending at bit `hi` (bit 31 = bit hi, bit 0 = bit hi - 31;
+// bits below 0 read as 0).
+__device__ __forceinline__ uint32_t bits_window(const uint32_t* w, uint32_t hi) {
+    const uint32_t word = hi >> 5, sh = hi & 31u;
+    const uint32_t top = w[word] << (31u - sh);
+    const uint32_t low = (sh < 31u && word > 0) ? (w[word - 1] >> (sh + 1u)) : 0u;
+    return top | low;
 }
 
 // Sum over the warp of the 9 accumulators v[0..8] by a transposed reduce-scatter: each round
@@ -186,6 +195,8 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
         if (threadIdx.x == 0) debug_fail(a.status);
         end = start;
     }
+    const int lane = threadIdx.x & 31;
+    uint32_t* const wbits = a.contrib + (size_t)(threadIdx.x >> 5) * a.contrib_words;
     const float amax = a.cfg.alpha_max, tmin = a.cfg.T_min;
     const float log2_amin = __log2f(a.cfg.alpha_min);
 
@@ -212,44 +223,56 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
                 g = 0;
             }
             Staged st;
-            float2 lim;
-            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st, lim);
+            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
             s_sp[k] = st;
             s_rgb[k] = a.rgb[g];
-            s_lim[k] = lim;
+            s_lim[k] = splat_lim(st);
         }
         __syncthreads();
-        if (ndone < PX) {
-            for (int k = 0; k < nb; ++k) {
-                const Staged st = s_sp[k];
-                if (warp_misses(st, s_lim[k], wy0, wy1, wx1)) continue;
-                float p0, dp, q, qq;
-                splat_row(st, lyf, c0f, (float)TPR, p0, dp, q, qq);
-                if (qq > st.a.z) continue;                         // s >= q^2: the whole row skips
+        // 32 splats at a time: the warp's contribution bits for them are one word
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            uint32_t mb = 0;   // bit k - k0: some pixel of this thread blended splat k
+            if (ndone < PX) {
+                const int k1 = min(k0 + 32, nb);
+                for (int k = k0; k < k1; ++k) {
+                    const Staged st = s_sp[k];
+                    if (warp_misses(st, s_lim[k], wy0, wy1, wx1)) continue;
+                    float p0, dp, q, qq;
+                    splat_row(st, lyf, c0f, (float)TPR, p0, dp, q, qq);
+                    if (qq > st.a.z) continue;                         // s >= q^2: the whole row skips
 #pragma unroll
-                for (int j = 0; j < PX; ++j) {
-                    float p;
-                    const float s = splat_s(p0, dp, qq, j, p);
-                    if (done[j] || s > st.a.z) continue;           // alpha < 1/255: skip
-                    const float oG = exp2f(__fsub_rn(st.a.w, s));
-                    const float alpha = fminf(amax, oG);
-                    const float test = __fmul_rn(T[j], __fsub_rn(1.0f, alpha));
-                    if (test < tmin) {                             // stop before exceeding 0.9999
-                        done[j] = true;
-                        ++ndone;
-                        continue;
+                    for (int j = 0; j < PX; ++j) {
+                        float p;
+                        const float s = splat_s(p0, dp, qq, j, p);
+                        if (done[j] || s > st.a.z) continue;           // alpha < 1/255: skip
+                        const float oG = exp2f(__fsub_rn(st.a.w, s));
+                        const float alpha = fminf(amax, oG);
+                        const float test = __fmul_rn(T[j], __fsub_rn(1.0f, alpha));
+                        if (test < tmin) {                             // stop before exceeding 0.9999
+                            done[j] = true;
+                            ++ndone;
+                            continue;
+                        }
+                        const float w = alpha * T[j];
+                        const float4 col = s_rgb[k];
+                        Cr[j] += w * col.x;
+                        Cg[j] += w * col.y;
+                        Cb[j] += w * col.z;
+                        T[j] = test;
+                        last[j] = b - start + (uint32_t)k + 1u;
+                        mb |= 1u << (k - k0);
+                        if (COUNT) ++nblended[j];
                     }
-                    const float w = alpha * T[j];
-                    const float4 col = s_rgb[k];
-                    Cr[j] += w * col.x;
-                    Cg[j] += w * col.y;
-                    Cb[j] += w * col.z;
-                    T[j] = test;
-                    last[j] = b - start + (uint32_t)k + 1u;
-                    if (COUNT) ++nblended[j];
+                    if (ndone == PX) break;
                 }
-                if (ndone == PX) break;
             }
+            mb = __reduce_or_sync(0xffffffffu, mb);
+            if (lane == 0 && mb) {   // instances b + k0 .. b + k0 + 31 of this warp's bit array
+                const uint32_t gi = b + (uint32_t)k0, sh = gi & 31u;
+                atomicOr(wbits + (gi >> 5), mb << sh);
+                if (sh) atomicOr(wbits + (gi >> 5) + 1, mb >> (32u - sh));
+            }
+            if (__all_sync(0xffffffffu, ndone == PX)) break;
         }
     }
     const size_t P = (size_t)c.W * c.H;
@@ -283,9 +306,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
-    float2* s_lim = reinterpret_cast<float2*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
-    uint32_t* s_idx =
-        reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * a.batch);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
+    const uint32_t* const wbits = a.contrib + (size_t)(threadIdx.x >> 5) * a.contrib_words;
     __shared__ uint32_t s_max;
     const CamK& c = a.cam;
     const int tile = (int)(blockIdx.x - m.base[f]);
@@ -301,9 +323,6 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
         if (threadIdx.x == 0) debug_fail(a.status);
         len = 0;
     }
-    constexpr int WROWS = 32 / TPR;   // tile rows per warp
-    const float wy0 = (float)((threadIdx.x >> 5) * WROWS), wy1 = wy0 + (float)(WROWS - 1);
-    const float wx1 = (float)(c.tile_w - 1);
     const float amax = a.cfg.alpha_max;
     const float log2_amin = __log2f(a.cfg.alpha_min);
     const size_t P = (size_t)c.W * c.H;
@@ -357,22 +376,26 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                 g = 0;
             }
             Staged st;
-            float2 lim;
-            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st, lim);
+            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
             s_sp[k] = st;
             s_rgb[k] = a.rgb[g];
-            s_lim[k] = lim;
             s_idx[k] = g;
         }
         __syncthreads();
-        for (int k = 0; k < nb; ++k) {
+        // Only the splats some pixel of this warp blended in the forward pass (its contribution
+        // bits; the backward blends exactly the forward's pairs), 32 at a time.
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+          uint32_t todo = __brev(bits_window(wbits, start + (uint32_t)(bend - 1 - k0)));   // bit i: splat k0 + i
+          if (nb - k0 < 32) todo &= (1u << (nb - k0)) - 1u;
+          while (todo) {
+            const int k = k0 + __ffs(todo) - 1;
+            todo &= todo - 1u;
             const uint32_t pos = (uint32_t)(bend - 1 - k);
             float g[9];
 #pragma unroll
             for (int v = 0; v < 9; ++v) g[v] = 0.f;
             bool contrib = false;
             const Staged st = s_sp[k];
-            if (warp_misses(st, s_lim[k], wy0, wy1, wx1)) continue;
             float p0, dp, q, qq;
             splat_row(st, lyf, c0f, (float)TPR, p0, dp, q, qq);
             if (pos < tmax && qq <= st.a.z) {                      // s >= q^2: else the whole row skips
@@ -429,6 +452,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                 const float tot = warp_reduce9(g, lane);
                 if (slot >= 0 && !(lane & 1)) atomicAdd(dst + slot, tot * (slot < 2 ? k1 : slot < 5 ? k2 : slot == 5 ? ko : 1.0f));
             }
+          }
         }
     }
     const uint32_t wblend = __reduce_add_sync(0xffffffffu, nblend);
@@ -436,9 +460,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
 }
 
 size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * (size_t)batch; }
-size_t bwd_smem(int batch) {
-    return (sizeof(Staged) + sizeof(float4) + sizeof(float2) + sizeof(uint32_t)) * (size_t)batch;
-}
+size_t bwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(uint32_t)) * (size_t)batch; }
 
 }  // namespace
 
