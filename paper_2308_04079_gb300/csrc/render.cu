@@ -72,16 +72,39 @@ __device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, 
                       __frcp_rn(L.w));
 }
 
-// Half-widths of the bounding box of the ellipse s = d^T Q' d <= thr (Q' = L' L'^T) of a staged
-// splat: sqrt(thr (Q'^-1)_00) and sqrt(thr (Q'^-1)_11), widened by a small margin so that the
-// box test (warp_misses) never drops a pixel that the per-pixel test would keep.
-__device__ __forceinline__ float2 splat_lim(const Staged& s) {
-    const float thr = s.a.z;
-    if (!(thr > 0.f)) return make_float2(-1e30f, -1e30f);   // never reaches alpha >= alpha_min
-    const float l11 = s.b.x, l21 = s.b.y, l22 = s.b.z;
-    const float xl = sqrtf(thr * (l21 * l21 + l22 * l22)) / (l11 * l22);
-    const float yl = sqrtf(thr) / l22;
-    return make_float2(xl * 1.001f + 0.01f, yl * 1.001f + 0.01f);
+// Minimum of s = (l11 x + l21 y)^2 + (l22 y)^2 (the staged splat's scaled quadratic form) over
+// the rectangle [xa, xb] x [ya, yb] of pixel-centre offsets: 0 when the splat centre is inside,
+// else the smallest of the four edge minima (each a one-dimensional convex quadratic).
+__device__ __forceinline__ float rect_min_s(const Staged& st, float xa, float xb, float ya, float yb) {
+    const float l11 = st.b.x, l21 = st.b.y, l22 = st.b.z;
+    if (xa <= 0.f && 0.f <= xb && ya <= 0.f && 0.f <= yb) return 0.f;
+    const float i11 = 1.0f / l11, A = fmaf(l21, l21, l22 * l22), iA = 1.0f / A;
+    auto at = [&](float x, float y) { const float p = fmaf(l11, x, l21 * y), q = l22 * y; return fmaf(p, p, q * q); };
+    float m = 3.0e38f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float y = e ? yb : ya;                          // horizontal edge: x* = -l21 y / l11
+        m = fminf(m, at(fminf(fmaxf(-l21 * y * i11, xa), xb), y));
+        const float x = e ? xb : xa;                          // vertical edge: y* = -l11 l21 x / A
+        m = fminf(m, at(x, fminf(fmaxf(-l11 * l21 * x * iA, ya), yb)));
+    }
+    return m;
+}
+
+// Warps of a render block (bit w) whose band of tile rows [w rows_per_warp, (w + 1) rows_per_warp)
+// holds a point where the staged splat reaches alpha_min: the minimum of its quadratic form over
+// the band's rectangle (continuous, so it covers every pixel centre) within a small margin of the
+// threshold.  A cleared bit proves no pixel of that warp blends the splat.
+__device__ __forceinline__ uint32_t band_mask(const Staged& st, int tile_w, int tile_h, int rows_per_warp) {
+    const float thr = st.a.z;
+    if (!(thr > 0.f)) return 0u;
+    const float lim = fmaf(thr, 1.0009765625f, 0.0009765625f);   // thr (1 + 2^-10) + 2^-10
+    uint32_t m = 0;
+    for (int w = 0; w * rows_per_warp < tile_h; ++w) {
+        const float ya = st.a.y + (float)(w * rows_per_warp), yb = ya + (float)(rows_per_warp - 1);
+        if (rect_min_s(st, st.a.x, st.a.x + (float)(tile_w - 1), ya, yb) <= lim) m |= 1u << w;
+    }
+    return m;
 }
 
 // 32 bits of a contribution bit array ending at bit `hi` (bit 31 = bit hi, bit 0 = bit hi - 31;
@@ -138,12 +161,6 @@ __device__ __forceinline__ int reduce_slot(int lane) {
     return slot > 8 ? -1 : slot;
 }
 
-// True when no pixel of the warp's tile rows [wy0, wy1] can be within the splat's box: the warp
-// skips the splat (the test is uniform across the warp).
-__device__ __forceinline__ bool warp_misses(const Staged& s, float2 lim, float wy0, float wy1, float wx1) {
-    return (s.a.x > lim.x) | (s.a.x + wx1 < -lim.x) | (wy0 + s.a.y > lim.y) | (wy1 + s.a.y < -lim.y);
-}
-
 // Per (thread row, splat): p at the thread's first pixel, its step to the next owned pixel
 // (`step` columns to the right), q, q^2.
 __device__ __forceinline__ void splat_row(const Staged& s, float lyf, float c0f, float step, float& p0, float& dp,
@@ -177,7 +194,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
-    float2* s_lim = reinterpret_cast<float2*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
+    uint32_t* s_band = reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
     const CamK& c = a.cam;
     const int tile = (int)(blockIdx.x - m.base[f]);
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
@@ -186,9 +203,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     const int x0 = tx * c.tile_w, y0 = ty * c.tile_h;
     const int py = y0 + ly;
     const float lyf = (float)ly, c0f = (float)c0;
-    constexpr int WROWS = 32 / TPR;   // tile rows per warp
-    const float wy0 = (float)((threadIdx.x >> 5) * WROWS), wy1 = wy0 + (float)(WROWS - 1);
-    const float wx1 = (float)(c.tile_w - 1);
+    const int warp = threadIdx.x >> 5;
     const uint32_t start = a.ranges[2 * tile];
     uint32_t end = a.ranges[2 * tile + 1];
     if (GS_DEBUG && (end < start || end > a.capacity)) {   // a range outside the instance lists
@@ -226,7 +241,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
             stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
             s_sp[k] = st;
             s_rgb[k] = a.rgb[g];
-            s_lim[k] = splat_lim(st);
+            s_band[k] = band_mask(st, c.tile_w, c.tile_h, 32 / TPR);
         }
         __syncthreads();
         // 32 splats at a time: the warp's contribution bits for them are one word
@@ -235,8 +250,8 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
             if (ndone < PX) {
                 const int k1 = min(k0 + 32, nb);
                 for (int k = k0; k < k1; ++k) {
+                    if (!((s_band[k] >> warp) & 1u)) continue;           // no pixel of this warp reaches alpha_min
                     const Staged st = s_sp[k];
-                    if (warp_misses(st, s_lim[k], wy0, wy1, wx1)) continue;
                     float p0, dp, q, qq;
                     splat_row(st, lyf, c0f, (float)TPR, p0, dp, q, qq);
                     if (qq > st.a.z) continue;                         // s >= q^2: the whole row skips
@@ -459,7 +474,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     if ((threadIdx.x & 31) == 0 && wblend) atomicAdd(a.blended, (unsigned long long)wblend);
 }
 
-size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(float2)) * (size_t)batch; }
+size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(uint32_t)) * (size_t)batch; }
 size_t bwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(uint32_t)) * (size_t)batch; }
 
 }  // namespace
