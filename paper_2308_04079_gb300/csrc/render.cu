@@ -63,6 +63,23 @@ struct Staged {
     float4 b;   // (l11', l21', l22', 1/o)
 };
 
+// 2^x with the hardware approximation (PTX ex2.approx.ftz.f32), the one transcendental of the
+// blend; a subnormal result flushes to zero, which never matters here (o G below 1/255 is
+// skipped before it is used).  The forward and the backward both evaluate alpha with it.
+__device__ __forceinline__ float hw_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/x with the hardware approximation (PTX rcp.approx.ftz.f32); the backward divides only by
+// 1 - alpha >= 0.01.
+__device__ __forceinline__ float hw_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s) {
     const float ox = tile_offset(x0, m.x, m.z);
     const float oy = tile_offset(y0, m.y, m.w);
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
                         float p;
                         const float s = splat_s(p0, dp, qq, j, p);
                         if (done[j] || s > st.a.z) continue;           // alpha < 1/255: skip
-                        const float oG = exp2f(__fsub_rn(st.a.w, s));
+                        const float oG = hw_exp2(__fsub_rn(st.a.w, s));
                         const float alpha = fminf(amax, oG);
                         const float test = __fmul_rn(T[j], __fsub_rn(1.0f, alpha));
                         if (test < tmin) {                             // stop before exceeding 0.9999
@@ -424,10 +441,10 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
                     const bool grad = !LIMIT || seen[j]++ >= skip[j];
                     contrib |= grad;
                     ++nblend;
-                    const float oG = exp2f(__fsub_rn(st.a.w, s));
+                    const float oG = hw_exp2(__fsub_rn(st.a.w, s));
                     const float alpha = fminf(amax, oG);
                     const float one_m = __fsub_rn(1.0f, alpha);
-                    const float Ti = __fdividef(T[j], one_m);   // one_m >= 0.01: 2-ulp division
+                    const float Ti = T[j] * hw_rcp(one_m);      // T_i = T_{i+1} / (1 - alpha_i), one_m >= 0.01
                     const float w = alpha * Ti;
                     // dL/dalpha = T_i (c_i - R_{i+1}) . dL/dC;  R_i . dL/dC = R_{i+1} . dL/dC + alpha (c_i - R_{i+1}) . dL/dC
                     const float diff = col.x * dLr[j] + col.y * dLg[j] + col.z * dLb[j] - Rd[j];
