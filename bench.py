@@ -53,7 +53,7 @@ KERNEL_NAMES = {"preprocess": "k_preprocess_t", "render_forward": "k_render_forw
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
 # single-kernel stage on the 3M-Gaussian 1080p frame, taken from a capture of the current
 # kernel; a stage without such a capture reports None.
-TRAFFIC = {"render_backward_tiles": 106_704_896}
+TRAFFIC = {"render_backward_tiles": None}
 
 
 def env_int(k, d):
@@ -127,7 +127,7 @@ class ClockSampler:
 # Measured ALU peaks (denominators of the render kernels' roofline)
 # ------------------------------------------------------------------------------------------
 def measure_alu_peaks(dev, seconds: float = 0.4) -> dict:
-    """FP32 FMA and exp2f throughput of this GPU: gs_peak_fma / gs_peak_ex2 with two 1024-thread
+    """FP32 FMA and 2^x (ex2.approx.ftz.f32) throughput of this GPU: gs_peak_fma / gs_peak_ex2 with two 1024-thread
     blocks per SM, each timed with CUDA events over about `seconds`, clocks sampled meanwhile."""
     import torch
     from paper_2308_04079_gb300 import _abi
@@ -206,14 +206,14 @@ def launches_per_step(layout) -> int:
     passes + one segment pass (count, scan and records), then either sort-prepare + row passes
     over the records + column count + tile scan + column pass (key_passes = row passes + 1) or
     emit + sort-prepare + instance passes + ranges; KEY64: count + pair scan + segment write +
-    emit + sort-prepare + instance passes + ranges; forward; backward tiles; backward
-    Gaussians.  Both two-phase forms launch 5 + key_passes binning kernels after the depth
-    sort."""
+    emit + sort-prepare + instance passes + ranges; every schedule ends with the tile order of
+    the render passes; forward; backward tiles; backward Gaussians.  Both two-phase forms
+    launch 5 + key_passes binning kernels after the depth sort."""
     if layout.depth_passes:
         binning = (1 + layout.depth_passes) + 1 + 3 + layout.key_passes
     else:
         binning = 3 + 3 + layout.key_passes
-    return 1 + binning + 1 + 2
+    return 1 + binning + 1 + 1 + 2
 
 
 def byte_model(n, n_vis, K, segs, P, tiles, sh_floats, layout):
@@ -882,7 +882,7 @@ def main():
     ap.add_argument("--density-only", action="store_true",
                     help="time one density-control refinement (gs_densify) of --gaussians Gaussians only")
     ap.add_argument("--peaks-only", action="store_true",
-                    help="measure and print the FP32 FMA and exp2f peaks of GPU 0 only")
+                    help="measure and print the FP32 FMA and 2^x peaks of GPU 0 only")
     args = ap.parse_args()
     if args.peaks_only:
         import torch

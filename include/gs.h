@@ -172,6 +172,10 @@ typedef struct gs_layout {
                                  the row passes over the segment records + the column pass;
                                  otherwise the radix passes over the instance keys            */
     int depth_passes;         /* radix passes over the Gaussian depths (TWO_PHASE), else 0    */
+    uint64_t tile_order;      /* uint32[tiles] render order written by gs_bin_sort: the tiles
+                                 by decreasing list length (four classes per power of two),
+                                 equal classes in tile order; block b of the render passes
+                                 takes tile_order[b]                                          */
 } gs_layout;
 
 /* Device-side status block (in the workspace). */
@@ -218,7 +222,10 @@ gs_status gs_preprocess(const gs_frame* frame, const gs_gaussians* g, cudaStream
  * arithmetic.  Every dropped pair would be skipped by the alpha test at every pixel of its
  * tile, so the images and gradients are those of the full rectangle.  The instance count stays on the device (status block);
  * if it exceeds frame->capacity, no instance is written past the capacity and the status
- * flag GS_ERR_CAPACITY is raised (the caller grows the workspace and re-runs).
+ * flag GS_ERR_CAPACITY is raised (the caller grows the workspace and re-runs).  Last, the
+ * render order of the tiles (gs_layout.tile_order: longest lists first) is written for
+ * gs_render_forward and gs_render_backward, which therefore need a gs_bin_sort of the frame
+ * before them. 
  * Errors: GS_ERR_INVALID_ARG, GS_ERR_CUDA. */
 gs_status gs_bin_sort(const gs_frame* frame, cudaStream_t stream);
 
@@ -452,12 +459,13 @@ gs_status gs_bin_sort_timed(const gs_frame* frame, float* ms, const char** names
 gs_status gs_read_status(const gs_frame* frame, gs_device_status* out, cudaStream_t stream);
 
 /* Throughput microbenchmarks (no counterpart in the paper; measurement utilities).  The render
- * kernels' work per (pixel, splat) pair is FP32 fused multiply-adds and one exp2f; these two
- * kernels measure this GPU's rate of each, the denominator of the render kernels' roofline.
+ * kernels' work per (pixel, splat) pair is FP32 fused multiply-adds and one 2^x (PTX
+ * ex2.approx.ftz.f32, the instruction the render kernels use); these two kernels measure this
+ * GPU's rate of each, the denominator of the render kernels' roofline.
  *   gs_peak_fma   `blocks` blocks of 1024 threads, each running independent chains of fmaf
- *   gs_peak_ex2   the same with exp2f
+ *   gs_peak_ex2   the same with ex2.approx.ftz.f32
  *   gs_peak_ops   operations one launch of either performs (FMA instructions per lane, i.e.
- *                 flops / 2, or exp2f evaluations), for (blocks, iters)
+ *                 flops / 2, or 2^x evaluations), for (blocks, iters)
  * sink: a device float[blocks] that is never written in practice (it keeps the chains live).
  * Asynchronous on `stream`; time them with events.  Errors: GS_ERR_INVALID_ARG for blocks <= 0,
  * iters <= 0 or a null sink, GS_ERR_CUDA. */

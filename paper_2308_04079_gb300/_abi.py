@@ -66,7 +66,7 @@ class gs_layout(ctypes.Structure):
     _fields_ = [("xy", c_uint64), ("depth", c_uint64), ("conic_opacity", c_uint64), ("rgb", c_uint64),
                 ("radius", c_uint64), ("tau", c_uint64), ("vals_sorted", c_uint64), ("keys_sorted", c_uint64), ("ranges", c_uint64),
                 ("grad2d", c_uint64), ("status", c_uint64), ("total_bytes", c_uint64), ("tiles_x", c_int),
-                ("tiles_y", c_int), ("key_passes", c_int), ("depth_passes", c_int)]
+                ("tiles_y", c_int), ("key_passes", c_int), ("depth_passes", c_int), ("tile_order", c_uint64)]
 
 
 class gs_device_status(ctypes.Structure):

@@ -27,7 +27,7 @@ struct Layout {
     size_t gkey[2], gval[2];
     size_t pairs, scan_lb, sort_lb[2];
     size_t ikey[2], ival[2];
-    size_t ranges, grad2d, pix_count, contrib, contrib_words, total;
+    size_t ranges, tile_order, grad2d, pix_count, contrib, contrib_words, total;
     size_t sort_lb_rows, scan_lb_rows;
     size_t tile_cnt, col_lb, col_lb_rows;
     int tiles_x, tiles_y, tiles, key_passes, depth_passes, tile_passes, tile_digit_bits;
@@ -103,6 +103,7 @@ bool make_layout(int n, int W, int H, uint64_t cap, const gs_raster_config* cfg,
     // first tiles and offsets (capacity + 1 entries) in ikey[1], Gaussian ids in ival[1].
     for (int k = 0; k < 2; ++k) { L->ikey[k] = take(cc * 8 + 16); L->ival[k] = take(cc * 4); }
     L->ranges = take((size_t)L->tiles * 2 * sizeof(uint32_t));
+    L->tile_order = take((size_t)L->tiles * sizeof(uint32_t));
     L->tile_cnt = take((size_t)L->tiles * sizeof(uint32_t));
     // column-count look-back rows, one per chunk of row-sorted segment records
     L->col_lb_rows = L->row_sort ? (cc + kColChunk - 1) / kColChunk : 0;
@@ -594,7 +595,19 @@ gs_status bin_sort_impl(const FrameSet<MAXF>& fs, cudaStream_t s) {
         st = tiles_by_radix(radix, key64, s);
         if (st != GS_OK) return st;
     }
-    return rows.count ? tiles_by_rows(rows, s) : GS_OK;
+    if (rows.count) {
+        st = tiles_by_rows(rows, s);
+        if (st != GS_OK) return st;
+    }
+    // the render passes' block order: every frame's tiles by decreasing list length
+    Multi<TileOrderArgs, MAXF> o;
+    o.frames = fs.count;
+    for (int v = 0; v < fs.count; ++v)
+        o.a[v] = TileOrderArgs{at<uint32_t>(fs.f[v]->ws, fs.L[v].ranges), at<uint32_t>(fs.f[v]->ws, fs.L[v].tile_order),
+                               fs.L[v].tiles};
+    st = ok(launch_tile_order(o, s));
+    phase("tile order", s);
+    return st;
 }
 
 template <int MAXF>
@@ -626,6 +639,7 @@ gs_status render_forward_impl(const FrameSet<MAXF>& fs, const float* bg, float* 
         a.status = &control_of(fs, v)->status;
         a.contrib = at<uint32_t>(ws, L.contrib);
         a.contrib_words = (uint32_t)L.contrib_words;
+        a.order = at<uint32_t>(ws, L.tile_order);
         clr[v] = ClearArgs{};
         clr[v].ptr[0] = a.contrib;
         clr[v].words[0] = (unsigned long long)render_warps(f->cfg.tile_h) * L.contrib_words;
@@ -672,6 +686,7 @@ gs_status render_backward_tiles_impl(const FrameSet<MAXF>& fs, const float* bg, 
         a.status = st;
         a.contrib = at<uint32_t>(ws, L.contrib);
         a.contrib_words = (uint32_t)L.contrib_words;
+        a.order = at<uint32_t>(ws, L.tile_order);
     }
     gs_status st = clear_regions(fs, clr, s);
     if (st != GS_OK) return st;
@@ -815,6 +830,7 @@ gs_status gs_workspace_layout(int n, int width, int height, uint64_t capacity, c
     out->tiles_y = L.tiles_y;
     out->key_passes = L.key_passes;
     out->depth_passes = L.depth_passes;
+    out->tile_order = L.tile_order;
     return GS_OK;
 }
 

@@ -57,6 +57,24 @@ __device__ __forceinline__ void debug_fail(gs_device_status* st) {
     if (GS_DEBUG && st) atomicOr(&st->flags, kFlagInternal);
 }
 
+// 2^x with the hardware approximation (PTX ex2.approx.ftz.f32), the one transcendental of the
+// blend; a subnormal result flushes to zero, which never matters there (o G below 1/255 is
+// skipped before it is used).  The forward and the backward both evaluate alpha with it, and the
+// ex2 throughput microbenchmark measures it.
+__device__ __forceinline__ float hw_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/x with the hardware approximation (PTX rcp.approx.ftz.f32); the render backward divides only
+// by 1 - alpha >= 0.01.
+__device__ __forceinline__ float hw_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }

@@ -284,6 +284,7 @@ struct RenderFwdArgs {
     gs_device_status* status;
     uint32_t* contrib;         // per warp of a tile block: bit i set when the warp blended instance i (zeroed)
     uint32_t contrib_words;    // words per warp
+    const uint32_t* order;     // [tiles] the tile of each block (k_tile_order)
 };
 
 struct RenderBwdArgs {
@@ -307,6 +308,14 @@ struct RenderBwdArgs {
     gs_device_status* status;
     const uint32_t* contrib;   // the forward pass's contribution bits (see RenderFwdArgs)
     uint32_t contrib_words;
+    const uint32_t* order;     // [tiles] the tile of each block (k_tile_order)
+};
+
+// Render order of a frame's tiles (k_tile_order): decreasing instance count.
+struct TileOrderArgs {
+    const uint32_t* ranges;    // [2 * tiles] the binning stage's tile ranges
+    uint32_t* order;           // [tiles] out: tile ids, longest lists first, stable
+    int tiles;
 };
 
 // Host-side launchers (defined next to their kernels).  Each returns the launch status.
@@ -326,6 +335,7 @@ template <int MAXF> cudaError_t launch_tile_scan(const Multi<ColArgs, MAXF>& m, 
 template <int MAXF> cudaError_t launch_col_scatter(const Multi<ColArgs, MAXF>& m, cudaStream_t s);
 template <int MAXF> cudaError_t launch_render_forward(Multi<RenderFwdArgs, MAXF>& m, cudaStream_t s);
 template <int MAXF> cudaError_t launch_render_backward(Multi<RenderBwdArgs, MAXF>& m, cudaStream_t s);
+template <int MAXF> cudaError_t launch_tile_order(const Multi<TileOrderArgs, MAXF>& m, cudaStream_t s);
 cudaError_t launch_clear(const Multi<ClearArgs, kMaxFrames>& m, cudaStream_t s);
 
 }  // namespace gs

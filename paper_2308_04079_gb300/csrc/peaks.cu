@@ -1,6 +1,7 @@
 // peaks.cu -- throughput microbenchmarks that anchor the roofline of the issue-bound render
-// kernels, whose work per (pixel, splat) pair is FP32 fused multiply-adds plus one exp2f: the
-// measured FP32 FMA rate (2 flops per lane per instruction) and exp2f rate of this GPU.
+// kernels, whose work per (pixel, splat) pair is FP32 fused multiply-adds plus one 2^x: the
+// measured FP32 FMA rate (2 flops per lane per instruction) and the rate of the render's 2^x
+// instruction (hw_exp2, PTX ex2.approx.ftz.f32) on this GPU.
 //
 // Every thread runs kChains independent dependency chains, kUnroll steps per loop trip, so each
 // SM sub-partition always has ready instructions despite the pipeline latency.  The chains'
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_ex2(int iters, float* sin
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-            for (int k = 0; k < kChains; ++k) a[k] = exp2f(-a[k]);   // stays in (0.5, 1]
+            for (int k = 0; k < kChains; ++k) a[k] = hw_exp2(-a[k]);   // stays in (0.5, 1]
     }
     float s = 0.f;
 #pragma unroll

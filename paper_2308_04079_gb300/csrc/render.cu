@@ -41,6 +41,11 @@
 // The forward and the backward evaluate a (pixel, splat) pair with the same staging and the same
 // operation sequence (stage_splat, splat_row, splat_s), so their skip and clamp decisions agree
 // bit for bit.
+//
+// Block order: block b of a frame renders tile order[b], the frame's tiles by decreasing list
+// length (k_tile_order, run at the end of the binning stage).  The work of a tile grows with its
+// list and varies by a factor of several across a frame; blocks start roughly in index order, so
+// in row-major order the longest tiles (the frame's centre) could start late and finish alone.
 #include "gs_device.cuh"
 #include "gs_kernels.h"
 
@@ -62,23 +67,6 @@ struct Staged {
     float4 a;   // (ox, oy, thr, lo): tile-relative offset, skip threshold, log2(opacity)
     float4 b;   // (l11', l21', l22', 1/o)
 };
-
-// 2^x with the hardware approximation (PTX ex2.approx.ftz.f32), the one transcendental of the
-// blend; a subnormal result flushes to zero, which never matters here (o G below 1/255 is
-// skipped before it is used).  The forward and the backward both evaluate alpha with it.
-__device__ __forceinline__ float hw_exp2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// 1/x with the hardware approximation (PTX rcp.approx.ftz.f32); the backward divides only by
-// 1 - alpha >= 0.01.
-__device__ __forceinline__ float hw_rcp(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 __device__ __forceinline__ void stage_splat(float4 m, float4 L, int x0, int y0, float log2_amin, Staged& s) {
     const float ox = tile_offset(x0, m.x, m.z);
@@ -197,6 +185,68 @@ __device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, fl
     return __fmaf_rn(p, p, qq);
 }
 
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderWarps = kOrderThreads / 32;
+constexpr int kOrderBuckets = 128;   // = 4 per lane of the scan warp
+
+// Bucket of a tile's list length: four per octave (the leading bit and the two below it),
+// longer lists in higher buckets; lengths below 2^30 reach bucket 120 at most.
+__device__ __forceinline__ int order_bucket(uint32_t len) {
+    if (len == 0) return 0;
+    const int e = 31 - __clz(len);
+    const uint32_t frac = e >= 2 ? (len >> (e - 2)) & 3u : (len << (2 - e)) & 3u;
+    return min(kOrderBuckets - 1, 1 + 4 * e + (int)frac);
+}
+
+// One block per frame: a stable counting sort of the tiles by decreasing bucket.  Warp w takes
+// a contiguous range of tiles: it counts its range per bucket (its own row of s_pos), a scan over
+// buckets (in decreasing order) and warps turns the counts into first positions, and each warp
+// places its range in tile order.
+template <int MAXF>
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_constant__ Multi<TileOrderArgs, MAXF> m) {
+    __shared__ uint32_t s_pos[kOrderWarps][kOrderBuckets];
+    __shared__ uint32_t s_tot[kOrderBuckets];
+    const TileOrderArgs& a = m.a[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = a.tiles;
+    const int per = ((tiles + kOrderThreads - 1) / kOrderThreads) * 32;   // tiles per warp, a multiple of 32
+    const int t_lo = min(tiles, warp * per), t_hi = min(tiles, t_lo + per);
+    for (int b = lane; b < kOrderBuckets; b += 32) s_pos[warp][b] = 0;
+    __syncwarp();
+    for (int t = t_lo + lane; t < t_hi; t += 32) atomicAdd(&s_pos[warp][order_bucket(a.ranges[2 * t + 1] - a.ranges[2 * t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets) {
+        uint32_t sum = 0;
+        for (int w = 0; w < kOrderWarps; ++w) sum += s_pos[w][threadIdx.x];
+        s_tot[threadIdx.x] = sum;
+    }
+    __syncthreads();
+    if (warp == 0) {   // lane l: buckets 127 - 4l, ..., 124 - 4l
+        uint32_t c[4], sum = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { c[e] = s_tot[kOrderBuckets - 1 - 4 * lane - e]; sum += c[e]; }
+        uint32_t run = warp_inclusive_scan<uint32_t>(sum) - sum;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { s_tot[kOrderBuckets - 1 - 4 * lane - e] = run; run += c[e]; }
+    }
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets) {
+        uint32_t run = s_tot[threadIdx.x];
+        for (int w = 0; w < kOrderWarps; ++w) { const uint32_t c = s_pos[w][threadIdx.x]; s_pos[w][threadIdx.x] = run; run += c; }
+    }
+    __syncthreads();
+    for (int t0 = t_lo; t0 < t_hi; t0 += 32) {   // warp-uniform
+        const int t = t0 + lane;
+        const int b = t < t_hi ? order_bucket(a.ranges[2 * t + 1] - a.ranges[2 * t]) : -1;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        if (b >= 0) a.order[s_pos[warp][b] + rank] = (uint32_t)t;
+        __syncwarp();
+        if (b >= 0 && rank == 0) s_pos[warp][b] += __popc(peers);
+        __syncwarp();
+    }
+}
+
 template <int PX, int TPR, int MAXF, bool COUNT>
 __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__ Multi<RenderFwdArgs, MAXF> m) {
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
@@ -214,7 +264,12 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
     uint32_t* s_band = reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
     const CamK& c = a.cam;
-    const int tile = (int)(blockIdx.x - m.base[f]);
+    const uint32_t tile_id = a.order[blockIdx.x - m.base[f]];
+    if (tile_id >= m.base[f + 1] - m.base[f]) {   // an order not written by gs_bin_sort
+        if (threadIdx.x == 0) debug_fail(a.status);
+        return;
+    }
+    const int tile = (int)tile_id;
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
     const int nthreads = blockDim.x;
     const int ly = threadIdx.x / TPR, c0 = threadIdx.x % TPR;   // TPR threads per tile row
@@ -343,7 +398,12 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     const uint32_t* const wbits = a.contrib + (size_t)(threadIdx.x >> 5) * a.contrib_words;
     __shared__ uint32_t s_max;
     const CamK& c = a.cam;
-    const int tile = (int)(blockIdx.x - m.base[f]);
+    const uint32_t tile_id = a.order[blockIdx.x - m.base[f]];
+    if (tile_id >= m.base[f + 1] - m.base[f]) {   // an order not written by gs_bin_sort
+        if (threadIdx.x == 0) debug_fail(a.status);
+        return;
+    }
+    const int tile = (int)tile_id;
     const int tx = tile % c.tiles_x, ty = tile / c.tiles_x;
     const int nthreads = blockDim.x;
     const int ly = threadIdx.x / TPR, c0 = threadIdx.x % TPR;   // TPR threads per tile row
@@ -544,6 +604,14 @@ cudaError_t launch_render_backward(Multi<RenderBwdArgs, MAXF>& m, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <int MAXF>
+cudaError_t launch_tile_order(const Multi<TileOrderArgs, MAXF>& m, cudaStream_t s) {
+    k_tile_order<MAXF><<<m.frames, kOrderThreads, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tile_order<1>(const Multi<TileOrderArgs, 1>&, cudaStream_t);
+template cudaError_t launch_tile_order<kMaxFrames>(const Multi<TileOrderArgs, kMaxFrames>&, cudaStream_t);
 template cudaError_t launch_render_forward<1>(Multi<RenderFwdArgs, 1>&, cudaStream_t);
 template cudaError_t launch_render_forward<kMaxFrames>(Multi<RenderFwdArgs, kMaxFrames>&, cudaStream_t);
 template cudaError_t launch_render_backward<1>(Multi<RenderBwdArgs, 1>&, cudaStream_t);

@@ -49,6 +49,27 @@ def _frame(sp, W, H, tile, mode, capacity, rule="reach"):
     return fr
 
 
+def _expected_tile_order(ranges):
+    """The render order gs_bin_sort must write: tiles by decreasing list-length class (four
+    classes per power of two: the leading bit's position and the two bits below it; class 0
+    for an empty tile), equal classes in increasing tile id."""
+    length = (ranges[:, 1].astype(np.int64) - ranges[:, 0].astype(np.int64))
+    cls = np.zeros(len(length), np.int64)
+    for t, n in enumerate(length.tolist()):
+        if n > 0:
+            e = n.bit_length() - 1
+            two = (n >> (e - 2)) & 3 if e >= 2 else (n << (2 - e)) & 3
+            cls[t] = min(127, 1 + 4 * e + two)
+    return np.argsort(-cls, kind="stable").astype(np.uint32)
+
+
+def _check_tile_order(fr):
+    import torch
+    ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    order = fr.view("tile_order", torch.int32, fr.tiles).cpu().numpy().view(np.uint32)
+    assert np.array_equal(order, _expected_tile_order(ranges))
+
+
 def _bin_gpu(sp, W, H, tile, mode, capacity, rule="reach"):
     fr = _frame(sp, W, H, tile, mode, capacity, rule)
     fr.bin_sort()
@@ -87,6 +108,7 @@ def test_bin_sort_bit_exact(mode, rule, seed, n, W, H, tile, rmax, huge):
     assert np.array_equal(vals, vals_o)
     ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
     assert np.array_equal(ranges, ranges_o)
+    _check_tile_order(fr)
     if mode == "key64":
         keys = fr.view("keys_sorted", torch.int64, K).cpu().numpy().view(np.uint64)
         assert np.array_equal(keys, keys_o)
@@ -112,6 +134,7 @@ def test_bin_sort_empty_and_all_culled(mode):
     fr, code, st = _bin_gpu(sp, 64, 48, (16, 16), mode, 10)
     assert code == _abi.GS_OK and st.num_instances == 0
     assert np.all(fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy() == 0)
+    assert np.array_equal(fr.view("tile_order", torch.int32, fr.tiles).cpu().numpy(), np.arange(fr.tiles))
 
 
 @pytest.mark.parametrize("mode", ["two_phase", "key64"])
@@ -164,6 +187,7 @@ def test_batch_mixing_row_sort_and_radix_frames():
         assert np.array_equal(ranges, ranges_o)
         tiles = fr.view("keys_sorted", torch.int32, K).cpu().numpy().view(np.uint32)
         assert np.array_equal(tiles, (keys_o >> np.uint64(32)).astype(np.uint32))
+        _check_tile_order(fr)
 
 
 def test_config3_full_frame_binning_bit_exact():
@@ -198,6 +222,7 @@ def test_config3_full_frame_binning_bit_exact():
     assert np.array_equal(tiles, (keys_o >> np.uint64(32)).astype(np.uint32))
     ranges = fr.view("ranges", torch.int32, 2 * fr.tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
     assert np.array_equal(ranges, ranges_o)
+    _check_tile_order(fr)
 
 
 def test_config3_kept_tiles_cover_every_reaching_tile_and_stay_in_the_rectangle():

@@ -6,8 +6,8 @@
   frame whose binning timed out, and the next call with the default limit on the same
   workspace is exact.
 * The GS_DEBUG build (libgs_gb300_debug.so, selected by GS_DEBUG=1): the small parity cases run
-  clean under its bounds checks, and a corrupted tile range or instance index is reported as
-  GS_ERR_INTERNAL instead of being read out of bounds.
+  clean under its bounds checks, and a corrupted tile range, instance index or render order
+  entry is reported as GS_ERR_INTERNAL instead of being read out of bounds.
 """
 import os
 import subprocess
@@ -116,6 +116,12 @@ def test_debug_checks_report_a_corrupted_range_and_index():
     fr.ensure_binned(gt)
     vals = fr.view("vals_sorted", torch.int32, fr.capacity)
     vals[int(ranges[busy, 0])] = gt.n + 5
+    fr.render_forward((0, 0, 0), img, T, last)
+    assert fr.status()[0] == _abi.GS_ERR_INTERNAL
+    # a render order naming a tile that does not exist
+    fr.ensure_binned(gt)
+    order = fr.view("tile_order", torch.int32, fr.tiles)
+    order[3] = fr.tiles + 7
     fr.render_forward((0, 0, 0), img, T, last)
     assert fr.status()[0] == _abi.GS_ERR_INTERNAL
 
