@@ -247,25 +247,16 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
     }
 }
 
-template <int PX, int TPR, int MAXF, bool COUNT>
-__global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__ Multi<RenderFwdArgs, MAXF> m) {
-    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
-    // a batch reads its frame's arguments from a shared copy (loads through a pointer into the
-    // parameter array would be generic loads, repeated after every global store)
-    __shared__ __align__(16) RenderFwdArgs s_args;
-    if (MAXF > 1) {
-        for (int k = threadIdx.x; k < (int)(sizeof(RenderFwdArgs) / 4); k += blockDim.x)
-            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
-        __syncthreads();
-    }
-    const RenderFwdArgs& a = MAXF == 1 ? m.a[0] : s_args;
+// Forward pass of the tile order[block_slot] of a frame with ntiles tiles.
+template <int PX, int TPR, bool COUNT>
+__device__ __forceinline__ void forward_tile(const RenderFwdArgs& a, uint32_t block_slot, uint32_t ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
     uint32_t* s_band = reinterpret_cast<uint32_t*>(smem_raw + (sizeof(Staged) + sizeof(float4)) * a.batch);
     const CamK& c = a.cam;
-    const uint32_t tile_id = a.order[blockIdx.x - m.base[f]];
-    if (tile_id >= m.base[f + 1] - m.base[f]) {   // an order not written by gs_bin_sort
+    const uint32_t tile_id = a.order[block_slot];
+    if (tile_id >= ntiles) {   // an order not written by gs_bin_sort
         if (threadIdx.x == 0) debug_fail(a.status);
         return;
     }
@@ -287,6 +278,12 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     uint32_t* const wbits = a.contrib + (size_t)(threadIdx.x >> 5) * a.contrib_words;
     const float amax = a.cfg.alpha_max, tmin = a.cfg.T_min;
     const float log2_amin = __log2f(a.cfg.alpha_min);
+    // what the loops read, in registers
+    const int batch = a.batch, n = a.n, tile_w = c.tile_w, tile_h = c.tile_h;
+    const uint32_t* const vals = a.vals;
+    const float4* const xy = a.xy;
+    const float4* const conic = a.conic_opacity;
+    const float4* const rgb = a.rgb;
 
     float T[PX], Cr[PX], Cg[PX], Cb[PX];
     uint32_t last[PX], nblended[PX];
@@ -301,20 +298,20 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
         done[j] = !(x0 + c0 + TPR * j < c.W && py < c.H);
         ndone += done[j];
     }
-    for (uint32_t b = start; b < end; b += a.batch) {
+    for (uint32_t b = start; b < end; b += batch) {
         if (__syncthreads_count(ndone == PX) == nthreads) break;
-        const int nb = (int)min((uint32_t)a.batch, end - b);
+        const int nb = (int)min((uint32_t)batch, end - b);
         for (int k = threadIdx.x; k < nb; k += nthreads) {
-            uint32_t g = a.vals[b + k];
-            if (g >= (uint32_t)a.n) {   // only reachable after a timed-out sort
+            uint32_t g = vals[b + k];
+            if (g >= (uint32_t)n) {   // only reachable after a timed-out sort
                 debug_fail(a.status);
                 g = 0;
             }
             Staged st;
-            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
+            stage_splat(xy[g], conic[g], x0, y0, log2_amin, st);
             s_sp[k] = st;
-            s_rgb[k] = a.rgb[g];
-            s_band[k] = band_mask(st, c.tile_w, c.tile_h, 32 / TPR);
+            s_rgb[k] = rgb[g];
+            s_band[k] = band_mask(st, tile_w, tile_h, 32 / TPR);
         }
         __syncthreads();
         // 32 splats at a time: the warp's contribution bits for them are one word
@@ -379,18 +376,24 @@ __global__ void __launch_bounds__(64) k_render_forward_t(const __grid_constant__
     }
 }
 
-template <int PX, int TPR, int MAXF, bool LIMIT>
-__global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant__ Multi<RenderBwdArgs, MAXF> m) {
-    const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns tiles [base[f], base[f+1])
-    // a batch reads its frame's arguments from a shared copy (loads through a pointer into the
-    // parameter array would be generic loads, repeated after every global store)
-    __shared__ __align__(16) RenderBwdArgs s_args;
-    if (MAXF > 1) {
-        for (int k = threadIdx.x; k < (int)(sizeof(RenderBwdArgs) / 4); k += blockDim.x)
-            reinterpret_cast<uint32_t*>(&s_args)[k] = reinterpret_cast<const uint32_t*>(&m.a[f])[k];
-        __syncthreads();
+// One block per tile.  A single frame reads its arguments straight from the parameter bank; a
+// batch copies its frame's block of arguments into registers once (measured on four 1M-Gaussian
+// views: half the instructions of a shared-memory copy, whose compiled form executed the blend
+// loop's skipped pairs at the cost of blended ones).
+template <int PX, int TPR, int MAXF, bool COUNT>
+__global__ void __launch_bounds__(64, 1) k_render_forward_t(const __grid_constant__ Multi<RenderFwdArgs, MAXF> m) {
+    if constexpr (MAXF == 1) {
+        forward_tile<PX, TPR, COUNT>(m.a[0], blockIdx.x, m.base[1]);
+    } else {
+        const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);
+        const RenderFwdArgs a = m.a[f];
+        forward_tile<PX, TPR, COUNT>(a, blockIdx.x - m.base[f], m.base[f + 1] - m.base[f]);
     }
-    const RenderBwdArgs& a = MAXF == 1 ? m.a[0] : s_args;
+}
+
+// Backward pass of the tile order[block_slot] of a frame with ntiles tiles.
+template <int PX, int TPR, bool LIMIT>
+__device__ __forceinline__ void backward_tile(const RenderBwdArgs& a, uint32_t block_slot, uint32_t ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Staged* s_sp = reinterpret_cast<Staged*>(smem_raw);
     float4* s_rgb = reinterpret_cast<float4*>(smem_raw + sizeof(Staged) * a.batch);
@@ -398,8 +401,8 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     const uint32_t* const wbits = a.contrib + (size_t)(threadIdx.x >> 5) * a.contrib_words;
     __shared__ uint32_t s_max;
     const CamK& c = a.cam;
-    const uint32_t tile_id = a.order[blockIdx.x - m.base[f]];
-    if (tile_id >= m.base[f + 1] - m.base[f]) {   // an order not written by gs_bin_sort
+    const uint32_t tile_id = a.order[block_slot];
+    if (tile_id >= ntiles) {   // an order not written by gs_bin_sort
         if (threadIdx.x == 0) debug_fail(a.status);
         return;
     }
@@ -419,6 +422,13 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     const float amax = a.cfg.alpha_max;
     const float log2_amin = __log2f(a.cfg.alpha_min);
     const size_t P = (size_t)c.W * c.H;
+    // what the loops read, in registers (see the forward pass)
+    const int batch = a.batch, n = a.n;
+    const uint32_t* const vals = a.vals;
+    const float4* const xy = a.xy;
+    const float4* const conic = a.conic_opacity;
+    const float4* const rgb = a.rgb;
+    float* const grad2d = a.grad2d;
 
     // Per pixel: T, R . dL/dC (only this projection of the colour behind is ever needed) and dL/dC.
     float T[PX], Rd[PX], dLr[PX], dLg[PX], dLb[PX];
@@ -459,19 +469,19 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     const int lane = threadIdx.x & 31;
     const int slot = reduce_slot(lane);
 
-    for (int bend = (int)count; bend > 0; bend -= a.batch) {
-        const int nb = min(a.batch, bend);
+    for (int bend = (int)count; bend > 0; bend -= batch) {
+        const int nb = min(batch, bend);
         __syncthreads();
         for (int k = threadIdx.x; k < nb; k += nthreads) {
-            uint32_t g = a.vals[start + (uint32_t)(bend - 1 - k)];
-            if (g >= (uint32_t)a.n) {   // only reachable after a timed-out sort
+            uint32_t g = vals[start + (uint32_t)(bend - 1 - k)];
+            if (g >= (uint32_t)n) {   // only reachable after a timed-out sort
                 debug_fail(a.status);
                 g = 0;
             }
             Staged st;
-            stage_splat(a.xy[g], a.conic_opacity[g], x0, y0, log2_amin, st);
+            stage_splat(xy[g], conic[g], x0, y0, log2_amin, st);
             s_sp[k] = st;
-            s_rgb[k] = a.rgb[g];
+            s_rgb[k] = rgb[g];
             s_idx[k] = g;
         }
         __syncthreads();
@@ -532,7 +542,7 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
             }
             const uint32_t who = __ballot_sync(0xffffffffu, contrib);
             if (who == 0) continue;
-            float* dst = a.grad2d + 12 * (size_t)s_idx[k];
+            float* dst = grad2d + 12 * (size_t)s_idx[k];
             const float k1 = kUnscale, k2 = kLn2, ko = st.b.w;
             if (__popc(who) <= kDirectLanes) {
                 // few contributing lanes: each adds its own sums (cheaper than a butterfly)
@@ -550,6 +560,18 @@ __global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant_
     }
     const uint32_t wblend = __reduce_add_sync(0xffffffffu, nblend);
     if ((threadIdx.x & 31) == 0 && wblend) atomicAdd(a.blended, (unsigned long long)wblend);
+}
+
+// One block per tile, arguments as in k_render_forward_t.
+template <int PX, int TPR, int MAXF, bool LIMIT>
+__global__ void __launch_bounds__(64) k_render_backward_t(const __grid_constant__ Multi<RenderBwdArgs, MAXF> m) {
+    if constexpr (MAXF == 1) {
+        backward_tile<PX, TPR, LIMIT>(m.a[0], blockIdx.x, m.base[1]);
+    } else {
+        const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);
+        const RenderBwdArgs a = m.a[f];
+        backward_tile<PX, TPR, LIMIT>(a, blockIdx.x - m.base[f], m.base[f + 1] - m.base[f]);
+    }
 }
 
 size_t fwd_smem(int batch) { return (sizeof(Staged) + sizeof(float4) + sizeof(uint32_t)) * (size_t)batch; }
