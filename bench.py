@@ -206,14 +206,15 @@ def launches_per_step(layout) -> int:
     passes + one segment pass (count, scan and records), then either sort-prepare + row passes
     over the records + column count + tile scan + column pass (key_passes = row passes + 1) or
     emit + sort-prepare + instance passes + ranges; KEY64: count + pair scan + segment write +
-    emit + sort-prepare + instance passes + ranges; every schedule ends with the tile order of
-    the render passes; forward; backward tiles; backward Gaussians.  Both two-phase forms
-    launch 5 + key_passes binning kernels after the depth sort."""
+    emit + sort-prepare + instance passes + ranges; every schedule starts with one clear kernel
+    (its four zeroed regions) and ends with the tile order of the render passes; forward;
+    backward tiles after one clear kernel (accumulators and counter); backward Gaussians.  Both
+    two-phase forms launch 5 + key_passes binning kernels after the depth sort."""
     if layout.depth_passes:
         binning = (1 + layout.depth_passes) + 1 + 3 + layout.key_passes
     else:
         binning = 3 + 3 + layout.key_passes
-    return 1 + binning + 1 + 1 + 2
+    return 1 + (1 + binning + 1) + 1 + (1 + 1) + 1
 
 
 def byte_model(n, n_vis, K, segs, P, tiles, sh_floats, layout):

@@ -1262,7 +1262,12 @@ __global__ void __launch_bounds__(256) k_clear(const __grid_constant__ Multi<Cle
 }
 
 cudaError_t launch_clear(const Multi<ClearArgs, kMaxFrames>& m, cudaStream_t s) {
-    k_clear<<<persistent_grid((const void*)k_clear, 256), 256, 0, s>>>(m);
+    unsigned long long words = 0;   // blocks for the largest region (16 bytes per thread), at most one wave
+    for (int f = 0; f < m.frames; ++f)
+        for (int r = 0; r < kClearRegions; ++r) words = std::max(words, m.a[f].ptr[r] ? m.a[f].words[r] : 0ull);
+    const unsigned long long want = (words / 4 + 255) / 256;
+    const int grid = (int)std::max(1ull, std::min(want, (unsigned long long)persistent_grid((const void*)k_clear, 256)));
+    k_clear<<<grid, 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 

@@ -240,7 +240,12 @@ bool sh_vec(const float* sh, int sh_stride, const float* gsh = nullptr) {
 // for a batch.
 template <int MAXF>
 gs_status clear_regions(const FrameSet<MAXF>& fs, const ClearArgs* regions, cudaStream_t s) {
-    if (MAXF == 1 || fs.count == 1) {
+    // one region: a memset; several: one kernel for all of them (each memset is an operation
+    // of its own on the stream)
+    int nonempty = 0;
+    for (int v = 0; v < fs.count; ++v)
+        for (int r = 0; r < kClearRegions; ++r) nonempty += regions[v].ptr[r] && regions[v].words[r];
+    if (nonempty <= 1) {
         for (int v = 0; v < fs.count; ++v)
             for (int r = 0; r < kClearRegions; ++r)
                 if (regions[v].ptr[r] && regions[v].words[r] &&

@@ -123,8 +123,11 @@ __device__ __forceinline__ void load_sh(const float* __restrict__ sh, float (&f)
 
 }  // namespace
 
+// 6 blocks of 256 per SM (40 registers): config 3 (3M Gaussians) 0.157 -> 0.148 ms against the
+// 48-register build at 5 blocks; streaming or L2-only loads of the SH rows were slower (0.194,
+// 0.175 ms) and also slowed the backward, which re-reads the rows that stay in L2.
 template <int DEG, bool VEC, int MAXF, bool ISO>
-__global__ void __launch_bounds__(256) k_preprocess_t(const __grid_constant__ Multi<PreprocessArgs, MAXF> m) {
+__global__ void __launch_bounds__(256, 6) k_preprocess_t(const __grid_constant__ Multi<PreprocessArgs, MAXF> m) {
     constexpr int D = (DEG + 1) * (DEG + 1);
     const int f = find_frame<MAXF>(m.base, m.frames, blockIdx.x);   // frame f owns blocks [base[f], base[f+1])
     // a batch reads its frame's arguments from a shared copy (generic loads otherwise)

@@ -68,13 +68,14 @@ def test_bench_launch_count_and_byte_model_follow_the_schedule():
     c.sort_mode = _abi.GS_SORT_KEY64
     k64 = _abi.gs_workspace_layout(3_000_000, 1920, 1080, 1 << 20, c)
     assert bench.row_sort(rows) and not bench.row_sort(wide) and not bench.row_sort(k64)
-    # preprocess, depth histogram + 4 depth passes, segment pass, sort-prepare, row pass,
-    # column count, tile scan, column pass, tile order, forward, backward tiles, backward Gaussians
-    assert bench.launches_per_step(rows) == 16
+    # preprocess, clear, depth histogram + 4 depth passes, segment pass, sort-prepare, row pass,
+    # column count, tile scan, column pass, tile order, forward, clear, backward tiles, backward
+    # Gaussians
+    assert bench.launches_per_step(rows) == 18
     # the same with emit + 2 tile-id passes + ranges in place of the row sort's four kernels
-    assert bench.launches_per_step(wide) == 1 + 5 + 1 + 1 + 1 + wide.key_passes + 1 + 1 + 3
+    assert bench.launches_per_step(wide) == 1 + 1 + 5 + 1 + 1 + 1 + wide.key_passes + 1 + 1 + 4
     # KEY64: count + pair scan + segment write + emit + sort-prepare + 6 passes + ranges
-    assert bench.launches_per_step(k64) == 1 + 3 + 3 + 6 + 1 + 3
+    assert bench.launches_per_step(k64) == 1 + 1 + 3 + 3 + 6 + 1 + 4
     n, n_vis, K, segs, tiles = 3_000_000, 2_436_483, 28_516_288, 9_019_658, 8160
     depth = 8 * n + 4 * 16 * n
     b = bench.byte_model(n, n_vis, K, segs, 1920 * 1080, tiles, 48, rows)["bin_sort"]
