@@ -1255,6 +1255,13 @@ void orc_render_backward(long n, const double* means, const double* scales, cons
 /* the leftmost X(clip(-y*), -1) (each branch is concave/convex in y); widened by */
 /* 0.01 px they bound the columns px with px + 0.5 - u inside; the tiles holding  */
 /* those columns, cut to the rectangle, are kept.                                 */
+/* This rule is a restatement of a decision the rasterizer takes in fp32, not a   */
+/* definition from the paper: it serves the bit-exact binning test of the         */
+/* default schedule only.  It is pinned apart from the rasterizer by FP64 brute   */
+/* force over pixel centres (every tile with a pixel reaching alpha_min is kept,  */
+/* every kept tile lies in the rectangle and near the ellipse; orc_reach_needed), */
+/* and on the benchmark frame the GPU's kept tiles are checked against that FP64  */
+/* set directly; images are shown identical to the rectangle rule's.              */
 /* ------------------------------------------------------------------------- */
 static float reach_x32(float t, float inv11, float l21, float l22, float y, float s) {
     float q = l22 * y;
