@@ -188,7 +188,6 @@ __device__ __forceinline__ float splat_s(float p0, float dp, float qq, int j, fl
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderWarps = kOrderThreads / 32;
 constexpr int kOrderBuckets = 128;   // = 4 per lane of the scan warp
-constexpr int kOrderCached = 8;      // rounds of 32 tiles per warp whose buckets stay in registers
 
 // Bucket of a tile's list length: four per octave (the leading bit and the two below it),
 // longer lists in higher buckets; lengths below 2^30 reach bucket 120 at most.
@@ -212,19 +211,9 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
     const int tiles = a.tiles;
     const int per = ((tiles + kOrderThreads - 1) / kOrderThreads) * 32;   // tiles per warp, a multiple of 32
     const int t_lo = min(tiles, warp * per), t_hi = min(tiles, t_lo + per);
-    // the buckets of a warp's first kOrderCached rounds of 32 tiles stay in registers (every
-    // tile of frames up to 32 x kOrderCached x kOrderWarps = 8192 tiles, 1080p at 16x16);
-    // further rounds load their ranges again
-    auto bucket_of = [&](int t) { return t < t_hi ? order_bucket(a.ranges[2 * t + 1] - a.ranges[2 * t]) : -1; };
-    int bk[kOrderCached];
-#pragma unroll
-    for (int i = 0; i < kOrderCached; ++i) bk[i] = bucket_of(t_lo + 32 * i + lane);
     for (int b = lane; b < kOrderBuckets; b += 32) s_pos[warp][b] = 0;
     __syncwarp();
-#pragma unroll
-    for (int i = 0; i < kOrderCached; ++i)
-        if (bk[i] >= 0) atomicAdd(&s_pos[warp][bk[i]], 1u);
-    for (int t = t_lo + 32 * kOrderCached + lane; t < t_hi; t += 32) atomicAdd(&s_pos[warp][bucket_of(t)], 1u);
+    for (int t = t_lo + lane; t < t_hi; t += 32) atomicAdd(&s_pos[warp][order_bucket(a.ranges[2 * t + 1] - a.ranges[2 * t])], 1u);
     __syncthreads();
     if (threadIdx.x < kOrderBuckets) {
         uint32_t sum = 0;
@@ -246,17 +235,16 @@ __global__ void __launch_bounds__(kOrderThreads) k_tile_order(const __grid_const
         for (int w = 0; w < kOrderWarps; ++w) { const uint32_t c = s_pos[w][threadIdx.x]; s_pos[w][threadIdx.x] = run; run += c; }
     }
     __syncthreads();
-    auto place = [&](int t, int b) {   // warp-uniform call, rounds in increasing tile order
+    for (int t0 = t_lo; t0 < t_hi; t0 += 32) {   // warp-uniform
+        const int t = t0 + lane;
+        const int b = t < t_hi ? order_bucket(a.ranges[2 * t + 1] - a.ranges[2 * t]) : -1;
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         const uint32_t rank = __popc(peers & lanemask_lt());
         if (b >= 0) a.order[s_pos[warp][b] + rank] = (uint32_t)t;
         __syncwarp();
         if (b >= 0 && rank == 0) s_pos[warp][b] += __popc(peers);
         __syncwarp();
-    };
-#pragma unroll
-    for (int i = 0; i < kOrderCached; ++i) place(t_lo + 32 * i + lane, bk[i]);
-    for (int t0 = t_lo + 32 * kOrderCached; t0 < t_hi; t0 += 32) place(t0 + lane, bucket_of(t0 + lane));
+    }
 }
 
 // Forward pass of the tile order[block_slot] of a frame with ntiles tiles.
