@@ -89,6 +89,10 @@ CASES = [
     (7, 20000, 4400, 200, (16, 16), 20, 0),
     (8, 20000, 640, 4200, (16, 16), 20, 1),
     (9, 15000, 2040, 300, (8, 8), 12, 0),
+    # large splats only (up to ~190 tile rows each): a segment-pass chunk of 256 entries spans
+    # more than the 4096 rectangle rows it keeps in shared memory, so the rows past them are
+    # evaluated again when their records are written
+    (10, 600, 1920, 2400, (16, 16), 1500, 0),
 ]
 
 
