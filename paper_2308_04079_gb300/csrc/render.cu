@@ -13,9 +13,14 @@
 // Forward (eq. front-to-back, App. C): a = min(0.99, o exp(power)); skip a < 1/255; stop before
 //   T (1 - a) < 1e-4; C += a T c; T *= 1 - a.  The tile stops as soon as all its pixels are done
 //   (checked once per batch with __syncthreads_count).  Writes C + T bg, T and the 1-based list
-//   position of the last blended Gaussian.
-// Backward: the tile's list is walked back to front from the largest last position in the tile;
-//   each pixel only processes positions below its own last position, recovers
+//   position of the last blended Gaussian.  The staging thread of a splat also computes, per
+//   warp (a band of 8 tile rows), whether the splat can reach alpha_min anywhere in the band
+//   (band_mask), and a warp skips the splats that cannot; for every 32 splats a warp ORs into
+//   its contribution bits (one bit per instance of the frame) those that some pixel of the
+//   warp blended.
+// Backward: the tile's list is walked back to front from the largest last position in the tile,
+//   each warp visiting only the splats its contribution bits name (it blends exactly the
+//   forward's pairs); each pixel only processes positions below its own last position, recovers
 //   T_i = T_{i+1} / (1 - a_i) from the stored final T, and keeps R . dL/dC, the projection of
 //   the colour behind the current Gaussian (normalised by the transmittance in front of it; R
 //   starts at bg) on the pixel's dL/dC, which is all the recurrence needs:
@@ -29,9 +34,10 @@
 //   by its minor axis and their major-axis part, which the scale along the long axis needs, is
 //   lost to cancellation in fp32 sums over many pixels; in the whitened frame every direction of
 //   the splat has the same scale.  A thread sums its pixels' terms (mean, Sigma', opacity,
-//   colour); when more than twelve lanes of a warp contributed, the warp sums its lanes with a
-//   transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals with one atomic
-//   instruction, otherwise the contributing lanes add their own sums.
+//   colour); when more than kDirectLanes (20) lanes of a warp contributed, the warp sums its
+//   lanes with a transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals
+//   with one atomic instruction each, otherwise every contributing lane adds its own sums (two
+//   float4 atomics and one scalar).
 //
 // Limited-BW (cfg.grad_limit = N > 0, the ablation of Sec. 7.3): the forward pass also records
 // the number of blended splats of every pixel (COUNT); the backward pass (LIMIT) keeps the
