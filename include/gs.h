@@ -47,8 +47,9 @@ typedef enum gs_status {
     GS_ERR_NUMERIC = 5,       /* non-finite inputs were found and culled (results are valid)   */
     GS_ERR_INTERNAL = 6       /* a device-side consistency check failed: the per-tile instance
                                  counts did not add up to the instance count, or (in a GS_DEBUG
-                                 build) an instance or range index was out of bounds; results
-                                 are invalid, nothing was written out of bounds               */
+                                 build) an instance or range index was out of bounds while no
+                                 capacity overflow or timeout had been reported; results are
+                                 invalid, nothing was written out of bounds                   */
 } gs_status;
 
 /* Pinhole camera (the paper's view configuration V, Algorithm 2; viewing transformation W

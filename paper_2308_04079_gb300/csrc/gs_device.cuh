@@ -53,8 +53,11 @@ constexpr uint32_t kSpinLimit = GS_DEFAULT_SPIN_LIMIT;
 #ifndef GS_DEBUG
 #define GS_DEBUG 0
 #endif
+// A check that fails after a capacity overflow or a timed-out wait reports nothing: the data
+// it looked at were never produced, and the status block already says why.
 __device__ __forceinline__ void debug_fail(gs_device_status* st) {
-    if (GS_DEBUG && st) atomicOr(&st->flags, kFlagInternal);
+    if (GS_DEBUG && st && !(*reinterpret_cast<volatile const uint32_t*>(&st->flags) & (kFlagCapacity | kFlagTimeout)))
+        atomicOr(&st->flags, kFlagInternal);
 }
 
 // 2^x with the hardware approximation (PTX ex2.approx.ftz.f32), the one transcendental of the
