@@ -13,10 +13,10 @@ from gpu_util import compare_grads, gpu_backward, gpu_forward
 pytestmark = pytest.mark.gpu
 
 
-def _check(g, cam, bg, dimg, tile_mask=None, cfg=None, label=""):
+def _check(g, cam, bg, dimg, tile_mask=None, cfg=None, label="", ocfg=None):
     run = gpu_forward(g, cam, bg, cfg)
     gg = gpu_backward(run, bg, dimg)
-    ob = oracle.render_backward(g, cam, dimg, bg, tile_mask=tile_mask)
+    ob = oracle.render_backward(g, cam, dimg, bg, cfg=ocfg, tile_mask=tile_mask)
     assert ob["dec_overflow"] == 0
     touched = np.abs(ob["opacities"]) > 0
     assert touched.sum() > 10
@@ -35,6 +35,20 @@ def test_tiny_scene_gradients(seed, kw):
     g, cam = S.tiny_scene(seed, **kw)
     dimg = S.upstream_grad(seed + 1, cam.height, cam.width)
     _check(g, cam, (0.1, 0.3, 0.2), dimg, label=f"tiny{seed}")
+
+
+@pytest.mark.parametrize("tile", [(16, 8), (8, 8)])
+@pytest.mark.parametrize("seed,kw", [(301, dict(n=200, width=100, height=37)),
+                                     (303, dict(n=400, width=90, height=70, deg=3, log_scale_mean=-3.0))])
+def test_tiny_scene_gradients_other_tile_shapes(seed, kw, tile):
+    """The 16x8 and 8x8 tile shapes (one warp per tile; two pixels per thread for 8x8): the
+    oracle bins with the same shape (the 3-sigma rectangle is tile-granular, so the shape is
+    part of the definition)."""
+    from paper_2308_04079_gb300 import make_config
+    g, cam = S.tiny_scene(seed, **kw)
+    dimg = S.upstream_grad(seed + 1, cam.height, cam.width)
+    _check(g, cam, (0.1, 0.3, 0.2), dimg, cfg=make_config(tile=tile),
+           ocfg=oracle.cfg_array(tile_w=tile[0], tile_h=tile[1]), label=f"tiny{seed} {tile[0]}x{tile[1]}")
 
 
 def test_config2_crop_gradients():
