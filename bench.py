@@ -452,9 +452,11 @@ def run_ours(args, rank, world, local_rank):
         batch = run_batch(args, dev)
         multi = run_multiscene(args, dev)
 
-    cpu = None
+    cpu = small = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, cam, bg, dimg)
+        if args.gaussians == CONFIG3_N:
+            small = run_small_configs(dev, stream)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -467,6 +469,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "density_control": density, "variants": variants,
         "batch": batch,
         "multi_scene": multi,
+        "small_configs": small,
         "gpu_launches": launches_per_step(fr.layout) * args.steps, "kernels": kernels,
     }
     if rank == 0:
@@ -831,6 +834,59 @@ def cpu_baseline(g, cam, bg, dimg):
               f"all {tiles} 16x16 tiles ({s:.1f} s)")
     return {"value": round(1.0 / s, 6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": sample}
+
+
+def run_small_configs(dev, stream):
+    """Configs 1 (1k Gaussians, 128x128, forward only) and 2 (200k Gaussians, 1080p, forward +
+    backward): the GPU's time per frame through the same calls as the main step (CUDA events,
+    median of 20 after 5 warm-ups) beside the FP64 oracle's time for the same frame on all host
+    cores."""
+    import torch
+    import oracle
+    import synthetic as S
+    from paper_2308_04079_gb300 import Frame, GaussianTensors, make_config
+    out = {}
+    for name, fn in (("config1", S.config1), ("config2", S.config2)):
+        res = fn()
+        g, cam, bg = res[0], res[1], tuple(float(x) for x in res[2])
+        dimg = res[3] if len(res) > 3 else None
+        gt = GaussianTensors.from_numpy(g, device=dev).prepared()
+        fr = Frame(gt.n, cam, make_config(), device=dev)
+        fr.ensure_binned(gt)
+        img, T, last = fr.outputs()
+        d = torch.from_numpy(dimg).to(dev) if dimg is not None else None
+        grads = fr.new_grads(gt)
+
+        def frame():
+            fr.preprocess(gt)
+            fr.bin_sort()
+            fr.render_forward(bg, img, T, last)
+            if d is not None:
+                fr.render_backward(gt, bg, d, T, last, grads)
+
+        for _ in range(5):
+            frame()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(20):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            frame()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        g64 = _f64_gaussians(g)
+        t0 = time.perf_counter()
+        if d is None:
+            oracle.render_forward(g64, cam, bg)
+        else:
+            oracle.render_backward(g64, cam, dimg, bg, allowance=False)
+            oracle.render_forward(g64, cam, bg)
+        t_orc = time.perf_counter() - t0
+        out[name] = {"what": "forward" if d is None else "forward + backward", "gaussians": gt.n,
+                     "size": f"{cam.width}x{cam.height}", "gpu_ms": round(float(np.median(times)), 4),
+                     "oracle_s": round(t_orc, 3), "oracle_cores": oracle.num_threads()}
+    return out
 
 
 def run_reference(args, rank, world):
