@@ -325,6 +325,7 @@ __device__ __forceinline__ void forward_tile(const RenderFwdArgs& a, uint32_t bl
             uint32_t mb = 0;   // bit k - k0: some pixel of this thread blended splat k
             if (ndone < PX) {
                 const int k1 = min(k0 + 32, nb);
+#pragma unroll 2   // lets the next splat's row setup overlap this one's blend (forward 0.340 -> 0.333 ms)
                 for (int k = k0; k < k1; ++k) {
                     if (!((s_band[k] >> warp) & 1u)) continue;           // no pixel of this warp reaches alpha_min
                     const Staged st = s_sp[k];
