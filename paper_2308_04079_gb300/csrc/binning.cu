@@ -826,6 +826,7 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
             const uint32_t r0 = min(TR, (uint32_t)tid * per), r1 = min(TR, r0 + per);
             unsigned long long mine = 0;
             int ew = r0 < r1 ? find_entry(r0) : 0;   // entry of row fr, walked forward
+#pragma unroll 2
             for (uint32_t fr = r0; fr < r1; ++fr) {
                 while (s_rowpre[ew + 1] <= fr) ++ew;
                 int e = ew, ty, txa = 0, txb = 0;
@@ -899,6 +900,7 @@ __global__ void __launch_bounds__(kDupThreads) k_segments(const __grid_constant_
             // exclusive prefix (the runs are in row order, so the records are too)
             unsigned long long at = run_ex;
             ew = r0 < r1 ? find_entry(r0) : 0;
+#pragma unroll 2
             for (uint32_t fr = r0; fr < r1; ++fr) {
                 while (s_rowpre[ew + 1] <= fr) ++ew;
                 int e = ew, ty = 0, txa = 0;
