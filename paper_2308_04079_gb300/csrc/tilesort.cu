@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(kColThreads, 5) k_col_scatter(const __grid_con
                     }
                     __syncthreads();
                     const uint32_t rbase = r * tx;
+#pragma unroll 4
                     for (uint32_t s = (uint32_t)tid; s < n; s += kColThreads) {
                         const uint32_t d = s_col[s];
                         const uint32_t dest = s_dst[d] + s;
