@@ -34,7 +34,7 @@
 //   by its minor axis and their major-axis part, which the scale along the long axis needs, is
 //   lost to cancellation in fp32 sums over many pixels; in the whitened frame every direction of
 //   the splat has the same scale.  A thread sums its pixels' terms (mean, Sigma', opacity,
-//   colour); when more than kDirectLanes (20) lanes of a warp contributed, the warp sums its
+//   colour); when more than kDirectLanes (24) lanes of a warp contributed, the warp sums its
 //   lanes with a transposed reduce-scatter (warp_reduce9) and nine lanes add the nine totals
 //   with one atomic instruction each, otherwise every contributing lane adds its own sums (two
 //   float4 atomics and one scalar).
@@ -66,8 +66,8 @@ constexpr float kUnscale = 1.1774100225154747f;
 // (1/2) / kScaleLog2^2 = ln 2: scaled (p, q)(p, q)^T sums to K = (1/2) sum dL/dpower (p, q)(p, q)^T.
 constexpr float kLn2 = 0.69314718055994531f;
 // At most this many contributing lanes add their own sums instead of a warp reduction (measured
-// on the 3M-Gaussian 1080p frame: 20 beats 6, 12 and 32).
-constexpr int kDirectLanes = 20;
+// on the 3M-Gaussian 1080p frame: 24 beats 6, 12, 16, 20 and 32).
+constexpr int kDirectLanes = 24;
 
 struct Staged {
     float4 a;   // (ox, oy, thr, lo): tile-relative offset, skip threshold, log2(opacity)
