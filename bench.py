@@ -53,7 +53,7 @@ KERNEL_NAMES = {"preprocess": "k_preprocess_t", "render_forward": "k_render_forw
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of each
 # single-kernel stage on the 3M-Gaussian 1080p frame, taken from a capture of the current
 # kernel; a stage without such a capture reports None.
-TRAFFIC = {"render_backward_tiles": 104_857_600, "render_forward": 70_443_008}
+TRAFFIC = {"render_backward_tiles": 107_670_016, "render_forward": 70_443_008}
 
 
 def env_int(k, d):
