@@ -464,6 +464,7 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(gt.n, cam, (cfg.tile_w, cfg.tile_h), world),
         "workload_stats": {"sort_mode": args.sort_mode, "visible": n_vis, "instances": K, "segments": segs,
+                           "tiles": int(fr.tiles), "mean_list_length": round(K / fr.tiles, 2),
                            "sum_last": int(sum_last), "blended_pairs": blended},
         "alu_peaks": peaks,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "render_only": render_only, "train_step": train, "density_control": density, "variants": variants,
@@ -582,6 +583,29 @@ def run_variants(args, dev, stream, g, cam, bg, d_dimg, plain_ms):
     return out
 
 
+def frame_stats(frames, lasts=None, backward=True):
+    """Workload figures of a config, summed over its frames: visible Gaussians, instances K,
+    segment records, tiles, the mean tile list length K / tiles and, when given, the walked
+    (pixel, splat) pairs (the sum of every pixel's last position) and the blended pairs of the
+    last backward pass."""
+    import torch
+    vis = K = segs = tiles = blended = 0
+    for f in frames:
+        _, st = f.status()
+        vis += int(st.num_visible)
+        K += int(st.num_instances)
+        segs += int(st.num_segments)
+        blended += int(st.blended_pairs)
+        tiles += int(f.tiles)
+    out = {"frames": len(frames), "visible": vis, "instances": K, "segments": segs, "tiles": tiles,
+           "mean_list_length": round(K / max(tiles, 1), 2)}
+    if lasts is not None:
+        out["sum_last"] = int(sum(float(x.to(torch.float64).sum().item()) for x in lasts))
+    if backward:
+        out["blended_pairs"] = blended
+    return out
+
+
 def run_batch(args, dev):
     """Config 4: one 1M-Gaussian scene (config-3 distribution), 16 views of uneven size,
     forward+backward with the gradients summed over the views -- as one batch (one launch per
@@ -638,12 +662,13 @@ def run_batch(args, dev):
         code, _ = f.status()
         if code not in (0, 5):
             raise RuntimeError(f"batched frame failed with status {code}")
+    stats = frame_stats(frames, [o[2] for o in outs])
     sizes = sorted({(c.width, c.height) for c in cams})
     return {"workload": f"one scene of {gt.n} Gaussians (config-3 distribution), {len(frames)} views of uneven size "
                         f"({', '.join(f'{w}x{h}' for w, h in sizes)}), forward+backward, gradients summed over views",
             "views": len(frames), "batched_ms": round(ms_batch, 4), "per_view_ms": round(ms_loop, 4),
             "speedup": round(ms_loop / ms_batch, 3), "views_per_s": round(len(frames) / (ms_batch * 1e-3), 1),
-            "images_identical": bool(same), "steps": steps}
+            "images_identical": bool(same), "steps": steps, "workload_stats": stats}
 
 
 def run_multiscene(args, dev):
@@ -688,12 +713,13 @@ def run_multiscene(args, dev):
     b.record(stream)
     torch.cuda.synchronize()
     ms_plain = a.elapsed_time(b) / steps
+    stats = frame_stats(sb.frames, [o[2] for o in sb.outs])
     return {"workload": f"{len(scenes)} scenes of {', '.join(str(s.gaussians.n) for s in scenes)} Gaussians, "
                         f"{len(sb.frames)} frames at mixed resolutions, forward+backward, one CUDA graph",
             "tile": f"{cfg.tile_w}x{cfg.tile_h}", "batch_depth": int(cfg.batch_depth),
             "autotune": [{"tile": f"{t[0]}x{t[1]}", "batch_depth": d, "ms": round(ms, 4)} for t, d, ms in table],
             "graph_ms": round(ms_graph, 4), "plain_ms": round(ms_plain, 4), "speedup": round(ms_plain / ms_graph, 3),
-            "frames_per_s": round(len(sb.frames) / (ms_graph * 1e-3), 1), "steps": steps}
+            "frames_per_s": round(len(sb.frames) / (ms_graph * 1e-3), 1), "steps": steps, "workload_stats": stats}
 
 
 def run_e2e(args, g, gt, fr, dimg, bg, img, T, last, grads, stream, world, dev):
@@ -885,7 +911,8 @@ def run_small_configs(dev, stream):
         t_orc = time.perf_counter() - t0
         out[name] = {"what": "forward" if d is None else "forward + backward", "gaussians": gt.n,
                      "size": f"{cam.width}x{cam.height}", "gpu_ms": round(float(np.median(times)), 4),
-                     "oracle_s": round(t_orc, 3), "oracle_cores": oracle.num_threads()}
+                     "oracle_s": round(t_orc, 3), "oracle_cores": oracle.num_threads(),
+                     "workload_stats": frame_stats([fr], [last], backward=d is not None)}
     return out
 
 
